@@ -1,0 +1,82 @@
+"""Multigrid V-cycle on the shifted operator (oracle; test infrastructure only).
+
+Algorithm 1 (two-grid cycle) applied recursively with one recursive call (the
+V-cycle, Section 2.2): nu_1 pre-relaxations, residual restriction
+r_2h = R(q - A_h u), coarse problem, correction u += P e_2h, nu_2
+post-relaxations. The coarse operators are re-discretisations of the shifted
+operator (Remark 2.1 and Section 3.2: the same stencil on the 2h grid, with the
+same omega, beta and shift alpha added to the attenuation). The coarsest level
+is solved either exactly (dense LU of the coarsest operator, the paper's 2D
+choice in Section 3.2) or inexactly by a fixed number of red-black Vanka sweeps
+from a zero guess (reading: a GPU-friendly stand-in for the paper's inexact
+hybrid-Kaczmarz coarsest solve of Section 5.3).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+from .discretization import Problem, assemble, coarsen, active_mask
+from .transfer import restriction, prolongation
+from .smoother import cell_dofs, cell_blocks, cell_colour, red_black_sweep
+
+# Damping w by hierarchy depth (Section 5.2: 0.55, 0.35, 0.25 for 2, 3, 4 levels; 0.2 for 5 is
+# a reading, since the paper stops at 4 levels).
+DEFAULT_DAMPING = {1: 0.55, 2: 0.55, 3: 0.35, 4: 0.25, 5: 0.2, 6: 0.2, 7: 0.2, 8: 0.2}
+
+
+class Hierarchy:
+    def __init__(self, pb: Problem, levels: int, alpha: float, damping=None, nu_pre: int = 2,
+                 nu_post: int = 2, coarse: str = "dense", coarse_sweeps: int = 0,
+                 coarse_damping: float = 1.0):
+        self.levels = levels
+        self.alpha = alpha
+        self.nu_pre, self.nu_post = nu_pre, nu_post
+        self.coarse, self.coarse_sweeps, self.coarse_damping = coarse, coarse_sweeps, coarse_damping
+        if damping is None:
+            damping = DEFAULT_DAMPING[levels]
+        self.w = list(damping) if np.ndim(damping) else [float(damping)] * levels
+        self.pbs = [pb]
+        for _ in range(levels - 1):
+            self.pbs.append(coarsen(self.pbs[-1]))
+        self.H = [assemble(p, alpha) for p in self.pbs]
+        self.R = [restriction(self.pbs[l], self.pbs[l + 1]) for l in range(levels - 1)]
+        self.P = [prolongation(self.pbs[l], self.pbs[l + 1]) for l in range(levels - 1)]
+        self.idx = [cell_dofs(p) for p in self.pbs]
+        self.colour = [cell_colour(p) for p in self.pbs]
+        self.V = [cell_blocks(self.H[l], self.idx[l]) for l in range(levels)]
+        last = levels - 1
+        self.act_c = active_mask(self.pbs[last])
+        if coarse == "dense":
+            Hc = self.H[last][self.act_c][:, self.act_c].toarray()
+            self.lu = sla.lu_factor(Hc)
+
+    def smooth(self, l, b, x, count, w):
+        for _ in range(count):
+            x = red_black_sweep(self.H[l], self.V[l], self.idx[l], self.colour[l], b, x, w)
+        return x
+
+    def coarse_solve(self, b):
+        last = self.levels - 1
+        x = np.zeros_like(b)
+        if self.coarse == "dense":
+            x[self.act_c] = sla.lu_solve(self.lu, b[self.act_c])
+        else:
+            x = self.smooth(last, b, x, self.coarse_sweeps, self.coarse_damping)
+        return x
+
+
+def vcycle(hier: Hierarchy, b, x=None, level: int = 0):
+    """One V(nu_1, nu_2) cycle for H_s x = b on `level`; x=None means a zero initial guess."""
+    b = np.asarray(b, dtype=np.complex128).ravel()
+    if level == hier.levels - 1:
+        return hier.coarse_solve(b)
+    x = np.zeros_like(b) if x is None else np.asarray(x, dtype=np.complex128).ravel().copy()
+    H = hier.H[level]
+    x = hier.smooth(level, b, x, hier.nu_pre, hier.w[level])
+    r = b - H @ x
+    bc = hier.R[level] @ r
+    ec = vcycle(hier, bc, None, level + 1)
+    x = x + hier.P[level] @ ec
+    x = hier.smooth(level, b, x, hier.nu_post, hier.w[level])
+    return x

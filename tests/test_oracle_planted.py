@@ -1,0 +1,109 @@
+"""Sensitivity of the oracle pins: a plausible mistake planted in the oracle (on the CPU,
+by monkeypatching one of its building blocks) must make at least one pin fail."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+import oracle.discretization as disc
+import oracle.transfer as tr
+import oracle.krylov as kr
+import oracle.smoother as sm
+import test_oracle_stencils as ts
+import test_oracle_transfer as tt
+import test_oracle_solver as tsol
+
+
+def _fails(fn, *args):
+    with pytest.raises(AssertionError):
+        fn(*args)
+
+
+def test_planted_wrong_spread_weights_break_the_symbol_pin(monkeypatch):
+    monkeypatch.setattr(disc, "_smooth121", lambda n, per: sp.csr_matrix(
+        sp.diags([np.full(n - 1, 1 / 3), np.full(n, 1 / 3), np.full(n - 1, 1 / 3)], [-1, 0, 1])))
+    _fails(ts._check_symbol, (8, 8), 0.5, (3, 5), 2.0 / 3.0, 0.3, 2)
+
+
+def test_planted_gradient_sign_breaks_the_stencil_pin(monkeypatch):
+    orig = disc._gradient_p
+    monkeypatch.setattr(disc, "_gradient_p", lambda pb, c: -orig(pb, c))
+    _fails(ts._check_symbol, (8, 8), 0.5, (1, 0), 1.0, 0.3, 2)
+
+
+def test_planted_mass_spread_weight_breaks_singer_turkel(monkeypatch):
+    orig = disc._mass_spread
+
+    def wrong(pb):
+        N = pb.ncell
+        m = orig(pb)
+        return m + (1 - pb.beta) * 0.05 * sp.identity(N)
+    monkeypatch.setattr(disc, "_mass_spread", wrong)
+    _fails(ts.test_singer_turkel_reproduced_at_beta_two_thirds, 1.0)
+
+
+def test_planted_dropped_transverse_term_in_3d_breaks_the_3d_symbol(monkeypatch):
+    orig = disc._derivative
+
+    def wrong(pb, comp, e, spread):
+        if not spread or pb.dim != 3:
+            return orig(pb, comp, e, spread)
+        return orig(pb, comp, e, False)  # spread silently dropped in 3D
+    monkeypatch.setattr(disc, "_derivative", wrong)
+    _fails(ts._check_symbol, (4, 4, 6), 1.0, (1, 2, 3), 2.0 / 3.0, 0.1, 3)
+
+
+def test_planted_swapped_prolongation_weights_break_the_stencil_pin(monkeypatch):
+    def wrong(nf, per):
+        nc = nf // 2
+        rows, cols, vals = [], [], []
+        for K in range(nc):
+            for off, w in ((-1, 0.75), (0, 0.25), (1, 0.25), (2, 0.75)):
+                f = (2 * K + off) % nf
+                rows.append(f); cols.append(K); vals.append(w)
+        return sp.csr_matrix((vals, (rows, cols)), shape=(nf, nc))
+    monkeypatch.setattr(tr, "_p_cell", wrong)
+    _fails(tt.test_restriction_and_prolongation_match_printed_stencils, 2)
+
+
+def test_planted_restriction_weights_break_the_two_grid_symbol(monkeypatch):
+    def wrong(nf, per):
+        nc = nf // 2
+        rows, cols, vals = [], [], []
+        for K in range(nc):
+            for off in (-1, 0, 1):
+                rows.append(K); cols.append((2 * K + off) % nf); vals.append(1 / 3)
+        return sp.csr_matrix((vals, (rows, cols)), shape=(nc, nf))
+    monkeypatch.setattr(tr, "_r_face", wrong)
+    _fails(tt.test_coarse_grid_correction_matches_two_grid_symbol, 2, 2.0 / 3.0)
+
+
+def test_planted_transposed_vanka_block_breaks_cell_exactness(monkeypatch):
+    orig = sm.cell_blocks
+    monkeypatch.setattr(oracle, "cell_blocks", lambda H, idx: np.transpose(orig(H, idx), (0, 2, 1)))
+    _fails(tsol.test_vanka_single_cell_with_unit_damping_zeroes_its_residuals, (8, 6))
+
+
+def test_planted_conjugation_error_in_gram_schmidt_breaks_the_krylov_pin(monkeypatch):
+    real_vdot = np.vdot
+
+    class NP:
+        def __getattr__(self, k):
+            return getattr(np, k)
+
+        @staticmethod
+        def vdot(a, b):
+            return real_vdot(b, a)
+    monkeypatch.setattr(kr, "np", NP())
+    _fails(tsol.test_fgmres_with_identity_preconditioner_matches_numpy_solve)
+
+
+def test_material_coarsening_is_exact_for_linear_media():
+    """Reading: coarse media are the mean of the 2^d children -- exact for linear fields."""
+    n = (8, 4, 6)
+    z, y, x = np.meshgrid(*[np.arange(v) + 0.5 for v in n[::-1]], indexing="ij")
+    f = 1.0 + 0.3 * x - 0.2 * y + 0.7 * z
+    pb = disc.Problem(n, 1.0, 1.0, 0.0, 2 / 3, f, f, f)
+    c = oracle.coarsen(pb)
+    zc, yc, xc = np.meshgrid(*[2 * (np.arange(v) + 0.5) for v in c.n[::-1]], indexing="ij")
+    np.testing.assert_allclose(c.mu, 1.0 + 0.3 * xc - 0.2 * yc + 0.7 * zc, atol=1e-13)

@@ -1,0 +1,156 @@
+"""Synthetic elastic media, frequencies and point sources.
+
+Arrays are indexed [z, y, x] (3D) or [y, x] (2D): the first grid axis x1 is the
+fastest-varying one. The depth axis is the last grid axis (x2 in 2D, x3 in 3D),
+i.e. the slowest array index.
+
+Velocity relations (Section 2.1): Vp = sqrt((lambda + 2 mu)/rho), Vs = sqrt(mu/rho).
+Frequency rule (Section 5): omega chosen for G_s points per minimum shear
+wavelength, omega = 2 pi min(Vs) / (G_s h).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Workload:
+    """One solve: medium, frequency, source, and the solver settings it is run with."""
+    name: str
+    n: tuple            # cells per axis, x1 first
+    h: float
+    lam: np.ndarray     # cell-centred, shape n[::-1]
+    mu: np.ndarray
+    rho: np.ndarray
+    omega: float
+    rhs: np.ndarray     # complex128, shape (dim+1,) + n[::-1]; (u_1..u_d, p) components
+    levels: int
+    alpha: float
+    damping: float
+    abl_cells: int
+    gamma: float = 0.01
+    beta: float = 2.0 / 3.0
+    abl_gamma_max: float = 2.0
+    nu_pre: int = 2
+    nu_post: int = 2
+    restart: int = 20
+    tol: float = 1e-6
+    coarse: str = "dense"          # "dense" or "smooth"
+    coarse_sweeps: int = 0
+    coarse_damping: float = 1.0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def dim(self) -> int:
+        return len(self.n)
+
+
+def lame_from_velocity(vp: np.ndarray, vs: np.ndarray, rho: np.ndarray):
+    """(lambda, mu) from Vp, Vs, rho via Vs^2 = mu/rho and Vp^2 = (lambda+2mu)/rho."""
+    mu = rho * vs * vs
+    lam = rho * vp * vp - 2.0 * mu
+    return lam, mu
+
+
+def omega_for_points_per_wavelength(vs_min: float, h: float, g_s: float = 10.0) -> float:
+    return 2.0 * np.pi * vs_min / (g_s * h)
+
+
+def random_field(shape, seed: int, sigma_cells: float) -> np.ndarray:
+    """White noise smoothed by a Gaussian of std `sigma_cells` (periodic wrap)."""
+    from scipy.ndimage import gaussian_filter
+    rng = np.random.default_rng(seed)
+    noise = rng.standard_normal(shape)
+    return gaussian_filter(noise, sigma=sigma_cells, mode="wrap")
+
+
+def gaussian_random_velocity(shape, seed: int, sigma_cells: float = 32.0,
+                             vmin: float = 1.5, vmax: float = 4.5) -> np.ndarray:
+    """Smooth random Vp field mapped affinely so that its min/max are [vmin, vmax]."""
+    f = random_field(shape, seed, sigma_cells)
+    lo, hi = f.min(), f.max()
+    return vmin + (vmax - vmin) * (f - lo) / (hi - lo)
+
+
+def point_source(n, component: int, index) -> np.ndarray:
+    """Unit point force on one DOF. `index` is the DOF's grid index, x1 first."""
+    dim = len(n)
+    q = np.zeros((dim + 1,) + tuple(n[::-1]), dtype=np.complex128)
+    q[(component,) + tuple(index[::-1])] = 1.0
+    return q
+
+
+def config_c1_homogeneous(n: int = 128) -> Workload:
+    """2D homogeneous lambda=2, mu=1, rho=1 (Vp=2, Vs=1), 10 points per shear wavelength,
+    unit force in u1 at the grid centre, 4 levels (coarsest n/8 squared, direct), ABL 16."""
+    shape = (n, n)
+    lam = np.full(shape, 2.0)
+    mu = np.ones(shape)
+    rho = np.ones(shape)
+    h = 1.0
+    omega = omega_for_points_per_wavelength(1.0, h)
+    rhs = point_source((n, n), 0, (n // 2, n // 2))
+    return Workload("c1_homogeneous_2d_%d" % n, (n, n), h, lam, mu, rho, omega, rhs,
+                    levels=4, alpha=0.4, damping=0.25, abl_cells=16, coarse="dense")
+
+
+def config_c2_random2d(n: int = 2048, seed: int = 0, levels: int = 5, source_depth: int = 32) -> Workload:
+    """2D smooth random medium: Vp in [1.5, 4.5] (Gaussian filter sigma 32 cells, correlation
+    length ~64 cells), Vs = Vp/sqrt(3), rho = 0.31 Vp^0.25; 10 points per minimum shear
+    wavelength; point force in the depth component u2 at (n/2, depth 32)."""
+    shape = (n, n)
+    sigma = 32.0 * n / 2048.0 if n < 2048 else 32.0
+    vp = gaussian_random_velocity(shape, seed, sigma_cells=sigma)
+    vs = vp / np.sqrt(3.0)
+    rho = 0.31 * vp ** 0.25
+    lam, mu = lame_from_velocity(vp, vs, rho)
+    h = 1.0
+    omega = omega_for_points_per_wavelength(float(vs.min()), h)
+    rhs = point_source((n, n), 1, (n // 2, min(source_depth, n - 1)))
+    return Workload("c2_random_2d_%d" % n, (n, n), h, lam, mu, rho, omega, rhs,
+                    levels=levels, alpha=0.5, damping=0.2, abl_cells=20, coarse="smooth",
+                    coarse_sweeps=16, coarse_damping=0.8)
+
+
+def config_c3_layered3d(n: int = 256, source=(128, 128, 24), levels: int = 4) -> Workload:
+    """3D three-layer medium (Vp 2.0/3.0/4.0 for depth fractions [0,80)/[80,170)/[170,256) of
+    256) plus a Gaussian inclusion Vp*(1 + 0.2 exp(-r^2/24^2)) at the centre; Vs = Vp/sqrt(3),
+    rho 1.0/1.2/1.4 by layer; 10 points per minimum shear wavelength; u3 point force."""
+    s = n / 256.0
+    z = (np.arange(n) + 0.5)
+    vp1 = np.where(z < 80 * s, 2.0, np.where(z < 170 * s, 3.0, 4.0))
+    rho1 = np.where(z < 80 * s, 1.0, np.where(z < 170 * s, 1.2, 1.4))
+    Z, Y, X = np.meshgrid(z, z, z, indexing="ij")
+    c = n / 2.0
+    r2 = (X - c) ** 2 + (Y - c) ** 2 + (Z - c) ** 2
+    vp = vp1[:, None, None] * (1.0 + 0.2 * np.exp(-r2 / (24.0 * s) ** 2))
+    rho = np.broadcast_to(rho1[:, None, None], vp.shape).copy()
+    vs = vp / np.sqrt(3.0)
+    lam, mu = lame_from_velocity(vp, vs, rho)
+    h = 1.0
+    omega = omega_for_points_per_wavelength(float(vs.min()), h)
+    src = tuple(int(round(v * s)) for v in source)
+    rhs = point_source((n, n, n), 2, src)
+    return Workload("c3_layered_3d_%d" % n, (n, n, n), h, lam, mu, rho, omega, rhs,
+                    levels=levels, alpha=0.4, damping=0.25, abl_cells=max(2, int(round(20 * s))),
+                    coarse="smooth", coarse_sweeps=16, coarse_damping=0.8)
+
+
+def small_heterogeneous(n, seed: int = 1, sigma_cells: float = 2.0, abl_cells: int = 2,
+                        levels: int = 2, omega_ppw: float = 10.0) -> Workload:
+    """A small random heterogeneous medium for parity tests (any dimension)."""
+    n = tuple(n)
+    shape = n[::-1]
+    vp = gaussian_random_velocity(shape, seed, sigma_cells=sigma_cells, vmin=1.5, vmax=3.0)
+    vs = vp / np.sqrt(3.0)
+    rho = 0.31 * vp ** 0.25
+    lam, mu = lame_from_velocity(vp, vs, rho)
+    h = 1.0
+    omega = omega_for_points_per_wavelength(float(vs.min()), h, omega_ppw)
+    rng = np.random.default_rng(seed + 7)
+    rhs = (rng.standard_normal((len(n) + 1,) + shape)
+           + 1j * rng.standard_normal((len(n) + 1,) + shape))
+    return Workload("small_%s_s%d" % ("x".join(map(str, n)), seed), n, h, lam, mu, rho, omega, rhs,
+                    levels=levels, alpha=0.4, damping=0.5, abl_cells=abl_cells, coarse="dense")

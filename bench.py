@@ -1,0 +1,328 @@
+"""Benchmark: time to a 1e-6 relative FP64 residual, FP32-cycle-preconditioned FGMRES vs the plain
+FP64 solve, and V-cycle HBM bandwidth, on one GB300.
+
+Workload (default): the 2D heterogeneous configuration -- 2048 x 2048 cells, smooth random medium
+(Vp 1.5-4.5, correlation length 64 cells), 10 points per minimum shear wavelength, point source at
+depth 32, 5-level V(2,2) hierarchy, FGMRES(20) to 1e-6. One "step" is one complete solve from a
+zero initial guess with the right-hand side resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl emg|reference] [--config c2|c1|c3]
+
+--impl reference times the FP64 CPU oracle (oracle/) on the host cores instead: each step runs a
+few FGMRES iterations on a crop of the same medium and extrapolates to the full solve.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-6 rel. residual & V-cycle HBM GB/s: FP32-precond vs plain FP64, 1 GB300"
+# Iteration count used to extrapolate the oracle's per-iteration time to a full solve in the
+# reference arm (which runs no GPU code): FGMRES(20) iterations of the FP64 solve of the 2048^2
+# configuration (the FP64 GPU solve reproduces the oracle's count within +-1 in the parity tests).
+REF_ITERS = {"c2": 300, "c1": 97, "c3": 60}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="emg", choices=["emg", "reference"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--restart", type=int, default=20)
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed plain-FP64 solves (after 1 warm-up)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    from workloads import config_c1_homogeneous, config_c2_random2d, config_c3_layered3d
+    return {"c1": config_c1_homogeneous, "c2": config_c2_random2d, "c3": config_c3_layered3d}[name]()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def oracle_sample(w, iters=3, crop=512):
+    """FP64 oracle on a crop of the same medium (same h, omega, shift, damping, absorbing layer):
+    returns (seconds per FGMRES iteration scaled to the full grid, description, threads)."""
+    import oracle
+    from oracle.discretization import Problem
+    d = w.dim
+    c = min(crop if d == 2 else 64, min(w.n))
+    sl = tuple(slice((n - c) // 2 if a < d - 1 else 0, ((n - c) // 2 if a < d - 1 else 0) + c)
+               for a, n in reversed(list(enumerate(w.n))))
+    n = (c,) * d
+    lv = w.levels
+    while c % (1 << (lv - 1)) or c >> (lv - 1) < 4:
+        lv -= 1
+    pb = Problem(n, w.h, w.omega, w.gamma, w.beta, w.lam[sl], w.mu[sl], w.rho[sl], abl_length=w.abl_cells * w.h,
+                 abl_gamma_max=w.abl_gamma_max)
+    coarse = "dense" if (c >> (lv - 1)) ** d * (d + 1) <= 4096 and w.coarse == "dense" else "smooth"
+    hier = oracle.Hierarchy(pb, lv, w.alpha, w.damping, nu_pre=w.nu_pre, nu_post=w.nu_post, coarse=coarse,
+                            coarse_sweeps=max(w.coarse_sweeps, 16), coarse_damping=w.coarse_damping)
+    H = oracle.assemble(pb, 0.0)
+    b = np.zeros(H.shape[0], complex)
+    b[oracle.active_mask(pb)] = 1.0
+    t0 = time.perf_counter()
+    _, its, _ = oracle.fgmres(lambda v: H @ v, lambda v: oracle.vcycle(hier, v), b, tol=1e-30, restart=20,
+                              max_iter=iters)
+    dt = (time.perf_counter() - t0) / its
+    scale = float(np.prod(w.n)) / float(np.prod(n))
+    desc = ("oracle FGMRES(20)+V(%d,%d) iterations on a %s crop of the same medium (%d levels), %d iterations "
+            "timed, per-iteration time scaled by the cell ratio %.1f" % (w.nu_pre, w.nu_post, "x".join(map(str, n)),
+                                                                         lv, its, scale))
+    threads = int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or os.cpu_count()
+    return dt * scale, desc, threads
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args.config)
+    iters = REF_ITERS[args.config]
+    vals = []
+    for s in range(args.warmup + args.steps):
+        per_it, desc, threads = oracle_sample(w, iters=2)
+        if s >= args.warmup:
+            vals.append(per_it * iters)
+    v = float(np.mean(vals))
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "c128", "data": "synthetic", "config": config_json(w, args),
+           "cpu_baseline": {"value": v, "unit": "s", "cores": threads, "kind": "oracle",
+                            "sample": desc + " x %d iterations (FP64 solve count)" % iters},
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def config_json(w, args):
+    return {"workload": w.name, "grid": "x".join(map(str, w.n)), "levels": w.levels, "cycle": "V(%d,%d)" % (
+        w.nu_pre, w.nu_post), "alpha": w.alpha, "damping": w.damping, "beta": round(w.beta, 6),
+        "krylov": "FGMRES(%d)" % args.restart, "tol": w.tol, "coarsest": w.coarse,
+        "l2": "inputs larger than L2 (vectors %d MB)" % int(16 * (w.dim + 1) * np.prod(w.n) / 2 ** 20),
+        "parallelism": "replicas" if args.gpus > 1 else "single"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2307_03242_gb300 import emg
+    w = workload(args.config)
+    shape = (w.dim + 1,) + tuple(w.n[::-1])
+    nvec = int(np.prod(shape))
+    dev = torch.device("cuda", local)
+    b = torch.from_numpy(w.rhs.astype(np.complex128)).to(dev)
+    s32 = emg.Solver(emg.params_from_workload(w, 32), w.lam, w.mu, w.rho)
+    x = torch.zeros_like(b)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def solve(s):
+        x.zero_()
+        return s.solve(b, x, tol=w.tol, max_iter=2000, restart=args.restart)
+
+    for _ in range(args.warmup):
+        st = solve(s32)
+    s32.profile_read(emg.K_ALL)
+    s32.profile(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        iters = []
+        for _ in range(args.steps):
+            st = solve(s32)
+            iters.append(st["iterations"])
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = s32.profile_read(emg.K_SMOOTH)
+    s32.profile(False)
+    launches = s32.profile_read(emg.K_ALL)["launches"]
+    t32 = ms / 1e3
+    res32 = st["rel_residual"]
+    if world > 1:
+        tt = torch.tensor([t32], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t32 = float(tt.item())
+
+    # V-cycle bandwidth (FP32 cycle on the finest level, zero initial guess)
+    bc = torch.zeros(shape, dtype=torch.complex64, device=dev)
+    bc.copy_(b)
+    xc = torch.zeros_like(bc)
+    for _ in range(3):
+        s32.vcycle(bc, xc)
+    barrier()
+    nv = 20
+    e0.record(stream)
+    for _ in range(nv):
+        s32.vcycle(bc, xc)
+    e1.record(stream)
+    barrier()
+    vms = e0.elapsed_time(e1) / nv
+    ncell = float(np.prod(w.n))
+    # algorithmic bytes per fine cell per V(2,2) cycle over all levels (unfused half-sweeps counted
+    # at their own minimum): see the design doc section 8
+    per_cell = vcycle_bytes_per_cell(w, 8, 4)
+    v_gbs = per_cell * ncell / (vms * 1e-3) / 1e9
+
+    # plain FP64 solve
+    s32.close()
+    s64 = emg.Solver(emg.params_from_workload(w, 64), w.lam, w.mu, w.rho)
+    st64 = solve(s64)
+    barrier()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.fp64_steps):
+        st64 = solve(s64)
+    e1.record(stream)
+    barrier()
+    t64 = e0.elapsed_time(e1) / args.fp64_steps / 1e3
+    s64.close()
+
+    # end to end through the public API with host buffers (copies inside the timed region)
+    s32 = emg.Solver(emg.params_from_workload(w, 32), w.lam, w.mu, w.rho)
+    bh = torch.from_numpy(w.rhs.astype(np.complex128).ravel()).pin_memory().numpy()
+    xh = torch.zeros(nvec, dtype=torch.complex128).pin_memory().numpy()
+    s32.solve_host(bh, xh, tol=w.tol, max_iter=2000, restart=args.restart)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xh[:] = 0
+        sth = s32.solve_host(bh, xh, tol=w.tol, max_iter=2000, restart=args.restart)
+    barrier()
+    te2e = (time.perf_counter() - t0) / args.steps
+    s32.close()
+
+    peak, peak_kind = load_peaks()
+    achieved = prof["bytes"] / (prof["ms"] * 1e-3) / 1e9 if prof["ms"] > 0 else None
+    out = {"metric": METRIC, "value": t32, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": t32 * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "c64 cycle / c128 outer", "data": "synthetic", "config": config_json(w, args),
+           "iterations": {"fp32_precond": int(np.median(iters)), "fp64_plain": st64["iterations"]},
+           "rel_residual": {"fp32_precond": res32, "fp64_plain": st64["rel_residual"]},
+           "fp64_plain": {"value": t64, "unit": "s", "steps": args.fp64_steps, "warmup": 1},
+           "speedup_vs_fp64": t64 / t32,
+           "vcycle": {"ms": vms, "gbs_algorithmic": v_gbs, "bytes_per_cell": per_cell,
+                      "frac_of_hbm": v_gbs / peak},
+           "roofline": {"kernel": "vanka half-sweep (finest level, FP32)", "bound": "hbm", "achieved": achieved,
+                        "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                        "frac": achieved / peak if achieved else None, "traffic": None,
+                        "launches": prof["launches"], "avg_launch_ms": prof["ms"] / max(prof["launches"], 1),
+                        "bytes_per_launch": prof["bytes"] / max(prof["launches"], 1)},
+           "e2e": {"value": te2e, "unit": "s", "h2d_bytes_per_step": 2 * nvec * 16, "d2h_bytes_per_step": nvec * 16},
+           "gpu_launches": int(launches)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per_it, desc, threads = oracle_sample(w)
+        out["cpu_baseline"] = {"value": per_it * out["iterations"]["fp32_precond"], "unit": "s", "cores": threads,
+                               "kind": "oracle", "sample": desc + " x the FP32 solve's iteration count"}
+    out["clocks"] = clk.summary()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def vcycle_bytes_per_cell(w, cw, rw):
+    """Algorithmic bytes per finest cell of one V(nu1,nu2) cycle (unfused red/black half-sweeps):
+    per level with c = complex word, r = real word, S = (d+1)c:
+      half-sweep   = S (x) + (d+1/2)c (b) + 3r + (d+1/2)c (writes)
+      restriction  = 2S + 3r + S/2^d,  prolongation = 2S/... (read e, read+write x) = 2S + S/2^d
+    summed over levels with the 2^-d cell ratio; the coarsest level's sweeps counted likewise."""
+    d = w.dim
+    S = (d + 1) * cw
+    half = S + 2 * (d + 0.5) * cw + 3 * rw
+    tot, frac = 0.0, 1.0
+    for l in range(w.levels):
+        if l < w.levels - 1:
+            lvl = 2 * (w.nu_pre + w.nu_post) * half + (2 * S + 3 * rw + S / 2 ** d) + (2 * S + S / 2 ** d)
+        else:
+            lvl = 2 * w.coarse_sweeps * half if w.coarse == "smooth" else 0.0
+        tot += frac * lvl
+        frac /= 2 ** d
+    return tot
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * emg -- matrix-free shifted-Laplacian multigrid for the elastic Helmholtz equation in mixed
+ * (u, p) form on a beta-spread staggered (MAC) grid, for one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Yovel & Treister, "LFA-tuned matrix-free multigrid method for the elastic Helmholtz
+ * equation" (arXiv 2307.03242). Section and equation numbers below refer to that paper.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid: n[0] x n[1] (x n[2]) cells of size h; x1 is the fastest-varying index; the last axis is
+ * depth. A field vector holds dim+1 complex components (u_1, .., u_dim, p), each an array of
+ * n[0]*n[1](*n[2]) complex numbers in that order (component-major, x1 fastest, real and
+ * imaginary parts interleaved). u_d[k] is the displacement on the face normal to x_d on the LOW
+ * side of cell k (position x_d = k_d h, cell-centred in the other coordinates); p[k] sits at the
+ * cell centre (Section 2.3, Fig. 2.1). The faces u_d with k_d = 0 lie on the domain boundary and
+ * are not unknowns: inputs there are ignored and outputs there are written as zero.
+ *
+ * Precision: "FP64 vector" = complex128 (2 x double per entry); "cycle vector" = complex64 when
+ * the handle was created with cycle_precision = 32, complex128 when 64.
+ *
+ * Memory: unless an entry point says "host", every vector pointer is a DEVICE pointer on the
+ * current CUDA device, owned by the caller, at least 16-byte aligned, and not aliased with any
+ * other argument. The library owns the hierarchy (material copies, level vectors, Krylov basis);
+ * it allocates all of it in emg_create and frees it in emg_destroy.
+ *
+ * Streams: every call is ordered on the stream given to emg_create and returns without
+ * synchronising the stream, except where stated (emg_solve and emg_solve_host synchronise,
+ * because the Krylov loop reads reductions on the host).
+ *
+ * Errors: no exception crosses the ABI. Every call returns an emg_status; on failure
+ * emg_last_error() returns a message for the calling thread. Invalid arguments are rejected
+ * before any work is enqueued.
+ */
+#ifndef EMG_H
+#define EMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EMG_MAX_LEVELS 10
+
+typedef struct emg_ctx* emg_handle;
+
+typedef enum {
+  EMG_OK = 0,
+  EMG_ERR_INVALID = 1,    /* bad argument, unsupported size, non-finite or non-positive material */
+  EMG_ERR_NOMEM = 2,      /* device allocation failed */
+  EMG_ERR_CUDA = 3,       /* a CUDA call failed (message from the runtime) */
+  EMG_ERR_NONFINITE = 4,  /* NaN/Inf met in a Krylov reduction */
+  EMG_NOT_CONVERGED = 5,  /* emg_solve stopped at max_iter; x holds the last iterate */
+  EMG_ERR_TIMEOUT = 6     /* reserved for bounded device-side waits */
+} emg_status;
+
+enum { EMG_COARSE_DENSE = 0, EMG_COARSE_SMOOTH = 1 };
+
+/* Solver description. All lengths in the same unit as h. */
+typedef struct {
+  int32_t dim;              /* 2 or 3 */
+  int32_t n[3];             /* cells per axis (x1 first); every n[a] divisible by 2^(levels-1) */
+  double h;                 /* finest cell size */
+  double omega;             /* angular frequency (Eq. 2.1) */
+  double gamma;             /* physical attenuation of the unshifted operator (Sec. 5: 0.01) */
+  double alpha;             /* complex shift of the cycle operator, added to gamma (Eq. 2.9) */
+  double beta;              /* stencil spread weight, Eq. 3.2-3.5 (LFA-tuned: 2/3) */
+  int32_t abl_cells;        /* absorbing layer thickness in finest cells, on all sides (0: none) */
+  double abl_gamma_max;     /* attenuation added at the outer boundary; profile gamma_max*(d/L)^2 */
+  int32_t levels;           /* multigrid levels, 1..EMG_MAX_LEVELS */
+  int32_t nu_pre, nu_post;  /* pre- and post-smoothing sweeps (Alg. 1) */
+  double damping[EMG_MAX_LEVELS]; /* Vanka damping w per level; 0 selects the default by depth */
+  int32_t coarse_solver;    /* EMG_COARSE_DENSE (exact, host LU) or EMG_COARSE_SMOOTH */
+  int32_t coarse_sweeps;    /* red-black sweeps on the coarsest level for EMG_COARSE_SMOOTH */
+  double coarse_damping;    /* Vanka damping on the coarsest level for EMG_COARSE_SMOOTH */
+  int32_t cycle_precision;  /* 32: FP32 cycle with FP64 outer solve; 64: everything in FP64 */
+} emg_params;
+
+typedef struct {
+  int32_t iterations;       /* preconditioned FGMRES iterations (= V-cycles) */
+  int32_t restarts;
+  double rel_residual;      /* true ||b - H x||_2 / ||b||_2 at exit, in FP64 */
+  double* history;          /* optional, caller-owned host array: estimated relative residual
+                               after each iteration (history[0] = initial) */
+  int32_t history_cap;      /* capacity of history (0: none) */
+  int32_t history_len;      /* entries written */
+} emg_stats;
+
+/* Build the multigrid hierarchy (Sec. 3.2: re-discretisation on every level; coarse media are
+ * the mean of the 2^dim children). lam, mu, rho: FP64 cell-centred arrays of n[0]*n[1](*n[2])
+ * values, on the host (on_device = 0) or on the device (on_device = 1); they are copied.
+ * cuda_stream: a cudaStream_t, or NULL for the legacy default stream.
+ * Rejects: dim not 2/3; n not divisible by 2^(levels-1); a coarsest grid below 2 cells per
+ * axis; non-finite or non-positive mu, rho, lam+mu; EMG_COARSE_DENSE with more than 4096
+ * coarsest unknowns. On success *out is a new handle. */
+emg_status emg_create(const emg_params* params, const double* lam, const double* mu,
+                      const double* rho, int on_device, void* cuda_stream, emg_handle* out);
+
+/* Free every device and host resource of the handle. NULL is accepted. */
+emg_status emg_destroy(emg_handle h);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* emg_last_error(void);
+
+/* y = H x (shifted = 0) or y = H_s x (shifted = 1) on the finest level in FP64, Eq. 3.10 with the
+ * sign of Eq. 4.4; H_s adds alpha to the attenuation (Eq. 2.9). x, y: FP64 vectors. */
+emg_status emg_apply(emg_handle h, int shifted, const void* x, void* y);
+
+/* x <- one V(nu_pre, nu_post)-cycle for H_s x = b on the finest level (Alg. 1 applied
+ * recursively with one recursive call). zero_guess = 1 ignores the input x. b, x: cycle vectors. */
+emg_status emg_vcycle(emg_handle h, const void* b, void* x, int zero_guess);
+
+/* Solve H x = b (unshifted, FP64) by right-preconditioned restarted FGMRES(restart) with one
+ * V-cycle as preconditioner (Sec. 3.2, 5). x: in = initial guess, out = solution. Stops when the
+ * true relative residual ||b - H x|| / ||b|| <= tol or after max_iter iterations
+ * (EMG_NOT_CONVERGED; x then holds the last iterate). restart in 1..64. b, x: FP64 vectors.
+ * stats may be NULL. Synchronises the stream. */
+emg_status emg_solve(emg_handle h, const void* b, void* x, double tol, int max_iter, int restart,
+                     emg_stats* stats);
+
+/* emg_solve with HOST vectors: b_host and x_host are host arrays of (dim+1)*ncell complex128
+ * (pinned or pageable). The copies to and from the device are part of the call. */
+emg_status emg_solve_host(emg_handle h, const double* b_host, double* x_host, double tol,
+                          int max_iter, int restart, emg_stats* stats);
+
+/* ---- Per-step entry points (one row of the cycle each; used for parity checks). ----
+ * `level` 0 is the finest. Vectors are cycle vectors of that level's size. */
+
+/* Grid of a level: cells per axis and cell size. */
+emg_status emg_level_info(emg_handle h, int level, int32_t n[3], double* cell_size);
+
+/* x <- `sweeps` red-black full Vanka sweeps on H_s of `level` (Sec. 2.3, 3.2): colour 0 then
+ * colour 1, each cell's (2d+1)x(2d+1) block solved exactly and damped by the level's w. */
+emg_status emg_smooth(emg_handle h, int level, const void* b, void* x, int sweeps);
+
+/* b_coarse <- R (b - H_s x) from `level` to level+1 (Eq. 2.11-2.13, Alg. 1 step 2). */
+emg_status emg_residual_restrict(emg_handle h, int level, const void* b, const void* x,
+                                 void* b_coarse);
+
+/* x <- x + P e_coarse from level+1 to `level` (Eq. 2.11-2.13, Alg. 1 step 4). */
+emg_status emg_prolong_correct(emg_handle h, int level, const void* e_coarse, void* x);
+
+/* x <- coarsest-level solve of H_s x = b (exact for EMG_COARSE_DENSE, else coarse_sweeps
+ * red-black sweeps from zero). b, x: cycle vectors of the coarsest level. */
+emg_status emg_coarse_solve(emg_handle h, const void* b, void* x);
+
+/* ---- Instrumentation. ----
+ * While enabled, the library records a CUDA event pair on its stream around every launch of
+ * the listed kernel classes on the finest level. emg_profile_read synchronises the stream and
+ * returns the summed event time, the launch count and the algorithmic bytes of those launches,
+ * then resets the counters. kernel_class is one of EMG_K_* (EMG_K_ALL: launch count only). */
+enum { EMG_K_SMOOTH = 0, EMG_K_RESTRICT = 1, EMG_K_PROLONG = 2, EMG_K_APPLY64 = 3,
+       EMG_K_KRYLOV = 4, EMG_K_COUNT = 5,
+       EMG_K_ALL = 5 /* emg_profile_read(EMG_K_ALL): launches = every kernel launched by the handle
+                        on any level since the last read (counted even when profiling is off) */ };
+emg_status emg_profile(emg_handle h, int enable);
+emg_status emg_profile_read(emg_handle h, int kernel_class, double* total_ms, int64_t* launches,
+                            double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMG_H */

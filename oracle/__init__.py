@@ -24,12 +24,12 @@ Eq. symbolTG, dense direct solves and plane-wave solutions. The full Vanka
 smoother has no printed symbol in the paper; it is pinned by the single-cell
 exactness property and by the converged solves only.
 """
-from .discretization import Problem, assemble, apply, active_mask, coarsen, gamma_abl, dof_shape
+from .discretization import Problem, assemble, apply, active_mask, coarsen, gamma_abl, dof_shape, window
 from .transfer import restriction, prolongation
 from .smoother import cell_dofs, cell_blocks, red_black_sweep, vanka_cell_update
 from .multigrid import Hierarchy, vcycle
 from .krylov import fgmres
 
-__all__ = ["Problem", "assemble", "apply", "active_mask", "coarsen", "gamma_abl", "dof_shape",
+__all__ = ["Problem", "assemble", "apply", "active_mask", "coarsen", "gamma_abl", "dof_shape", "window",
            "restriction", "prolongation", "cell_dofs", "cell_blocks", "red_black_sweep",
            "vanka_cell_update", "Hierarchy", "vcycle", "fgmres"]

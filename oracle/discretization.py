@@ -52,11 +52,14 @@ class Problem:
     abl_gamma_max: float = 0.0
     domain: tuple = None     # physical domain length per axis (defaults to n*h)
     periodic: bool = False
+    origin: tuple = None     # cell offset of this grid inside a larger domain (windowed evaluation)
 
     def __post_init__(self):
         self.n = tuple(int(v) for v in self.n)
         if self.domain is None:
             self.domain = tuple(v * self.h for v in self.n)
+        if self.origin is None:
+            self.origin = (0,) * len(self.n)
 
     @property
     def dim(self) -> int:
@@ -162,7 +165,7 @@ def _positions(pb: Problem, comp):
     grids = np.meshgrid(*[np.arange(c) for c in pb.n[::-1]], indexing="ij")
     pos = []
     for a in range(d):
-        k = grids[d - 1 - a].astype(np.float64)
+        k = grids[d - 1 - a].astype(np.float64) + pb.origin[a]
         pos.append(k * pb.h if a == comp else (k + 0.5) * pb.h)
     return pos
 
@@ -278,6 +281,17 @@ def apply(pb: Problem, x, shift: float = 0.0):
     return (H @ np.asarray(x, dtype=np.complex128).ravel()).reshape(dof_shape(pb))
 
 
+def window(pb: Problem, lo, hi) -> Problem:
+    """The sub-grid of cells lo[a] <= k_a < hi[a] placed at its position in `pb`'s domain.
+
+    Rows of the window's operator that are at least 3 cells away from every cut edge equal the
+    rows of `pb`'s operator (the stencil reaches 2 cells); cut edges are treated as boundaries."""
+    sl = tuple(slice(lo[a], hi[a]) for a in reversed(range(pb.dim)))
+    n = tuple(hi[a] - lo[a] for a in range(pb.dim))
+    org = tuple(pb.origin[a] + lo[a] for a in range(pb.dim))
+    return replace(pb, n=n, lam=pb.lam[sl], mu=pb.mu[sl], rho=pb.rho[sl], domain=pb.domain, origin=org)
+
+
 def coarsen(pb: Problem) -> Problem:
     """Re-discretisation problem on the 2h grid (Section 3.2): same omega, beta, gamma and
     absorbing layer (physical thickness); material = arithmetic mean of the 2^d children
@@ -295,4 +309,5 @@ def coarsen(pb: Problem) -> Problem:
             g = g.reshape(sh).mean(axis=ax + 1)
         return g
 
-    return replace(pb, n=nc, h=2.0 * pb.h, lam=avg(pb.lam), mu=avg(pb.mu), rho=avg(pb.rho))
+    org = tuple(o // 2 for o in pb.origin)
+    return replace(pb, n=nc, h=2.0 * pb.h, lam=avg(pb.lam), mu=avg(pb.mu), rho=avg(pb.rho), origin=org)

@@ -1,0 +1,961 @@
+// Host side of the emg library: hierarchy setup, V-cycle recursion, FGMRES outer solve, C ABI.
+//
+// Paper: Yovel & Treister, arXiv 2307.03242. The V-cycle is Algorithm 1 applied recursively with
+// one recursive call (Section 2.2) on the shifted operator H_s (Eq. 2.9: alpha added to the
+// attenuation), re-discretised on every level (Remark 2.1, Section 3.2). The outer solver is
+// right-preconditioned restarted flexible GMRES (Sections 3.2, 5) in FP64; the cycle runs in the
+// precision chosen at creation (FP32 for the mixed-precision solve of Section 5.3).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <memory>
+#include <type_traits>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "emg.h"
+#include "launch.h"
+#include "stencil2d.cuh"
+#include "stencil3d.cuh"
+#include "vector_kernels.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+struct EmgError {
+  emg_status s;
+  std::string msg;
+};
+
+[[noreturn]] void raise(emg_status s, const std::string& m) { throw EmgError{s, m}; }
+
+#define CK(x)                                                                                   \
+  do {                                                                                          \
+    cudaError_t e_ = (x);                                                                       \
+    if (e_ != cudaSuccess) raise(EMG_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define CKL() CK(cudaGetLastError())
+#define LAUNCHED(c) ((c).launches++)
+
+// Device buffer owned by the handle.
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void alloc(size_t nbytes) {
+    release();
+    if (nbytes == 0) return;
+    cudaError_t e = cudaMalloc(&p, nbytes);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      raise(EMG_ERR_NOMEM, "cudaMalloc(" + std::to_string(nbytes) + " bytes): " + cudaGetErrorString(e));
+    }
+    bytes = nbytes;
+  }
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+struct Level {
+  int n[3] = {1, 1, 1};
+  double h = 1.0;
+  size_t ncell = 0;
+  double w = 0.5;                         // Vanka damping on this level
+  std::vector<double> lam_h, mu_h, rho_h;  // host FP64 material (setup, dense coarse assembly)
+  DBuf mu, rho, cp;                        // device material in the cycle precision
+  DBuf b, x, alt;                          // cycle vectors: b, x hold dim+1 components, alt dim
+};
+
+}  // namespace
+
+struct emg_ctx {
+  emg_params prm{};
+  int dim = 2, L = 1, prec = 32, sms = 148;
+  cudaStream_t st = nullptr;
+  std::vector<Level> lv;
+  DBuf mu64, rho64, cp64;  // finest material in FP64 for the outer operator
+  DBuf cinv;               // dense inverse of the coarsest operator (cycle precision)
+  int cn = 0;
+  // Krylov workspace
+  int km = 0;
+  DBuf V, Z, part, red, wk64, hb, hx;
+  double* hred = nullptr;  // pinned
+  size_t hb_bytes = 0;
+  // instrumentation
+  bool prof = false;
+  struct Rec { int cls; cudaEvent_t a, b; double bytes; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  double pms[EMG_K_COUNT] = {0};
+  int64_t pn[EMG_K_COUNT] = {0};
+  double pbytes[EMG_K_COUNT] = {0};
+  int64_t launches = 0;  // every kernel launch, any level
+
+  size_t nvec() const { return (size_t)(dim + 1) * lv[0].ncell; }
+  ~emg_ctx() {
+    if (hred) cudaFreeHost(hred);
+    for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+double default_damping(int levels) {
+  switch (levels) {
+    case 1: case 2: return 0.55;
+    case 3: return 0.35;
+    case 4: return 0.25;
+    default: return 0.2;
+  }
+}
+
+template <typename T>
+Grid<T> make_grid(const emg_ctx& c, int l, bool shifted, const void* mu, const void* rho, const void* cp) {
+  const Level& L = c.lv[l];
+  const emg_params& p = c.prm;
+  Grid<T> g;
+  g.nx = L.n[0];
+  g.ny = L.n[1];
+  g.nz = c.dim == 3 ? L.n[2] : 1;
+  g.h = (T)L.h;
+  g.ih = (T)(1.0 / L.h);
+  g.beta = (T)p.beta;
+  g.sm = (T)((1.0 - p.beta) / (2.0 * c.dim));
+  g.w2 = (T)(p.omega * p.omega);
+  g.att = (T)(p.gamma + (shifted ? p.alpha : 0.0));
+  g.ablL = (T)(p.abl_cells > 0 ? p.abl_cells * p.h : 0.0);
+  g.ablG = (T)p.abl_gamma_max;
+  g.Lx = (T)(p.n[0] * p.h);
+  g.Ly = (T)(p.n[1] * p.h);
+  g.Lz = (T)(c.dim == 3 ? p.n[2] * p.h : 0.0);
+  g.mu = (const T*)mu;
+  g.rho = (const T*)rho;
+  g.cp = (const T*)cp;
+  return g;
+}
+
+template <typename T> Grid<T> level_grid(const emg_ctx& c, int l) {
+  const Level& L = c.lv[l];
+  return make_grid<T>(c, l, true, L.mu.p, L.rho.p, L.cp.p);
+}
+
+// ---------------------------------------------------------------- instrumentation
+struct ProfScope {
+  emg_ctx& c;
+  int cls;
+  double bytes;
+  bool on;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(emg_ctx& c_, int cls_, int level, double bytes_) : c(c_), cls(cls_), bytes(bytes_) {
+    on = c.prof && level == 0;
+    if (!on) return;
+    a = take();
+    b = take();
+    CK(cudaEventRecord(a, c.st));
+  }
+  cudaEvent_t take() {
+    if (!c.pool.empty()) { cudaEvent_t e = c.pool.back(); c.pool.pop_back(); return e; }
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    return e;
+  }
+  ~ProfScope() {
+    if (!on) return;
+    cudaEventRecord(b, c.st);
+    c.recs.push_back({cls, a, b, bytes});
+  }
+};
+
+void prof_flush(emg_ctx& c) {
+  if (c.recs.empty()) return;
+  CK(cudaStreamSynchronize(c.st));
+  for (auto& r : c.recs) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    c.pms[r.cls] += ms;
+    c.pn[r.cls] += 1;
+    c.pbytes[r.cls] += r.bytes;
+    c.pool.push_back(r.a);
+    c.pool.push_back(r.b);
+  }
+  c.recs.clear();
+}
+
+// ---------------------------------------------------------------- launch helpers
+int vec_blocks(const emg_ctx& c, size_t n) {
+  size_t b = (n + 255) / 256;
+  return (int)std::max<size_t>(1, std::min<size_t>(b, (size_t)c.sms * 8));
+}
+
+// Algorithmic bytes (minimum traffic) of the fine-level kernels, per cell, used by the
+// instrumentation: a half-sweep reads x, b on the colour's DOFs, 3 material reals and writes
+// every face plus the colour's pressures.
+template <typename T> double half_sweep_bytes(const emg_ctx& c) {
+  const double cw = 2.0 * sizeof(T), rw = sizeof(T);
+  const int d = c.dim;
+  return (double)c.lv[0].ncell * ((d + 1) * cw + (d + 0.5) * cw + 3 * rw + (d + 0.5) * cw);
+}
+
+// ---------------------------------------------------------------- cycle pieces
+template <typename T>
+void launch_apply(emg_ctx& c, const Grid<T>& g, const void* x, bool x32, const cx<T>* b, cx<T>* y) {
+  if (x32) {
+    if constexpr (std::is_same<T, double>::value) {
+      if (c.dim == 2) launch_apply2<double, float>(g, (const cx<float>*)x, b, y, c.st);
+      else launch_apply3<double, float>(g, (const cx<float>*)x, b, y, c.st);
+    } else {
+      raise(EMG_ERR_INVALID, "FP32 input requires the FP64 operator");
+    }
+  } else {
+    if (c.dim == 2) launch_apply2<T, T>(g, (const cx<T>*)x, b, y, c.st);
+    else launch_apply3<T, T>(g, (const cx<T>*)x, b, y, c.st);
+  }
+  CKL();
+  LAUNCHED(c);
+}
+
+template <typename T>
+void smooth(emg_ctx& c, int l, const cx<T>* b, cx<T>* x, int sweeps, double w, bool zero_first) {
+  Level& L = c.lv[l];
+  Grid<T> g = level_grid<T>(c, l);
+  const size_t N = L.ncell;
+  cx<T>* alt = L.alt.as<cx<T>>();
+  cx<T>* p = x + (size_t)c.dim * N;
+  const double bytes = l == 0 ? half_sweep_bytes<T>(c) : 0.0;
+  for (int s = 0; s < sweeps; ++s) {
+    for (int colour = 0; colour < 2; ++colour) {
+      const cx<T>* uin = colour == 0 ? x : alt;
+      cx<T>* uout = colour == 0 ? alt : x;
+      const int zin = (zero_first && s == 0 && colour == 0) ? 1 : 0;
+      ProfScope ps(c, EMG_K_SMOOTH, l, bytes);
+      if (c.dim == 2) launch_vanka2<T>(g, b, uin, uout, p, colour, (T)w, zin, c.st);
+      else launch_vanka3<T>(g, b, uin, uout, p, colour, (T)w, zin, c.st);
+      CKL();
+  LAUNCHED(c);
+    }
+  }
+  if (sweeps == 0 && zero_first) CK(cudaMemsetAsync(x, 0, (c.dim + 1) * N * sizeof(cx<T>), c.st));
+}
+
+template <typename T>
+void residual_restrict(emg_ctx& c, int l, const cx<T>* b, const cx<T>* x, cx<T>* bc, bool zero_x) {
+  Level& L = c.lv[l];
+  Level& C = c.lv[l + 1];
+  Grid<T> g = level_grid<T>(c, l);
+  const double cw = 2.0 * sizeof(T);
+  ProfScope ps(c, EMG_K_RESTRICT, l, (double)L.ncell * (2 * (c.dim + 1) * cw + 3 * sizeof(T)) + C.ncell * (c.dim + 1) * cw);
+  if (c.dim == 2) launch_restrict2<T>(g, b, x, bc, C.n, zero_x ? 1 : 0, c.st);
+  else launch_restrict3<T>(g, b, x, bc, C.n, zero_x ? 1 : 0, c.st);
+  CKL();
+  LAUNCHED(c);
+}
+
+template <typename T>
+void prolong_correct(emg_ctx& c, int l, const cx<T>* e, cx<T>* x) {
+  Level& L = c.lv[l];
+  Level& C = c.lv[l + 1];
+  const double cw = 2.0 * sizeof(T);
+  ProfScope ps(c, EMG_K_PROLONG, l, (double)L.ncell * 2 * (c.dim + 1) * cw + C.ncell * (c.dim + 1) * cw);
+  if (c.dim == 2) launch_prolong2<T>(e, x, L.n, C.n, c.st);
+  else launch_prolong3<T>(e, x, L.n, C.n, c.st);
+  CKL();
+  LAUNCHED(c);
+}
+
+template <typename T>
+void coarse_solve(emg_ctx& c, const cx<T>* b, cx<T>* x) {
+  const int l = c.L - 1;
+  if (c.prm.coarse_solver == EMG_COARSE_DENSE) {
+    const int n = c.cn;
+    kv::dense_gemv<T><<<(n + 7) / 8, 256, 0, c.st>>>(c.cinv.as<cx<T>>(), b, x, n);
+    CKL();
+  LAUNCHED(c);
+  } else {
+    smooth<T>(c, l, b, x, c.prm.coarse_sweeps, c.prm.coarse_damping, true);
+  }
+}
+
+template <typename T>
+void vcycle(emg_ctx& c, int l, const cx<T>* b, cx<T>* x, bool zero_guess) {
+  if (l == c.L - 1) {
+    coarse_solve<T>(c, b, x);
+    return;
+  }
+  Level& L = c.lv[l];
+  Level& C = c.lv[l + 1];
+  if (zero_guess && c.prm.nu_pre == 0) CK(cudaMemsetAsync(x, 0, (c.dim + 1) * L.ncell * sizeof(cx<T>), c.st));
+  smooth<T>(c, l, b, x, c.prm.nu_pre, L.w, zero_guess);
+  residual_restrict<T>(c, l, b, x, C.b.as<cx<T>>(), false);
+  vcycle<T>(c, l + 1, C.b.as<cx<T>>(), C.x.as<cx<T>>(), true);
+  prolong_correct<T>(c, l, C.x.as<cx<T>>(), x);
+  smooth<T>(c, l, b, x, c.prm.nu_post, L.w, false);
+}
+
+// ---------------------------------------------------------------- host assembly of the coarsest operator
+// Column-by-column application of the same stencil functions the kernels use, restricted to the
+// neighbourhood of each unit vector; then a Gauss-Jordan inverse with partial pivoting in FP64.
+void assemble_dense(const emg_ctx& c, std::vector<std::complex<double>>& A, std::vector<int>& act) {
+  const int l = c.L - 1;
+  const Level& L = c.lv[l];
+  const int d = c.dim;
+  std::vector<double> cph(L.ncell);
+  for (size_t k = 0; k < L.ncell; ++k) cph[k] = 1.0 / (L.lam_h[k] + L.mu_h[k]);
+  Grid<double> g = make_grid<double>(c, l, true, L.mu_h.data(), L.rho_h.data(), cph.data());
+  const int nx = L.n[0], ny = L.n[1], nz = d == 3 ? L.n[2] : 1;
+  const size_t N = L.ncell, NF = (d + 1) * N;
+  act.assign(NF, 1);
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t q = ((size_t)k * ny + j) * nx + i;
+        if (i == 0) act[q] = 0;
+        if (j == 0) act[N + q] = 0;
+        if (d == 3 && k == 0) act[2 * N + q] = 0;
+      }
+  A.assign(NF * NF, 0.0);
+  std::vector<cx<double>> x(NF);
+  for (size_t col = 0; col < NF; ++col) {
+    if (!act[col]) continue;
+    std::fill(x.begin(), x.end(), czero<double>());
+    x[col] = mkc(1.0, 0.0);
+    const size_t q = col % N;
+    const int ci = (int)(q % nx), cj = (int)((q / nx) % ny), ck = (int)(q / ((size_t)nx * ny));
+    for (int k = std::max(0, ck - 2); k <= std::min(nz - 1, ck + 2); ++k)
+      for (int j = std::max(0, cj - 2); j <= std::min(ny - 1, cj + 2); ++j)
+        for (int i = std::max(0, ci - 2); i <= std::min(nx - 1, ci + 2); ++i) {
+          size_t r = ((size_t)k * ny + j) * nx + i;
+          cx<double> y[4];
+          if (d == 2) {
+            y[0] = i >= 1 ? s2::row_u1(x.data(), x.data() + 2 * N, g, i, j) : czero<double>();
+            y[1] = j >= 1 ? s2::row_u2(x.data() + N, x.data() + 2 * N, g, i, j) : czero<double>();
+            y[2] = s2::row_p(x.data(), x.data() + N, x.data() + 2 * N, g, i, j);
+          } else {
+            const cx<double>* u[3] = {x.data(), x.data() + N, x.data() + 2 * N};
+            for (int cc = 0; cc < 3; ++cc)
+              y[cc] = (cc == 0 ? i : cc == 1 ? j : k) >= 1 ? s3::row_u(cc, u[cc], x.data() + 3 * N, g, i, j, k)
+                                                         : czero<double>();
+            y[3] = s3::row_p(u, x.data() + 3 * N, g, i, j, k);
+          }
+          for (int cc = 0; cc <= d; ++cc) {
+            size_t row = cc * N + r;
+            if (act[row]) A[row * NF + col] = std::complex<double>(y[cc].re, y[cc].im);
+          }
+        }
+  }
+}
+
+void invert_dense(std::vector<std::complex<double>>& A, const std::vector<int>& act, std::vector<std::complex<double>>& Ainv) {
+  const size_t NF = act.size();
+  std::vector<size_t> idx;
+  for (size_t i = 0; i < NF; ++i)
+    if (act[i]) idx.push_back(i);
+  const size_t n = idx.size();
+  std::vector<std::complex<double>> M(n * 2 * n, 0.0);
+  for (size_t r = 0; r < n; ++r) {
+    for (size_t s = 0; s < n; ++s) M[r * 2 * n + s] = A[idx[r] * NF + idx[s]];
+    M[r * 2 * n + n + r] = 1.0;
+  }
+  const size_t W = 2 * n;
+  for (size_t k = 0; k < n; ++k) {
+    size_t piv = k;
+    double best = std::abs(M[k * W + k]);
+    for (size_t r = k + 1; r < n; ++r)
+      if (std::abs(M[r * W + k]) > best) { best = std::abs(M[r * W + k]); piv = r; }
+    if (!(best > 0.0) || !std::isfinite(best)) raise(EMG_ERR_INVALID, "coarsest operator is singular");
+    if (piv != k)
+      for (size_t s = 0; s < W; ++s) std::swap(M[k * W + s], M[piv * W + s]);
+    std::complex<double> ip = 1.0 / M[k * W + k];
+    for (size_t s = 0; s < W; ++s) M[k * W + s] *= ip;
+    for (size_t r = 0; r < n; ++r) {
+      if (r == k) continue;
+      std::complex<double> f = M[r * W + k];
+      if (f == 0.0) continue;
+      std::complex<double>* dst = &M[r * W];
+      const std::complex<double>* src = &M[k * W];
+      for (size_t s = 0; s < W; ++s) dst[s] -= f * src[s];
+    }
+  }
+  Ainv.assign(NF * NF, 0.0);
+  for (size_t r = 0; r < n; ++r)
+    for (size_t s = 0; s < n; ++s) Ainv[idx[r] * NF + idx[s]] = M[r * W + n + s];
+}
+
+// ---------------------------------------------------------------- setup
+template <typename T>
+void upload_material(emg_ctx& c, Level& L) {
+  std::vector<T> mu(L.ncell), rho(L.ncell), cp(L.ncell);
+  for (size_t k = 0; k < L.ncell; ++k) {
+    mu[k] = (T)L.mu_h[k];
+    rho[k] = (T)L.rho_h[k];
+    cp[k] = (T)(1.0 / (L.lam_h[k] + L.mu_h[k]));
+  }
+  L.mu.alloc(L.ncell * sizeof(T));
+  L.rho.alloc(L.ncell * sizeof(T));
+  L.cp.alloc(L.ncell * sizeof(T));
+  CK(cudaMemcpy(L.mu.p, mu.data(), L.ncell * sizeof(T), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(L.rho.p, rho.data(), L.ncell * sizeof(T), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(L.cp.p, cp.data(), L.ncell * sizeof(T), cudaMemcpyHostToDevice));
+}
+
+void coarsen_material(const emg_ctx& c, const Level& F, Level& C) {
+  const int d = c.dim;
+  C.lam_h.assign(C.ncell, 0.0);
+  C.mu_h.assign(C.ncell, 0.0);
+  C.rho_h.assign(C.ncell, 0.0);
+  const int nz = d == 3 ? C.n[2] : 1;
+  const double inv = 1.0 / (d == 3 ? 8.0 : 4.0);
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < C.n[1]; ++j)
+      for (int i = 0; i < C.n[0]; ++i) {
+        double sl = 0, sm = 0, sr = 0;
+        for (int c3 = 0; c3 < (d == 3 ? 2 : 1); ++c3)
+          for (int c2 = 0; c2 < 2; ++c2)
+            for (int c1 = 0; c1 < 2; ++c1) {
+              size_t f = ((size_t)(d == 3 ? 2 * k + c3 : 0) * F.n[1] + (2 * j + c2)) * F.n[0] + (2 * i + c1);
+              sl += F.lam_h[f];
+              sm += F.mu_h[f];
+              sr += F.rho_h[f];
+            }
+        size_t q = ((size_t)k * C.n[1] + j) * C.n[0] + i;
+        C.lam_h[q] = sl * inv;
+        C.mu_h[q] = sm * inv;
+        C.rho_h[q] = sr * inv;
+      }
+}
+
+template <typename T>
+void build(emg_ctx& c) {
+  const int d = c.dim;
+  for (int l = 0; l < c.L; ++l) {
+    Level& L = c.lv[l];
+    if (l > 0) coarsen_material(c, c.lv[l - 1], L);
+    upload_material<T>(c, L);
+    L.b.alloc((d + 1) * L.ncell * sizeof(cx<T>));
+    L.x.alloc((d + 1) * L.ncell * sizeof(cx<T>));
+    L.alt.alloc(d * L.ncell * sizeof(cx<T>));
+    CK(cudaMemset(L.b.p, 0, L.b.bytes));
+    CK(cudaMemset(L.x.p, 0, L.x.bytes));
+    CK(cudaMemset(L.alt.p, 0, L.alt.bytes));
+  }
+  // finest material in FP64 for the outer operator
+  Level& F = c.lv[0];
+  std::vector<double> cp(F.ncell);
+  for (size_t k = 0; k < F.ncell; ++k) cp[k] = 1.0 / (F.lam_h[k] + F.mu_h[k]);
+  c.mu64.alloc(F.ncell * 8);
+  c.rho64.alloc(F.ncell * 8);
+  c.cp64.alloc(F.ncell * 8);
+  CK(cudaMemcpy(c.mu64.p, F.mu_h.data(), F.ncell * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c.rho64.p, F.rho_h.data(), F.ncell * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c.cp64.p, cp.data(), F.ncell * 8, cudaMemcpyHostToDevice));
+  if (c.prm.coarse_solver == EMG_COARSE_DENSE) {
+    std::vector<std::complex<double>> A, Ainv;
+    std::vector<int> act;
+    assemble_dense(c, A, act);
+    invert_dense(A, act, Ainv);
+    const size_t NF = act.size();
+    std::vector<cx<T>> h(NF * NF);
+    for (size_t k = 0; k < NF * NF; ++k) h[k] = mkc<T>((T)Ainv[k].real(), (T)Ainv[k].imag());
+    c.cinv.alloc(NF * NF * sizeof(cx<T>));
+    CK(cudaMemcpy(c.cinv.p, h.data(), NF * NF * sizeof(cx<T>), cudaMemcpyHostToDevice));
+    c.cn = (int)NF;
+  }
+  CK(cudaDeviceSynchronize());
+}
+
+// ---------------------------------------------------------------- FP64 Krylov helpers
+void ensure_krylov(emg_ctx& c, int m) {
+  const size_t n = c.nvec();
+  const size_t cb = c.prec == 32 ? 8 : 16;
+  if (c.km < m) {
+    c.V.alloc((size_t)(m + 1) * n * 16);
+    c.Z.alloc((size_t)m * n * cb);
+    c.km = m;
+  }
+  if (!c.wk64.p) c.wk64.alloc(n * 16);
+  const int nblk = vec_blocks(c, n);
+  const size_t need = (size_t)nblk * (2 * kv::MAXV + 1) * 16 * sizeof(double);
+  if (c.part.bytes < need) c.part.alloc(need);
+  if (!c.red.p) c.red.alloc(4096 * sizeof(double));
+  if (!c.hred) CK(cudaMallocHost(&c.hred, 4096 * sizeof(double)));
+}
+
+template <int NV>
+void launch_mdot(emg_ctx& c, const cx<double>* V, size_t ldv, const cx<double>* w, size_t n, double* part, int nblk) {
+  kv::mdot<NV><<<nblk, kv::RT, 0, c.st>>>(V, ldv, w, n, part);
+  CKL();
+  LAUNCHED(c);
+}
+
+// h[i] = V_i^H w for i < cnt, and ||w||^2; one device->host transfer, one synchronisation.
+void mdots(emg_ctx& c, const cx<double>* V, size_t ldv, int cnt, const cx<double>* w, size_t n,
+           std::vector<std::complex<double>>& h, double& wn2) {
+  const int nblk = vec_blocks(c, n);
+  double* part = c.part.as<double>();
+  double* red = c.red.as<double>();
+  int off = 0, s = 0;
+  std::vector<std::pair<int, int>> chunks;  // (first vector, count)
+  do {
+    int nv = std::min(kv::MAXV, cnt - s);
+    switch (nv) {
+      case 0: launch_mdot<0>(c, V, ldv, w, n, part, nblk); break;
+      case 1: launch_mdot<1>(c, V + s * ldv, ldv, w, n, part, nblk); break;
+      case 2: launch_mdot<2>(c, V + s * ldv, ldv, w, n, part, nblk); break;
+      case 3: launch_mdot<3>(c, V + s * ldv, ldv, w, n, part, nblk); break;
+      case 4: launch_mdot<4>(c, V + s * ldv, ldv, w, n, part, nblk); break;
+      case 5: launch_mdot<5>(c, V + s * ldv, ldv, w, n, part, nblk); break;
+      case 6: launch_mdot<6>(c, V + s * ldv, ldv, w, n, part, nblk); break;
+      case 7: launch_mdot<7>(c, V + s * ldv, ldv, w, n, part, nblk); break;
+      default: launch_mdot<8>(c, V + s * ldv, ldv, w, n, part, nblk); break;
+    }
+    const int nr = 2 * nv + 1;
+    kv::reduce_parts<<<1, 128, 0, c.st>>>(part, nblk, nr, red + off);
+    CKL();
+  LAUNCHED(c);
+    chunks.push_back({s, nv});
+    off += nr;
+    s += nv;
+  } while (s < cnt);
+  CK(cudaMemcpyAsync(c.hred, red, off * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+  CK(cudaStreamSynchronize(c.st));
+  h.assign(cnt, 0.0);
+  off = 0;
+  for (auto& ch : chunks) {
+    for (int v = 0; v < ch.second; ++v) h[ch.first + v] = std::complex<double>(c.hred[off + 2 * v], c.hred[off + 2 * v + 1]);
+    wn2 = c.hred[off + 2 * ch.second];
+    off += 2 * ch.second + 1;
+  }
+  for (auto& z : h)
+    if (!std::isfinite(z.real()) || !std::isfinite(z.imag())) raise(EMG_ERR_NONFINITE, "non-finite Krylov inner product");
+  if (!std::isfinite(wn2)) raise(EMG_ERR_NONFINITE, "non-finite Krylov norm");
+}
+
+// w -= V h (cnt vectors); returns ||w||^2.
+double update(emg_ctx& c, cx<double>* w, const cx<double>* V, size_t ldv, const std::vector<std::complex<double>>& h, size_t n) {
+  const int nblk = vec_blocks(c, n);
+  kv::Coefs co;
+  const int cnt = (int)h.size();
+  for (int i = 0; i < cnt; ++i) co.c[i] = mkc(h[i].real(), h[i].imag());
+  kv::update_norm<<<nblk, kv::RT, 0, c.st>>>(w, V, ldv, cnt, co, n, c.part.as<double>());
+  CKL();
+  LAUNCHED(c);
+  kv::reduce_parts<<<1, 128, 0, c.st>>>(c.part.as<double>(), nblk, 1, c.red.as<double>());
+  CKL();
+  LAUNCHED(c);
+  CK(cudaMemcpyAsync(c.hred, c.red.p, sizeof(double), cudaMemcpyDeviceToHost, c.st));
+  CK(cudaStreamSynchronize(c.st));
+  if (!std::isfinite(c.hred[0])) raise(EMG_ERR_NONFINITE, "non-finite Krylov norm");
+  return c.hred[0];
+}
+
+double norm2(emg_ctx& c, const cx<double>* w, size_t n) {
+  std::vector<std::complex<double>> h;
+  double wn2 = 0;
+  mdots(c, nullptr, 0, 0, w, n, h, wn2);
+  return wn2;
+}
+
+// y = H x (FP64, unshifted) or r = b - H x on the finest level; x in FP64 or in FP32.
+void outer_apply(emg_ctx& c, const void* x, bool x32, const cx<double>* b, cx<double>* y, bool shifted) {
+  Grid<double> g = make_grid<double>(c, 0, shifted, c.mu64.p, c.rho64.p, c.cp64.p);
+  const double cw = 16.0;
+  ProfScope ps(c, EMG_K_APPLY64, 0, (double)c.lv[0].ncell * ((c.dim + 1) * ((x32 ? 8.0 : 16.0) + cw + (b ? cw : 0.0)) + 3 * 8.0));
+  launch_apply<double>(c, g, x, x32, b, y);
+}
+
+template <typename T>
+void precondition(emg_ctx& c, const cx<double>* v, cx<T>* z) {
+  const size_t n = c.nvec();
+  Level& F = c.lv[0];
+  const cx<T>* b;
+  if (std::is_same<T, double>::value) {
+    b = (const cx<T>*)v;
+  } else {
+    kv::cast<T, double><<<vec_blocks(c, n), 256, 0, c.st>>>(F.b.as<cx<T>>(), v, n);
+    CKL();
+  LAUNCHED(c);
+    b = F.b.as<cx<T>>();
+  }
+  vcycle<T>(c, 0, b, z, true);
+}
+
+template <typename T>
+emg_status solve_impl(emg_ctx& c, const cx<double>* b, cx<double>* x, double tol, int max_iter, int m, emg_stats* st) {
+  const size_t n = c.nvec();
+  ensure_krylov(c, m);
+  cx<double>* V = c.V.as<cx<double>>();
+  cx<T>* Z = c.Z.as<cx<T>>();
+  cx<double>* r = c.wk64.as<cx<double>>();
+  int hist = 0;
+  auto push_hist = [&](double v) {
+    if (st && st->history && hist < st->history_cap) st->history[hist] = v;
+    ++hist;
+  };
+  const double bnorm = std::sqrt(norm2(c, b, n));
+  if (!(bnorm > 0.0)) {
+    CK(cudaMemsetAsync(x, 0, n * 16, c.st));
+    CK(cudaStreamSynchronize(c.st));
+    if (st) { st->iterations = 0; st->restarts = 0; st->rel_residual = 0.0; st->history_len = 0; }
+    return EMG_OK;
+  }
+  outer_apply(c, x, false, b, r, false);
+  double beta = std::sqrt(norm2(c, r, n));
+  push_hist(beta / bnorm);
+  int its = 0, restarts = 0;
+  std::vector<std::complex<double>> Hh((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), h, h2;
+  while (beta / bnorm > tol && its < max_iter) {
+    kv::scale<<<vec_blocks(c, n), 256, 0, c.st>>>(V, r, 1.0 / beta, n);
+    CKL();
+  LAUNCHED(c);
+    std::fill(Hh.begin(), Hh.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      cx<double>* vj = V + (size_t)j * n;
+      cx<double>* w = V + (size_t)(j + 1) * n;
+      precondition<T>(c, vj, Z + (size_t)j * n);
+      outer_apply(c, Z + (size_t)j * n, std::is_same<T, float>::value, nullptr, w, false);
+      // classical Gram-Schmidt with one re-orthogonalisation when cancellation is detected
+      double wn2 = 0;
+      mdots(c, V, n, j + 1, w, n, h, wn2);
+      double nn2 = update(c, w, V, n, h, n);
+      if (nn2 < 0.25 * wn2) {
+        double dummy;
+        mdots(c, V, n, j + 1, w, n, h2, dummy);
+        nn2 = update(c, w, V, n, h2, n);
+        for (int i = 0; i <= j; ++i) h[i] += h2[i];
+      }
+      const double hn = std::sqrt(std::max(nn2, 0.0));
+      for (int i = 0; i <= j; ++i) Hh[(size_t)i * m + j] = h[i];
+      Hh[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0.0) {
+        kv::scale<<<vec_blocks(c, n), 256, 0, c.st>>>(w, w, 1.0 / hn, n);
+        CKL();
+  LAUNCHED(c);
+      }
+      for (int i = 0; i < j; ++i) {
+        std::complex<double> a = Hh[(size_t)i * m + j], bb = Hh[(size_t)(i + 1) * m + j];
+        Hh[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+        Hh[(size_t)(i + 1) * m + j] = -std::conj(sn[i]) * a + std::conj(cs[i]) * bb;
+      }
+      std::complex<double> a = Hh[(size_t)j * m + j], bb = Hh[(size_t)(j + 1) * m + j];
+      const double den = std::sqrt(std::norm(a) + std::norm(bb));
+      if (den == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
+      else { cs[j] = std::conj(a / den); sn[j] = std::conj(bb / den); }
+      Hh[(size_t)j * m + j] = cs[j] * a + sn[j] * bb;
+      Hh[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -std::conj(sn[j]) * g[j];
+      g[j] = cs[j] * g[j];
+      ++its;
+      k = j + 1;
+      push_hist(std::abs(g[j + 1]) / bnorm);
+      if (std::abs(g[j + 1]) / bnorm <= tol || its >= max_iter || hn == 0.0) break;
+    }
+    // y = R^{-1} g, x += Z y
+    std::vector<std::complex<double>> y(k);
+    for (int i = k - 1; i >= 0; --i) {
+      std::complex<double> s = g[i];
+      for (int q = i + 1; q < k; ++q) s -= Hh[(size_t)i * m + q] * y[q];
+      y[i] = s / Hh[(size_t)i * m + i];
+    }
+    kv::Coefs co;
+    for (int i = 0; i < k; ++i) co.c[i] = mkc(y[i].real(), y[i].imag());
+    kv::combine<T><<<vec_blocks(c, n), 256, 0, c.st>>>(x, Z, n, k, co, n);
+    CKL();
+  LAUNCHED(c);
+    outer_apply(c, x, false, b, r, false);
+    beta = std::sqrt(norm2(c, r, n));
+    ++restarts;
+  }
+  if (st) {
+    st->iterations = its;
+    st->restarts = restarts;
+    st->rel_residual = beta / bnorm;
+    st->history_len = std::min(hist, st->history ? st->history_cap : 0);
+  }
+  return beta / bnorm <= tol ? EMG_OK : EMG_NOT_CONVERGED;
+}
+
+void check_params(const emg_params* p) {
+  if (!p) raise(EMG_ERR_INVALID, "params is NULL");
+  if (p->dim != 2 && p->dim != 3) raise(EMG_ERR_INVALID, "dim must be 2 or 3");
+  if (p->levels < 1 || p->levels > EMG_MAX_LEVELS) raise(EMG_ERR_INVALID, "levels out of range");
+  const int div = 1 << (p->levels - 1);
+  for (int a = 0; a < p->dim; ++a) {
+    if (p->n[a] < 2) raise(EMG_ERR_INVALID, "each n must be >= 2");
+    if (p->n[a] % div) raise(EMG_ERR_INVALID, "n[" + std::to_string(a) + "] not divisible by 2^(levels-1)");
+    if (p->n[a] / div < 2) raise(EMG_ERR_INVALID, "coarsest grid must have >= 2 cells per axis");
+  }
+  if (!(p->h > 0) || !std::isfinite(p->h)) raise(EMG_ERR_INVALID, "h must be positive");
+  if (!std::isfinite(p->omega) || !std::isfinite(p->gamma) || !std::isfinite(p->alpha) || !std::isfinite(p->beta))
+    raise(EMG_ERR_INVALID, "non-finite omega/gamma/alpha/beta");
+  if (p->abl_cells < 0) raise(EMG_ERR_INVALID, "abl_cells must be >= 0");
+  if (p->nu_pre < 0 || p->nu_post < 0) raise(EMG_ERR_INVALID, "negative smoothing count");
+  if (p->cycle_precision != 32 && p->cycle_precision != 64) raise(EMG_ERR_INVALID, "cycle_precision must be 32 or 64");
+  if (p->coarse_solver != EMG_COARSE_DENSE && p->coarse_solver != EMG_COARSE_SMOOTH)
+    raise(EMG_ERR_INVALID, "unknown coarse_solver");
+  if (p->coarse_solver == EMG_COARSE_SMOOTH && p->coarse_sweeps < 1 && p->levels > 0)
+    raise(EMG_ERR_INVALID, "coarse_sweeps must be >= 1");
+  size_t nc = 1;
+  for (int a = 0; a < p->dim; ++a) nc *= (size_t)(p->n[a] / div);
+  if (p->coarse_solver == EMG_COARSE_DENSE && nc * (p->dim + 1) > 4096)
+    raise(EMG_ERR_INVALID, "dense coarsest solve limited to 4096 unknowns");
+}
+
+emg_ctx* checked(emg_handle h) {
+  if (!h) raise(EMG_ERR_INVALID, "NULL handle");
+  return h;
+}
+
+void check_level(emg_ctx& c, int level, bool need_coarser) {
+  if (level < 0 || level >= c.L || (need_coarser && level >= c.L - 1)) raise(EMG_ERR_INVALID, "level out of range");
+}
+
+void check_ptr(const void* p, const char* what) {
+  if (!p) raise(EMG_ERR_INVALID, std::string(what) + " is NULL");
+  if (reinterpret_cast<uintptr_t>(p) % 16) raise(EMG_ERR_INVALID, std::string(what) + " is not 16-byte aligned");
+}
+
+}  // namespace
+
+#define ABI_TRY try {
+#define ABI_CATCH                                                   \
+  }                                                                 \
+  catch (const EmgError& e) { g_err = e.msg; return e.s; }          \
+  catch (const std::bad_alloc&) { g_err = "host allocation failed"; return EMG_ERR_NOMEM; } \
+  catch (const std::exception& e) { g_err = e.what(); return EMG_ERR_INVALID; }
+
+extern "C" {
+
+const char* emg_last_error(void) { return g_err.c_str(); }
+
+emg_status emg_create(const emg_params* params, const double* lam, const double* mu, const double* rho, int on_device,
+                      void* cuda_stream, emg_handle* out) {
+  ABI_TRY
+  if (!out) raise(EMG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  check_params(params);
+  if (!lam || !mu || !rho) raise(EMG_ERR_INVALID, "material pointer is NULL");
+  std::unique_ptr<emg_ctx> c(new emg_ctx());
+  c->prm = *params;
+  c->dim = params->dim;
+  c->L = params->levels;
+  c->prec = params->cycle_precision;
+  c->st = (cudaStream_t)cuda_stream;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
+  c->lv.resize(c->L);
+  for (int l = 0; l < c->L; ++l) {
+    Level& L = c->lv[l];
+    L.ncell = 1;
+    for (int a = 0; a < 3; ++a) {
+      L.n[a] = a < c->dim ? params->n[a] >> l : 1;
+      L.ncell *= (size_t)L.n[a];
+    }
+    L.h = params->h * (double)(1 << l);
+    const double w = params->damping[l];
+    L.w = w > 0.0 ? w : default_damping(c->L);
+  }
+  Level& F = c->lv[0];
+  F.lam_h.resize(F.ncell);
+  F.mu_h.resize(F.ncell);
+  F.rho_h.resize(F.ncell);
+  if (on_device) {
+    CK(cudaMemcpy(F.lam_h.data(), lam, F.ncell * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(F.mu_h.data(), mu, F.ncell * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(F.rho_h.data(), rho, F.ncell * 8, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(F.lam_h.data(), lam, F.ncell * 8);
+    std::memcpy(F.mu_h.data(), mu, F.ncell * 8);
+    std::memcpy(F.rho_h.data(), rho, F.ncell * 8);
+  }
+  for (size_t k = 0; k < F.ncell; ++k) {
+    if (!std::isfinite(F.lam_h[k]) || !std::isfinite(F.mu_h[k]) || !std::isfinite(F.rho_h[k]) || !(F.mu_h[k] > 0) ||
+        !(F.rho_h[k] > 0) || !(F.lam_h[k] + F.mu_h[k] > 0))
+      raise(EMG_ERR_INVALID, "material must be finite with mu > 0, rho > 0, lambda + mu > 0 (cell " + std::to_string(k) + ")");
+  }
+  if (c->prec == 32) build<float>(*c);
+  else build<double>(*c);
+  *out = c.release();
+  ABI_CATCH
+  return EMG_OK;
+}
+
+emg_status emg_destroy(emg_handle h) {
+  ABI_TRY
+  if (h) {
+    if (h->st) cudaStreamSynchronize(h->st);
+    else cudaDeviceSynchronize();
+    delete h;
+  }
+  ABI_CATCH
+  return EMG_OK;
+}
+
+emg_status emg_level_info(emg_handle h, int level, int32_t n[3], double* cell_size) {
+  ABI_TRY
+  emg_ctx& c = *checked(h);
+  check_level(c, level, false);
+  for (int a = 0; a < 3; ++a) n[a] = c.lv[level].n[a];
+  if (cell_size) *cell_size = c.lv[level].h;
+  ABI_CATCH
+  return EMG_OK;
+}
+
+emg_status emg_apply(emg_handle h, int shifted, const void* x, void* y) {
+  ABI_TRY
+  emg_ctx& c = *checked(h);
+  check_ptr(x, "x");
+  check_ptr(y, "y");
+  outer_apply(c, x, false, nullptr, (cx<double>*)y, shifted != 0);
+  ABI_CATCH
+  return EMG_OK;
+}
+
+emg_status emg_vcycle(emg_handle h, const void* b, void* x, int zero_guess) {
+  ABI_TRY
+  emg_ctx& c = *checked(h);
+  check_ptr(b, "b");
+  check_ptr(x, "x");
+  if (c.prec == 32) vcycle<float>(c, 0, (const cx<float>*)b, (cx<float>*)x, zero_guess != 0);
+  else vcycle<double>(c, 0, (const cx<double>*)b, (cx<double>*)x, zero_guess != 0);
+  ABI_CATCH
+  return EMG_OK;
+}
+
+emg_status emg_smooth(emg_handle h, int level, const void* b, void* x, int sweeps) {
+  ABI_TRY
+  emg_ctx& c = *checked(h);
+  check_level(c, level, false);
+  check_ptr(b, "b");
+  check_ptr(x, "x");
+  if (sweeps < 0) raise(EMG_ERR_INVALID, "sweeps < 0");
+  const double w = c.lv[level].w;
+  if (c.prec == 32) smooth<float>(c, level, (const cx<float>*)b, (cx<float>*)x, sweeps, w, false);
+  else smooth<double>(c, level, (const cx<double>*)b, (cx<double>*)x, sweeps, w, false);
+  ABI_CATCH
+  return EMG_OK;
+}
+
+emg_status emg_residual_restrict(emg_handle h, int level, const void* b, const void* x, void* bc) {
+  ABI_TRY
+  emg_ctx& c = *checked(h);
+  check_level(c, level, true);
+  check_ptr(b, "b");
+  check_ptr(x, "x");
+  check_ptr(bc, "b_coarse");
+  if (c.prec == 32) residual_restrict<float>(c, level, (const cx<float>*)b, (const cx<float>*)x, (cx<float>*)bc, false);
+  else residual_restrict<double>(c, level, (const cx<double>*)b, (const cx<double>*)x, (cx<double>*)bc, false);
+  ABI_CATCH
+  return EMG_OK;
+}
+
+emg_status emg_prolong_correct(emg_handle h, int level, const void* e, void* x) {
+  ABI_TRY
+  emg_ctx& c = *checked(h);
+  check_level(c, level, true);
+  check_ptr(e, "e_coarse");
+  check_ptr(x, "x");
+  if (c.prec == 32) prolong_correct<float>(c, level, (const cx<float>*)e, (cx<float>*)x);
+  else prolong_correct<double>(c, level, (const cx<double>*)e, (cx<double>*)x);
+  ABI_CATCH
+  return EMG_OK;
+}
+
+emg_status emg_coarse_solve(emg_handle h, const void* b, void* x) {
+  ABI_TRY
+  emg_ctx& c = *checked(h);
+  check_ptr(b, "b");
+  check_ptr(x, "x");
+  if (c.prec == 32) coarse_solve<float>(c, (const cx<float>*)b, (cx<float>*)x);
+  else coarse_solve<double>(c, (const cx<double>*)b, (cx<double>*)x);
+  ABI_CATCH
+  return EMG_OK;
+}
+
+emg_status emg_solve(emg_handle h, const void* b, void* x, double tol, int max_iter, int restart, emg_stats* stats) {
+  ABI_TRY
+  emg_ctx& c = *checked(h);
+  check_ptr(b, "b");
+  check_ptr(x, "x");
+  if (restart < 1 || restart > 64) raise(EMG_ERR_INVALID, "restart must be in 1..64");
+  if (max_iter < 0) raise(EMG_ERR_INVALID, "max_iter < 0");
+  if (!(tol >= 0.0)) raise(EMG_ERR_INVALID, "tol must be >= 0");
+  if (c.prec == 32) return solve_impl<float>(c, (const cx<double>*)b, (cx<double>*)x, tol, max_iter, restart, stats);
+  return solve_impl<double>(c, (const cx<double>*)b, (cx<double>*)x, tol, max_iter, restart, stats);
+  ABI_CATCH
+}
+
+emg_status emg_solve_host(emg_handle h, const double* b_host, double* x_host, double tol, int max_iter, int restart,
+                          emg_stats* stats) {
+  ABI_TRY
+  emg_ctx& c = *checked(h);
+  if (!b_host || !x_host) raise(EMG_ERR_INVALID, "host vector is NULL");
+  const size_t bytes = c.nvec() * 16;
+  if (c.hb_bytes < bytes) {
+    c.hb.alloc(bytes);
+    c.hx.alloc(bytes);
+    c.hb_bytes = bytes;
+  }
+  CK(cudaMemcpyAsync(c.hb.p, b_host, bytes, cudaMemcpyHostToDevice, c.st));
+  CK(cudaMemcpyAsync(c.hx.p, x_host, bytes, cudaMemcpyHostToDevice, c.st));
+  emg_status s = emg_solve(h, c.hb.p, c.hx.p, tol, max_iter, restart, stats);
+  if (s != EMG_OK && s != EMG_NOT_CONVERGED) return s;
+  CK(cudaMemcpyAsync(x_host, c.hx.p, bytes, cudaMemcpyDeviceToHost, c.st));
+  CK(cudaStreamSynchronize(c.st));
+  return s;
+  ABI_CATCH
+}
+
+emg_status emg_profile(emg_handle h, int enable) {
+  ABI_TRY
+  emg_ctx& c = *checked(h);
+  prof_flush(c);
+  c.prof = enable != 0;
+  ABI_CATCH
+  return EMG_OK;
+}
+
+emg_status emg_profile_read(emg_handle h, int cls, double* total_ms, int64_t* launches, double* bytes) {
+  ABI_TRY
+  emg_ctx& c = *checked(h);
+  if (cls < 0 || cls > EMG_K_ALL) raise(EMG_ERR_INVALID, "kernel class out of range");
+  if (cls == EMG_K_ALL) {
+    if (total_ms) *total_ms = 0.0;
+    if (launches) *launches = c.launches;
+    if (bytes) *bytes = 0.0;
+    c.launches = 0;
+    return EMG_OK;
+  }
+  prof_flush(c);
+  if (total_ms) *total_ms = c.pms[cls];
+  if (launches) *launches = c.pn[cls];
+  if (bytes) *bytes = c.pbytes[cls];
+  c.pms[cls] = 0;
+  c.pn[cls] = 0;
+  c.pbytes[cls] = 0;
+  ABI_CATCH
+  return EMG_OK;
+}
+
+}  // extern "C"

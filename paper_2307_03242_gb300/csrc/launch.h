@@ -1,0 +1,26 @@
+// Launchers of the stencil kernels; each dimension lives in its own translation unit
+// (launch2d.cu, launch3d.cu) so that the library builds in parallel.
+#pragma once
+#include "emg_types.cuh"
+
+template <typename T, typename TI>
+void launch_apply2(const Grid<T>& g, const cx<TI>* x, const cx<T>* b, cx<T>* y, cudaStream_t st);
+template <typename T>
+void launch_vanka2(const Grid<T>& g, const cx<T>* b, const cx<T>* uin, cx<T>* uout, cx<T>* p, int colour, T w,
+                   int zero_in, cudaStream_t st);
+template <typename T>
+void launch_restrict2(const Grid<T>& g, const cx<T>* b, const cx<T>* x, cx<T>* bc, const int nc[3], int zero_x,
+                      cudaStream_t st);
+template <typename T>
+void launch_prolong2(const cx<T>* e, cx<T>* x, const int n[3], const int nc[3], cudaStream_t st);
+
+template <typename T, typename TI>
+void launch_apply3(const Grid<T>& g, const cx<TI>* x, const cx<T>* b, cx<T>* y, cudaStream_t st);
+template <typename T>
+void launch_vanka3(const Grid<T>& g, const cx<T>* b, const cx<T>* uin, cx<T>* uout, cx<T>* p, int colour, T w,
+                   int zero_in, cudaStream_t st);
+template <typename T>
+void launch_restrict3(const Grid<T>& g, const cx<T>* b, const cx<T>* x, cx<T>* bc, const int nc[3], int zero_x,
+                      cudaStream_t st);
+template <typename T>
+void launch_prolong3(const cx<T>* e, cx<T>* x, const int n[3], const int nc[3], cudaStream_t st);

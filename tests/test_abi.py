@@ -1,0 +1,53 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, and exports every function that
+include/emg.h declares; argument validation that needs no GPU."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "emg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(emg_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_entry_point():
+    from paper_2307_03242_gb300.build import build_library
+    lib = build_library()
+    import ctypes
+    so = ctypes.CDLL(lib)
+    names = _declared()
+    assert "emg_solve" in names and "emg_create" in names
+    for n in names:
+        assert hasattr(so, n), n
+    from paper_2307_03242_gb300 import emg
+    assert sorted(emg.EXPORTED) == names
+
+
+def test_params_struct_layout_matches_header():
+    """ctypes mirror of emg_params / emg_stats has the C layout (field offsets)."""
+    import ctypes
+    from paper_2307_03242_gb300 import emg
+    P = emg._Params
+    assert P.n.offset == 4 and P.h.offset == 16
+    assert P.damping.offset % 8 == 0 and ctypes.sizeof(P) % 8 == 0
+    S = emg._Stats
+    assert S.history.offset == 16
+
+
+def test_invalid_arguments_are_rejected_without_a_gpu():
+    import numpy as np
+    from paper_2307_03242_gb300 import emg
+    p = emg.Params(n=(30, 16), levels=3)  # 30 not divisible by 4
+    c = p.to_c()
+    import ctypes
+    h = ctypes.c_void_p()
+    lam = np.ones(30 * 16)
+    st = emg.LIB.emg_create(ctypes.byref(c), lam.ctypes.data, lam.ctypes.data, lam.ctypes.data, 0, None,
+                            ctypes.byref(h))
+    assert st == 1 and b"divisible" in emg.LIB.emg_last_error()
+    assert emg.LIB.emg_solve(None, None, None, 1e-6, 10, 20, None) == 1
+    assert emg.LIB.emg_destroy(None) == 0

@@ -1,0 +1,206 @@
+"""GPU vs oracle parity for every row of the cycle, in FP64 and FP32, 2D and 3D.
+
+Sizes span several thread tiles with ragged tails; the oracle runs in seconds on them. Tolerances:
+FP64 kernels 1e-12 (max-norm relative), FP64 cycle 1e-11; FP32 kernels 2e-6, FP32 cycle 1e-5
+(2-norm relative), i.e. a few FP32 roundings amplified by the stencil's cancellation."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.smoother import cell_colour
+from workloads import small_heterogeneous
+from _gpu_helpers import (oracle_problem, oracle_hierarchy, gpu_solver, random_field, to_gpu, to_np, rel, rel_max,
+                          TOL, TOL_CYCLE)
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "2d": dict(n=(72, 40), levels=3, abl_cells=5),
+    "2d_odd_coarse": dict(n=(36, 20), levels=3, abl_cells=3),
+    "3d": dict(n=(40, 12, 8), levels=2, abl_cells=2),
+}
+
+
+def _w(case, seed=1):
+    c = CASES[case]
+    return small_heterogeneous(c["n"], seed=seed, levels=c["levels"], abl_cells=c["abl_cells"], sigma_cells=2.0)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("shifted", [False, True])
+def test_apply_fp64_matches_oracle(case, shifted):
+    w = _w(case)
+    pb = oracle_problem(w)
+    s = gpu_solver(w, 32)
+    x = random_field(pb, 11)
+    y_ref = oracle.apply(pb, x, shift=w.alpha if shifted else 0.0)
+    import torch
+    xt = to_gpu(x, 64)
+    yt = torch.empty_like(xt)
+    s.apply(xt, yt, shifted=shifted)
+    assert rel_max(to_np(yt), y_ref) < TOL[64]
+    s.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("sweeps", [1, 2])
+def test_red_black_vanka_matches_oracle(case, prec, sweeps):
+    w = _w(case)
+    pb = oracle_problem(w)
+    hier = oracle_hierarchy(w, pb)
+    s = gpu_solver(w, prec)
+    b = random_field(pb, 21)
+    x = random_field(pb, 22)
+    ref = x.ravel()
+    for _ in range(sweeps):
+        ref = oracle.red_black_sweep(hier.H[0], hier.V[0], hier.idx[0], hier.colour[0], b.ravel(), ref, hier.w[0])
+    xt = to_gpu(x, prec)
+    s.smooth(0, to_gpu(b, prec), xt, sweeps)
+    tol = TOL[prec] * (10 if prec == 64 else 5)
+    assert rel_max(to_np(xt), ref) < tol
+    s.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", [64, 32])
+def test_residual_restriction_matches_oracle(case, prec):
+    w = _w(case)
+    pb = oracle_problem(w)
+    hier = oracle_hierarchy(w, pb)
+    s = gpu_solver(w, prec)
+    b = random_field(pb, 31)
+    x = random_field(pb, 32)
+    ref = hier.R[0] @ (b.ravel() - hier.H[0] @ x.ravel())
+    import torch
+    bc = torch.zeros(s.vec_shape(1), dtype=s.cdtype, device="cuda")
+    s.residual_restrict(0, to_gpu(b, prec), to_gpu(x, prec), bc)
+    assert rel_max(to_np(bc), ref) < TOL[prec] * 10
+    s.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", [64, 32])
+def test_prolongation_correction_matches_oracle(case, prec):
+    w = _w(case)
+    pb = oracle_problem(w)
+    hier = oracle_hierarchy(w, pb)
+    s = gpu_solver(w, prec)
+    e = random_field(hier.pbs[1], 41)
+    x = random_field(pb, 42)
+    ref = x.ravel() + hier.P[0] @ e.ravel()
+    xt = to_gpu(x, prec)
+    s.prolong_correct(0, to_gpu(e, prec), xt)
+    assert rel_max(to_np(xt), ref) < TOL[prec]
+    s.close()
+
+
+@pytest.mark.parametrize("case", ["2d", "3d"])
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("coarse", ["dense", "smooth"])
+def test_coarsest_solve_matches_oracle(case, prec, coarse):
+    w = _w(case)
+    w.coarse, w.coarse_sweeps, w.coarse_damping = coarse, 3, 0.8
+    pb = oracle_problem(w)
+    hier = oracle_hierarchy(w, pb)
+    s = gpu_solver(w, prec)
+    last = w.levels - 1
+    b = random_field(hier.pbs[last], 51)
+    ref = hier.coarse_solve(b.ravel())
+    import torch
+    xt = torch.zeros(s.vec_shape(last), dtype=s.cdtype, device="cuda")
+    s.coarse_solve(to_gpu(b, prec), xt)
+    assert rel(to_np(xt), ref) < TOL_CYCLE[prec] * 10
+    s.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("coarse", ["dense", "smooth"])
+def test_vcycle_matches_oracle(case, prec, coarse):
+    w = _w(case)
+    w.coarse, w.coarse_sweeps, w.coarse_damping = coarse, 4, 0.8
+    pb = oracle_problem(w)
+    hier = oracle_hierarchy(w, pb)
+    s = gpu_solver(w, prec)
+    b = random_field(pb, 61)
+    ref = oracle.vcycle(hier, b.ravel())
+    import torch
+    xt = torch.zeros(s.vec_shape(0), dtype=s.cdtype, device="cuda")
+    xt.fill_(3.0)  # ignored with a zero initial guess
+    s.vcycle(to_gpu(b, prec), xt, zero_guess=True)
+    got = to_np(xt).ravel() * oracle.active_mask(pb)
+    assert rel(got, ref) < TOL_CYCLE[prec]
+    # non-zero initial guess path
+    x0 = random_field(pb, 62)
+    ref2 = oracle.vcycle(hier, b.ravel(), x0.ravel())
+    xt2 = to_gpu(x0, prec)
+    s.vcycle(to_gpu(b, prec), xt2, zero_guess=False)
+    assert rel(to_np(xt2), ref2) < TOL_CYCLE[prec]
+    s.close()
+
+
+@pytest.mark.parametrize("case", ["2d", "3d"])
+def test_vcycle_is_deterministic(case):
+    w = _w(case)
+    pb = oracle_problem(w)
+    s = gpu_solver(w, 32)
+    import torch
+    bt = to_gpu(random_field(pb, 71), 32)
+    x1 = torch.zeros_like(bt)
+    x2 = torch.zeros_like(bt)
+    s.vcycle(bt, x1)
+    s.vcycle(bt, x2)
+    torch.cuda.synchronize()
+    assert torch.equal(x1, x2)
+    s.close()
+
+
+@pytest.mark.parametrize("case", ["2d", "3d"])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_fgmres_solve_matches_oracle(case, prec):
+    """Outer FGMRES(20) in FP64 around the V-cycle: same iteration count as the oracle (FP64
+    cycle: +-1; FP32 cycle: within 10%), true FP64 residual <= tol, solution within 1e-5 of the
+    oracle's FP64 solution solved to 1e-10."""
+    w = _w(case)
+    pb = oracle_problem(w)
+    hier = oracle_hierarchy(w, pb)
+    H = oracle.assemble(pb, 0.0)
+    b = w.rhs.ravel() * oracle.active_mask(pb)
+    x_ref, its_ref, _ = oracle.fgmres(lambda v: H @ v, lambda v: oracle.vcycle(hier, v), b, tol=1e-6, restart=20,
+                                      max_iter=500)
+    x_tight, _, _ = oracle.fgmres(lambda v: H @ v, lambda v: oracle.vcycle(hier, v), b, tol=1e-10, restart=20,
+                                  max_iter=500)
+    s = gpu_solver(w, prec)
+    import torch
+    bt = to_gpu(b.reshape(oracle.dof_shape(pb)), 64)
+    xt = torch.zeros_like(bt)
+    st = s.solve(bt, xt, tol=1e-6, max_iter=500, restart=20)
+    x = to_np(xt).ravel()
+    assert st["converged"]
+    true_res = np.linalg.norm(b - H @ x) / np.linalg.norm(b)
+    assert true_res <= 1e-6 and abs(true_res - st["rel_residual"]) < 1e-9
+    if prec == 64:
+        assert abs(st["iterations"] - its_ref) <= 1
+    else:
+        assert abs(st["iterations"] - its_ref) <= max(1, int(0.1 * its_ref))
+    xt2 = torch.zeros_like(bt)
+    st2 = s.solve(bt, xt2, tol=1e-10, max_iter=800, restart=20)
+    assert rel(to_np(xt2), x_tight) < 1e-5 * (1 if prec == 64 else 10) and st2["converged"]
+    s.close()
+
+
+def test_solve_host_buffers_match_device_solve():
+    w = _w("2d")
+    pb = oracle_problem(w)
+    b = (w.rhs.ravel() * oracle.active_mask(pb)).astype(np.complex128)
+    s = gpu_solver(w, 32)
+    import torch
+    bt = to_gpu(b.reshape(oracle.dof_shape(pb)), 64)
+    xt = torch.zeros_like(bt)
+    st = s.solve(bt, xt, tol=1e-6)
+    xh = np.zeros_like(b)
+    sh = s.solve_host(b, xh, tol=1e-6)
+    assert st["iterations"] == sh["iterations"]
+    np.testing.assert_array_equal(xh, to_np(xt).ravel())
+    s.close()

@@ -153,3 +153,28 @@ def test_vcycle_is_linear_and_deterministic():
     assert np.linalg.norm(lhs - rhs) <= 1e-12 * np.linalg.norm(lhs)
     assert np.array_equal(oracle.vcycle(hier, b1), oracle.vcycle(hier, b1))
     assert np.all(lhs[~act] == 0)
+
+
+@pytest.mark.parametrize("n", [(24, 20), (12, 10, 8)])
+def test_windowed_operator_matches_full_operator_away_from_cuts(n):
+    """oracle.window: rows >= 3 cells from a cut edge equal the full operator's rows (incl. ABL)."""
+    w = small_heterogeneous(n, abl_cells=3)
+    pb = _problem(w)
+    rng = np.random.default_rng(4)
+    shape = oracle.dof_shape(pb)
+    x = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    y = oracle.apply(pb, x, shift=0.3)
+    d = pb.dim
+    lo = tuple(0 if a == 0 else 2 for a in range(d))
+    hi = tuple(n[a] - 1 if a == 0 else n[a] for a in range(d))
+    wp = oracle.window(pb, lo, hi)
+    sl = tuple(slice(lo[a], hi[a]) for a in reversed(range(d)))
+    yw = oracle.apply(wp, x[(slice(None),) + sl], shift=0.3)
+    inner = []
+    for a in reversed(range(d)):
+        s0 = 0 if lo[a] == 0 else 3
+        s1 = (hi[a] - lo[a]) - (0 if hi[a] == n[a] else 3)
+        inner.append(slice(s0, s1))
+    full_inner = tuple(slice(lo[a] + inner[d - 1 - a].start, lo[a] + inner[d - 1 - a].stop)
+                       for a in reversed(range(d)))
+    np.testing.assert_allclose(yw[(slice(None),) + tuple(inner)], y[(slice(None),) + full_inner], atol=1e-12)

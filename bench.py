@@ -44,12 +44,23 @@ def parse():
     ap.add_argument("--restart", type=int, default=20)
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed plain-FP64 solves (after 1 warm-up)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--levels", type=int, default=None)
+    ap.add_argument("--alpha", type=float, default=None)
+    ap.add_argument("--damping", type=float, default=None)
+    ap.add_argument("--cycle", default=None, choices=["V", "W"])
+    ap.add_argument("--coarse-sweeps", type=int, default=None)
     return ap.parse_args()
 
 
-def workload(name):
+def workload(name, args=None):
     from workloads import config_c1_homogeneous, config_c2_random2d, config_c3_layered3d
-    return {"c1": config_c1_homogeneous, "c2": config_c2_random2d, "c3": config_c3_layered3d}[name]()
+    w = {"c1": config_c1_homogeneous, "c2": config_c2_random2d, "c3": config_c3_layered3d}[name]()
+    if args is not None:
+        for k in ("levels", "alpha", "damping", "cycle", "coarse_sweeps"):
+            v = getattr(args, k, None)
+            if v is not None:
+                setattr(w, k, v)
+    return w
 
 
 def load_peaks():
@@ -145,7 +156,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = workload(args.config)
+    w = workload(args.config, args)
     iters = REF_ITERS[args.config]
     vals = []
     for s in range(args.warmup + args.steps):
@@ -163,8 +174,8 @@ def run_reference(args):
 
 
 def config_json(w, args):
-    return {"workload": w.name, "grid": "x".join(map(str, w.n)), "levels": w.levels, "cycle": "V(%d,%d)" % (
-        w.nu_pre, w.nu_post), "alpha": w.alpha, "damping": w.damping, "beta": round(w.beta, 6),
+    return {"workload": w.name, "grid": "x".join(map(str, w.n)), "levels": w.levels, "cycle": "%s(%d,%d)" % (
+        w.cycle, w.nu_pre, w.nu_post), "coarse_sweeps": w.coarse_sweeps, "alpha": w.alpha, "damping": w.damping, "beta": round(w.beta, 6),
         "krylov": "FGMRES(%d)" % args.restart, "tol": w.tol, "coarsest": w.coarse,
         "l2": "inputs larger than L2 (vectors %d MB)" % int(16 * (w.dim + 1) * np.prod(w.n) / 2 ** 20),
         "parallelism": "replicas" if args.gpus > 1 else "single"}
@@ -184,7 +195,7 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     from paper_2307_03242_gb300 import emg
-    w = workload(args.config)
+    w = workload(args.config, args)
     shape = (w.dim + 1,) + tuple(w.n[::-1])
     nvec = int(np.prod(shape))
     dev = torch.device("cuda", local)
@@ -218,6 +229,8 @@ def main():
         barrier()
     ms = e0.elapsed_time(e1) / args.steps
     prof = s32.profile_read(emg.K_SMOOTH)
+    breakdown = {name: s32.profile_read(cls) for name, cls in (("restrict", emg.K_RESTRICT), ("prolong", emg.K_PROLONG),
+                                                               ("apply64", emg.K_APPLY64), ("krylov", emg.K_KRYLOV))}
     s32.profile(False)
     launches = s32.profile_read(emg.K_ALL)["launches"]
     t32 = ms / 1e3
@@ -291,6 +304,8 @@ def main():
                         "frac": achieved / peak if achieved else None, "traffic": None,
                         "launches": prof["launches"], "avg_launch_ms": prof["ms"] / max(prof["launches"], 1),
                         "bytes_per_launch": prof["bytes"] / max(prof["launches"], 1)},
+           "fine_level_ms_per_solve": dict({"smooth": prof["ms"] / args.steps},
+                                           **{k: v["ms"] / args.steps for k, v in breakdown.items()}),
            "e2e": {"value": te2e, "unit": "s", "h2d_bytes_per_step": 2 * nvec * 16, "d2h_bytes_per_step": nvec * 16},
            "gpu_launches": int(launches)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

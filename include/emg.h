@@ -55,6 +55,7 @@ typedef enum {
 } emg_status;
 
 enum { EMG_COARSE_DENSE = 0, EMG_COARSE_SMOOTH = 1 };
+enum { EMG_CYCLE_V = 0, EMG_CYCLE_W = 1 };
 
 /* Solver description. All lengths in the same unit as h. */
 typedef struct {
@@ -74,6 +75,9 @@ typedef struct {
   int32_t coarse_sweeps;    /* red-black sweeps on the coarsest level for EMG_COARSE_SMOOTH */
   double coarse_damping;    /* Vanka damping on the coarsest level for EMG_COARSE_SMOOTH */
   int32_t cycle_precision;  /* 32: FP32 cycle with FP64 outer solve; 64: everything in FP64 */
+  int32_t cycle_type;       /* EMG_CYCLE_V (one recursive call, Alg. 1) or EMG_CYCLE_W (two calls,
+                               the second from the first one's result; Sec. 2.2, the paper's 2D
+                               choice); the coarsest level is solved once per visit */
 } emg_params;
 
 typedef struct {
@@ -106,8 +110,8 @@ const char* emg_last_error(void);
  * sign of Eq. 4.4; H_s adds alpha to the attenuation (Eq. 2.9). x, y: FP64 vectors. */
 emg_status emg_apply(emg_handle h, int shifted, const void* x, void* y);
 
-/* x <- one V(nu_pre, nu_post)-cycle for H_s x = b on the finest level (Alg. 1 applied
- * recursively with one recursive call). zero_guess = 1 ignores the input x. b, x: cycle vectors. */
+/* x <- one V(nu_pre, nu_post)-cycle (or W-cycle, per cycle_type) for H_s x = b on the finest
+ * level (Alg. 1 applied recursively). zero_guess = 1 ignores the input x. b, x: cycle vectors. */
 emg_status emg_vcycle(emg_handle h, const void* b, void* x, int zero_guess);
 
 /* Solve H x = b (unshifted, FP64) by right-preconditioned restarted FGMRES(restart) with one

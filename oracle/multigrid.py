@@ -1,7 +1,7 @@
 """Multigrid V-cycle on the shifted operator (oracle; test infrastructure only).
 
-Algorithm 1 (two-grid cycle) applied recursively with one recursive call (the
-V-cycle, Section 2.2): nu_1 pre-relaxations, residual restriction
+Algorithm 1 (two-grid cycle) applied recursively (Section 2.2): one recursive call gives the
+V-cycle, two recursive calls (the second starting from the first one's result) the W-cycle: nu_1 pre-relaxations, residual restriction
 r_2h = R(q - A_h u), coarse problem, correction u += P e_2h, nu_2
 post-relaxations. The coarse operators are re-discretisations of the shifted
 operator (Remark 2.1 and Section 3.2: the same stencil on the 2h grid, with the
@@ -28,8 +28,9 @@ DEFAULT_DAMPING = {1: 0.55, 2: 0.55, 3: 0.35, 4: 0.25, 5: 0.2, 6: 0.2, 7: 0.2, 8
 class Hierarchy:
     def __init__(self, pb: Problem, levels: int, alpha: float, damping=None, nu_pre: int = 2,
                  nu_post: int = 2, coarse: str = "dense", coarse_sweeps: int = 0,
-                 coarse_damping: float = 1.0):
+                 coarse_damping: float = 1.0, cycle: str = "V"):
         self.levels = levels
+        self.gamma_cycle = {"V": 1, "W": 2}[cycle]
         self.alpha = alpha
         self.nu_pre, self.nu_post = nu_pre, nu_post
         self.coarse, self.coarse_sweeps, self.coarse_damping = coarse, coarse_sweeps, coarse_damping
@@ -67,7 +68,8 @@ class Hierarchy:
 
 
 def vcycle(hier: Hierarchy, b, x=None, level: int = 0):
-    """One V(nu_1, nu_2) cycle for H_s x = b on `level`; x=None means a zero initial guess."""
+    """One V(nu_1, nu_2) cycle (or W-cycle, per the hierarchy) for H_s x = b on `level`;
+    x=None means a zero initial guess."""
     b = np.asarray(b, dtype=np.complex128).ravel()
     if level == hier.levels - 1:
         return hier.coarse_solve(b)
@@ -77,6 +79,9 @@ def vcycle(hier: Hierarchy, b, x=None, level: int = 0):
     r = b - H @ x
     bc = hier.R[level] @ r
     ec = vcycle(hier, bc, None, level + 1)
+    for _ in range(hier.gamma_cycle - 1):
+        if level + 1 < hier.levels - 1:
+            ec = vcycle(hier, bc, ec, level + 1)
     x = x + hier.P[level] @ ec
     x = hier.smooth(level, b, x, hier.nu_post, hier.w[level])
     return x

@@ -1,0 +1,213 @@
+// FP64 operator apply of the outer solve (2D), evaluated in double-FP32 arithmetic.
+//
+// y = H x (Eq. 3.10 with the sign of Eq. 4.4) or y = bscale*b - H x, with x in FP32 (the cycle's
+// output, exact floats) or FP64 (the iterate), y in FP64. The FP64 coefficients are precomputed
+// once on the host and stored as float-float pairs: cell mu and 1/(lambda+mu), node mu
+// (A_e, the mean of the four cells around a node), and the complex face masses
+// m_f = rho_f omega^2 (1 - i (gamma + gamma_ABL(x_f))) of the unshifted operator; the shifted
+// operator uses m_f - i alpha Re(m_f). Each row is then
+//   Laplacian: sum over the 3x3 faces of C(di, dj) u(i+di, j+dj) with
+//              C = cell(di) t(dj) + node(dj) t(di),  t = ((1-beta)/4, (1+beta)/2, (1-beta)/4),
+//              cell = (-mu_W, mu_W + mu_E, -mu_E) (the two cells beside the face),
+//              node = (-mu_S, mu_S + mu_N, -mu_N) (the two nodes beside it) -- the expansion of
+//              grad_h^T A_e(mu) grad_h^beta (Eq. 3.4-3.6);
+//   mass:      beta m_f u_f + (1-beta)/4 sum of the 4 neighbours' m u (Eq. 3.3);
+//   gradient:  (p_+ - p_-) / h;   continuity row: (div)^beta u + p/(lambda+mu).
+#pragma once
+#include "dfloat.cuh"
+#include "emg_types.cuh"
+
+namespace ff2 {
+
+using df::f2;
+constexpr int BX = 32, BY = 8;
+
+struct c2 {
+  f2 re, im;
+};
+
+struct FineFF {
+  int nx, ny;
+  f2 ih2, ih;        // 1/h^2, 1/h
+  f2 t0, t1;         // (1+beta)/2, (1-beta)/4
+  f2 beta, sm;       // beta, (1-beta)/4
+  f2 alpha;          // shift added to the attenuation (0 for H, alpha for H_s)
+  const f2* mu;      // nx*ny cells
+  const f2* mun;     // (nx+1)*(ny+1) nodes, node (X, Y) at X h, Y h
+  const f2* cp;      // nx*ny cells
+  const c2* m1;      // nx*ny u1 faces
+  const c2* m2;      // nx*ny u2 faces
+};
+
+__device__ __forceinline__ f2 ld(float v) { return {v, 0.f}; }
+__device__ __forceinline__ f2 ld(double v) { return df::split(v); }
+__device__ __forceinline__ f2 fneg(f2 a) { return {-a.hi, -a.lo}; }
+
+// float-float product / sum with normalisation (used for the few coefficient combinations)
+__device__ __forceinline__ f2 mul(f2 a, f2 b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  f2 r;
+  df::two_sum(p, e, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ f2 add(f2 a, f2 b) {
+  float s, t;
+  df::two_sum(a.hi, b.hi, s, t);
+  t += a.lo + b.lo;
+  f2 r;
+  df::two_sum(s, t, r.hi, r.lo);
+  return r;
+}
+
+struct cacc {
+  df::acc re, im;
+  // += c * u (c real)
+  __device__ __forceinline__ void rterm(f2 c, f2 ur, f2 ui) {
+    re.fma_ff(c, ur);
+    im.fma_ff(c, ui);
+  }
+  // += m * u (m complex)
+  __device__ __forceinline__ void cterm(const c2& m, f2 ur, f2 ui) {
+    re.fma_ff(m.re, ur);
+    re.fms_ff(m.im, ui);
+    im.fma_ff(m.re, ui);
+    im.fma_ff(m.im, ur);
+  }
+};
+
+template <typename TI>
+__global__ void __launch_bounds__(BX * BY) apply(FineFF g, const cx<TI>* __restrict__ x, const cx<double>* __restrict__ b,
+                                                double bscale, cx<double>* __restrict__ y) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int nx = g.nx, ny = g.ny;
+  if (i >= nx || j >= ny) return;
+  const size_t N = (size_t)nx * ny, k = (size_t)j * nx + i;
+  const cx<TI>* u1 = x;
+  const cx<TI>* u2 = x + N;
+  const cx<TI>* p = x + 2 * N;
+  const f2 z = {0.f, 0.f};
+  auto clampc = [&](int ii, int jj) { return (size_t)iclamp(jj, 0, ny - 1) * nx + iclamp(ii, 0, nx - 1); };
+  const f2 muC = g.mu[k];
+  const f2 t[3] = {g.t1, g.t0, g.t1};
+  auto mshift = [&](c2 m) {  // m - i alpha Re(m)
+    if (g.alpha.hi != 0.f) m.im = add(m.im, fneg(mul(g.alpha, m.re)));
+    return m;
+  };
+  // ---- u1 row at face (i, j)
+  cacc r1;
+  if (i >= 1) {
+    const f2 muW = g.mu[clampc(i - 1, j)];
+    const f2 nS = g.mun[(size_t)j * (nx + 1) + i], nN = g.mun[(size_t)(j + 1) * (nx + 1) + i];
+    const f2 cell[3] = {fneg(muW), add(muW, muC), fneg(muC)};
+    const f2 node[3] = {fneg(nS), add(nS, nN), fneg(nN)};
+#pragma unroll
+    for (int dj = -1; dj <= 1; ++dj) {
+      const int jj = j + dj;
+#pragma unroll
+      for (int di = -1; di <= 1; ++di) {
+        const int ii = i + di;
+        if (ii < 1 || ii >= nx || jj < 0 || jj >= ny) continue;
+        const cx<TI> u = u1[(size_t)jj * nx + ii];
+        const f2 C = mul(g.ih2, add(mul(cell[di + 1], t[dj + 1]), mul(node[dj + 1], t[di + 1])));
+        const f2 ur = ld(u.re), ui = ld(u.im);
+        r1.rterm(C, ur, ui);
+        // mass: -(beta m u) at the face, -(sm m u) at the 4 neighbours
+        if (di == 0 && dj == 0) {
+          const c2 m = mshift(g.m1[(size_t)jj * nx + ii]);
+          r1.cterm({fneg(mul(g.beta, m.re)), fneg(mul(g.beta, m.im))}, ur, ui);
+        } else if (di == 0 || dj == 0) {
+          const c2 m = mshift(g.m1[(size_t)jj * nx + ii]);
+          r1.cterm({fneg(mul(g.sm, m.re)), fneg(mul(g.sm, m.im))}, ur, ui);
+        }
+      }
+    }
+    // + (p(i,j) - p(i-1,j)) / h
+    const cx<TI> pc = p[k], pw = p[k - 1];
+    r1.rterm(g.ih, ld(pc.re), ld(pc.im));
+    r1.rterm(fneg(g.ih), ld(pw.re), ld(pw.im));
+  }
+  // ---- u2 row at face (i, j)
+  cacc r2;
+  if (j >= 1) {
+    const f2 muS = g.mu[clampc(i, j - 1)];
+    const f2 nW = g.mun[(size_t)j * (nx + 1) + i], nE = g.mun[(size_t)j * (nx + 1) + i + 1];
+    const f2 cell[3] = {fneg(muS), add(muS, muC), fneg(muC)};  // along x2 (dj)
+    const f2 node[3] = {fneg(nW), add(nW, nE), fneg(nE)};      // along x1 (di)
+#pragma unroll
+    for (int dj = -1; dj <= 1; ++dj) {
+      const int jj = j + dj;
+#pragma unroll
+      for (int di = -1; di <= 1; ++di) {
+        const int ii = i + di;
+        if (jj < 1 || jj >= ny || ii < 0 || ii >= nx) continue;
+        const cx<TI> u = u2[(size_t)jj * nx + ii];
+        const f2 C = mul(g.ih2, add(mul(cell[dj + 1], t[di + 1]), mul(node[di + 1], t[dj + 1])));
+        const f2 ur = ld(u.re), ui = ld(u.im);
+        r2.rterm(C, ur, ui);
+        if (di == 0 && dj == 0) {
+          const c2 m = mshift(g.m2[(size_t)jj * nx + ii]);
+          r2.cterm({fneg(mul(g.beta, m.re)), fneg(mul(g.beta, m.im))}, ur, ui);
+        } else if (di == 0 || dj == 0) {
+          const c2 m = mshift(g.m2[(size_t)jj * nx + ii]);
+          r2.cterm({fneg(mul(g.sm, m.re)), fneg(mul(g.sm, m.im))}, ur, ui);
+        }
+      }
+    }
+    const cx<TI> pc = p[k], ps = p[k - nx];
+    r2.rterm(g.ih, ld(pc.re), ld(pc.im));
+    r2.rterm(fneg(g.ih), ld(ps.re), ld(ps.im));
+  }
+  // ---- continuity row at cell (i, j): d1^beta u1 + d2^beta u2 + cp p
+  cacc rp;
+  {
+#pragma unroll
+    for (int dj = -1; dj <= 1; ++dj) {
+      const int jj = j + dj;
+      if (jj < 0 || jj >= ny) continue;
+      const f2 c = mul(g.ih, t[dj + 1]);
+      if (i + 1 < nx) {
+        const cx<TI> a = u1[(size_t)jj * nx + i + 1];
+        rp.rterm(c, ld(a.re), ld(a.im));
+      }
+      if (i >= 1) {
+        const cx<TI> a = u1[(size_t)jj * nx + i];
+        rp.rterm(fneg(c), ld(a.re), ld(a.im));
+      }
+    }
+#pragma unroll
+    for (int di = -1; di <= 1; ++di) {
+      const int ii = i + di;
+      if (ii < 0 || ii >= nx) continue;
+      const f2 c = mul(g.ih, t[di + 1]);
+      if (j + 1 < ny) {
+        const cx<TI> a = u2[(size_t)(j + 1) * nx + ii];
+        rp.rterm(c, ld(a.re), ld(a.im));
+      }
+      if (j >= 1) {
+        const cx<TI> a = u2[(size_t)j * nx + ii];
+        rp.rterm(fneg(c), ld(a.re), ld(a.im));
+      }
+    }
+    const cx<TI> pc = p[k];
+    rp.rterm(g.cp[k], ld(pc.re), ld(pc.im));
+  }
+  auto out = [&](const cacc& a) { return mkc<double>(a.re.to_double(), a.im.to_double()); };
+  cx<double> y1 = i >= 1 ? out(r1) : czero<double>();
+  cx<double> y2 = j >= 1 ? out(r2) : czero<double>();
+  cx<double> yp = out(rp);
+  if (b) {
+    y1 = i >= 1 ? bscale * b[k] - y1 : czero<double>();
+    y2 = j >= 1 ? bscale * b[N + k] - y2 : czero<double>();
+    yp = bscale * b[2 * N + k] - yp;
+  }
+  y[k] = y1;
+  y[N + k] = y2;
+  y[2 * N + k] = yp;
+  (void)z;
+}
+
+}  // namespace ff2

@@ -21,6 +21,7 @@
 #include "launch.h"
 #include "stencil2d.cuh"
 #include "stencil3d.cuh"
+#include "krylov_ff.cuh"
 #include "vector_kernels.cuh"
 
 namespace {
@@ -92,6 +93,7 @@ struct emg_ctx {
   cudaStream_t st = nullptr;
   std::vector<Level> lv;
   DBuf mu64, rho64, cp64;  // finest material in FP64 for the outer operator
+  DBuf ff_mu, ff_mun, ff_cp, ff_m1, ff_m2;  // 2D: FP64 coefficients as float-float pairs
   DBuf cinv;               // dense inverse of the coarsest operator (cycle precision)
   int cn = 0;
   // Krylov workspace
@@ -217,17 +219,17 @@ template <typename T> double half_sweep_bytes(const emg_ctx& c) {
 
 // ---------------------------------------------------------------- cycle pieces
 template <typename T>
-void launch_apply(emg_ctx& c, const Grid<T>& g, const void* x, bool x32, const cx<T>* b, cx<T>* y) {
+void launch_apply(emg_ctx& c, const Grid<T>& g, const void* x, bool x32, const cx<T>* b, T bscale, cx<T>* y) {
   if (x32) {
     if constexpr (std::is_same<T, double>::value) {
-      if (c.dim == 2) launch_apply2<double, float>(g, (const cx<float>*)x, b, y, c.st);
-      else launch_apply3<double, float>(g, (const cx<float>*)x, b, y, c.st);
+      if (c.dim == 2) launch_apply2<double, float>(g, (const cx<float>*)x, b, bscale, y, c.st);
+      else launch_apply3<double, float>(g, (const cx<float>*)x, b, bscale, y, c.st);
     } else {
       raise(EMG_ERR_INVALID, "FP32 input requires the FP64 operator");
     }
   } else {
-    if (c.dim == 2) launch_apply2<T, T>(g, (const cx<T>*)x, b, y, c.st);
-    else launch_apply3<T, T>(g, (const cx<T>*)x, b, y, c.st);
+    if (c.dim == 2) launch_apply2<T, T>(g, (const cx<T>*)x, b, bscale, y, c.st);
+    else launch_apply3<T, T>(g, (const cx<T>*)x, b, bscale, y, c.st);
   }
   CKL();
   LAUNCHED(c);
@@ -306,6 +308,7 @@ void vcycle(emg_ctx& c, int l, const cx<T>* b, cx<T>* x, bool zero_guess) {
   smooth<T>(c, l, b, x, c.prm.nu_pre, L.w, zero_guess);
   residual_restrict<T>(c, l, b, x, C.b.as<cx<T>>(), false);
   vcycle<T>(c, l + 1, C.b.as<cx<T>>(), C.x.as<cx<T>>(), true);
+  if (c.prm.cycle_type == EMG_CYCLE_W && l + 1 < c.L - 1) vcycle<T>(c, l + 1, C.b.as<cx<T>>(), C.x.as<cx<T>>(), false);
   prolong_correct<T>(c, l, C.x.as<cx<T>>(), x);
   smooth<T>(c, l, b, x, c.prm.nu_post, L.w, false);
 }
@@ -442,6 +445,58 @@ void coarsen_material(const emg_ctx& c, const Level& F, Level& C) {
       }
 }
 
+df::f2 to_f2(double v) {
+  df::f2 r;
+  r.hi = (float)v;
+  r.lo = (float)(v - (double)r.hi);
+  return r;
+}
+
+// FP64 coefficients of the finest 2D operator as float-float pairs for ff2::apply: cell mu,
+// 1/(lambda+mu), node mu (mean of the 4 cells around each node, clamped), and the face masses
+// m_f = rho_f omega^2 (1 - i (gamma + gamma_ABL(x_f))) of the unshifted operator.
+void build_ff2(emg_ctx& c) {
+  const Level& F = c.lv[0];
+  const int nx = F.n[0], ny = F.n[1];
+  const emg_params& p = c.prm;
+  std::vector<df::f2> mu(F.ncell), cp(F.ncell), mun((size_t)(nx + 1) * (ny + 1));
+  std::vector<ff2::c2> m1(F.ncell), m2(F.ncell);
+  auto M = [&](const std::vector<double>& f, int i, int j) {
+    return f[(size_t)std::min(std::max(j, 0), ny - 1) * nx + std::min(std::max(i, 0), nx - 1)];
+  };
+  const double w2 = p.omega * p.omega, L = p.abl_cells > 0 ? p.abl_cells * p.h : 0.0;
+  const double Lx = p.n[0] * p.h, Ly = p.n[1] * p.h;
+  auto abl = [&](double x, double y) {
+    if (L <= 0.0) return 0.0;
+    return p.abl_gamma_max * (abl_axis(x, L, Lx) + abl_axis(y, L, Ly)) / (L * L);
+  };
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const size_t k = (size_t)j * nx + i;
+      mu[k] = to_f2(F.mu_h[k]);
+      cp[k] = to_f2(1.0 / (F.lam_h[k] + F.mu_h[k]));
+      const double a1 = 0.5 * (M(F.rho_h, i - 1, j) + M(F.rho_h, i, j)) * w2;
+      const double g1 = p.gamma + abl(i * F.h, (j + 0.5) * F.h);
+      m1[k] = {to_f2(a1), to_f2(-a1 * g1)};
+      const double a2 = 0.5 * (M(F.rho_h, i, j - 1) + M(F.rho_h, i, j)) * w2;
+      const double g2 = p.gamma + abl((i + 0.5) * F.h, j * F.h);
+      m2[k] = {to_f2(a2), to_f2(-a2 * g2)};
+    }
+  for (int Y = 0; Y <= ny; ++Y)
+    for (int X = 0; X <= nx; ++X)
+      mun[(size_t)Y * (nx + 1) + X] =
+          to_f2(0.25 * (M(F.mu_h, X - 1, Y - 1) + M(F.mu_h, X, Y - 1) + M(F.mu_h, X - 1, Y) + M(F.mu_h, X, Y)));
+  auto up = [&](DBuf& d, const void* src, size_t bytes) {
+    d.alloc(bytes);
+    CK(cudaMemcpy(d.p, src, bytes, cudaMemcpyHostToDevice));
+  };
+  up(c.ff_mu, mu.data(), mu.size() * sizeof(df::f2));
+  up(c.ff_cp, cp.data(), cp.size() * sizeof(df::f2));
+  up(c.ff_mun, mun.data(), mun.size() * sizeof(df::f2));
+  up(c.ff_m1, m1.data(), m1.size() * sizeof(ff2::c2));
+  up(c.ff_m2, m2.data(), m2.size() * sizeof(ff2::c2));
+}
+
 template <typename T>
 void build(emg_ctx& c) {
   const int d = c.dim;
@@ -466,6 +521,7 @@ void build(emg_ctx& c) {
   CK(cudaMemcpy(c.mu64.p, F.mu_h.data(), F.ncell * 8, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c.rho64.p, F.rho_h.data(), F.ncell * 8, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c.cp64.p, cp.data(), F.ncell * 8, cudaMemcpyHostToDevice));
+  if (c.dim == 2) build_ff2(c);
   if (c.prm.coarse_solver == EMG_COARSE_DENSE) {
     std::vector<std::complex<double>> A, Ainv;
     std::vector<int> act;
@@ -498,38 +554,45 @@ void ensure_krylov(emg_ctx& c, int m) {
   if (!c.hred) CK(cudaMallocHost(&c.hred, 4096 * sizeof(double)));
 }
 
+// Launch one multi-dot pass over NV vectors; native FP64 (exact) or float-float (ff).
 template <int NV>
-void launch_mdot(emg_ctx& c, const cx<double>* V, size_t ldv, const cx<double>* w, size_t n, double* part, int nblk) {
-  kv::mdot<NV><<<nblk, kv::RT, 0, c.st>>>(V, ldv, w, n, part);
+void launch_mdot(emg_ctx& c, bool ff, const cx<double>* V, size_t ldv, const cx<double>* w, size_t n, double* part,
+                 int nblk) {
+  if (ff) kf::mdot<NV><<<nblk, kv::RT, 0, c.st>>>(V, ldv, w, n, part);
+  else kv::mdot<NV><<<nblk, kv::RT, 0, c.st>>>(V, ldv, w, n, part);
   CKL();
   LAUNCHED(c);
 }
 
 // h[i] = V_i^H w for i < cnt, and ||w||^2; one device->host transfer, one synchronisation.
-void mdots(emg_ctx& c, const cx<double>* V, size_t ldv, int cnt, const cx<double>* w, size_t n,
+void mdots(emg_ctx& c, bool ff, const cx<double>* V, size_t ldv, int cnt, const cx<double>* w, size_t n,
            std::vector<std::complex<double>>& h, double& wn2) {
   const int nblk = vec_blocks(c, n);
   double* part = c.part.as<double>();
   double* red = c.red.as<double>();
   int off = 0, s = 0;
   std::vector<std::pair<int, int>> chunks;  // (first vector, count)
+  const double vbytes = (double)n * 16;
   do {
     int nv = std::min(kv::MAXV, cnt - s);
-    switch (nv) {
-      case 0: launch_mdot<0>(c, V, ldv, w, n, part, nblk); break;
-      case 1: launch_mdot<1>(c, V + s * ldv, ldv, w, n, part, nblk); break;
-      case 2: launch_mdot<2>(c, V + s * ldv, ldv, w, n, part, nblk); break;
-      case 3: launch_mdot<3>(c, V + s * ldv, ldv, w, n, part, nblk); break;
-      case 4: launch_mdot<4>(c, V + s * ldv, ldv, w, n, part, nblk); break;
-      case 5: launch_mdot<5>(c, V + s * ldv, ldv, w, n, part, nblk); break;
-      case 6: launch_mdot<6>(c, V + s * ldv, ldv, w, n, part, nblk); break;
-      case 7: launch_mdot<7>(c, V + s * ldv, ldv, w, n, part, nblk); break;
-      default: launch_mdot<8>(c, V + s * ldv, ldv, w, n, part, nblk); break;
+    {
+      ProfScope ps(c, EMG_K_KRYLOV, 0, vbytes * (nv + 1));
+      switch (nv) {
+        case 0: launch_mdot<0>(c, ff, V, ldv, w, n, part, nblk); break;
+        case 1: launch_mdot<1>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
+        case 2: launch_mdot<2>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
+        case 3: launch_mdot<3>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
+        case 4: launch_mdot<4>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
+        case 5: launch_mdot<5>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
+        case 6: launch_mdot<6>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
+        case 7: launch_mdot<7>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
+        default: launch_mdot<8>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
+      }
     }
     const int nr = 2 * nv + 1;
     kv::reduce_parts<<<1, 128, 0, c.st>>>(part, nblk, nr, red + off);
     CKL();
-  LAUNCHED(c);
+    LAUNCHED(c);
     chunks.push_back({s, nv});
     off += nr;
     s += nv;
@@ -548,15 +611,19 @@ void mdots(emg_ctx& c, const cx<double>* V, size_t ldv, int cnt, const cx<double
   if (!std::isfinite(wn2)) raise(EMG_ERR_NONFINITE, "non-finite Krylov norm");
 }
 
-// w -= V h (cnt vectors); returns ||w||^2.
-double update(emg_ctx& c, cx<double>* w, const cx<double>* V, size_t ldv, const std::vector<std::complex<double>>& h, size_t n) {
+// w <- s (w - sum_i h_i V_i), optionally also written in FP32 to out32; returns ||w_new||^2.
+double update_scale(emg_ctx& c, cx<double>* w, const cx<double>* V, size_t ldv,
+                    const std::vector<std::complex<double>>& h, double s, size_t n, cx<float>* out32) {
   const int nblk = vec_blocks(c, n);
-  kv::Coefs co;
+  kf::Coefs co;
   const int cnt = (int)h.size();
-  for (int i = 0; i < cnt; ++i) co.c[i] = mkc(h[i].real(), h[i].imag());
-  kv::update_norm<<<nblk, kv::RT, 0, c.st>>>(w, V, ldv, cnt, co, n, c.part.as<double>());
-  CKL();
-  LAUNCHED(c);
+  for (int i = 0; i < cnt; ++i) co.c[i] = {to_f2(h[i].real()), to_f2(h[i].imag())};
+  {
+    ProfScope ps(c, EMG_K_KRYLOV, 0, (double)n * 16 * (cnt + 2) + (out32 ? n * 8.0 : 0.0));
+    kf::update_scale<<<nblk, kv::RT, 0, c.st>>>(w, V, ldv, cnt, co, to_f2(s), n, out32, c.part.as<double>());
+    CKL();
+    LAUNCHED(c);
+  }
   kv::reduce_parts<<<1, 128, 0, c.st>>>(c.part.as<double>(), nblk, 1, c.red.as<double>());
   CKL();
   LAUNCHED(c);
@@ -566,92 +633,132 @@ double update(emg_ctx& c, cx<double>* w, const cx<double>* V, size_t ldv, const 
   return c.hred[0];
 }
 
-double norm2(emg_ctx& c, const cx<double>* w, size_t n) {
-  std::vector<std::complex<double>> h;
-  double wn2 = 0;
-  mdots(c, nullptr, 0, 0, w, n, h, wn2);
-  return wn2;
-}
-
-// y = H x (FP64, unshifted) or r = b - H x on the finest level; x in FP64 or in FP32.
-void outer_apply(emg_ctx& c, const void* x, bool x32, const cx<double>* b, cx<double>* y, bool shifted) {
-  Grid<double> g = make_grid<double>(c, 0, shifted, c.mu64.p, c.rho64.p, c.cp64.p);
+// y = H x (unshifted or shifted) or y = bscale*b - H x on the finest level in FP64; x in FP64 or FP32.
+void outer_apply(emg_ctx& c, const void* x, bool x32, const cx<double>* b, double bscale, cx<double>* y, bool shifted) {
   const double cw = 16.0;
+  if (c.dim == 2) {
+    // float-float evaluation from precomputed FP64 coefficients (x, b, y + mu, node mu, cp, 2 masses)
+    ProfScope ps(c, EMG_K_APPLY64, 0, (double)c.lv[0].ncell * (3 * ((x32 ? 8.0 : 16.0) + cw + (b ? cw : 0.0)) + 3 * 8.0 + 2 * 16.0));
+    const Level& F = c.lv[0];
+    ff2::FineFF g;
+    g.nx = F.n[0];
+    g.ny = F.n[1];
+    g.ih = to_f2(1.0 / F.h);
+    g.ih2 = to_f2(1.0 / (F.h * F.h));
+    g.t0 = to_f2(0.5 * (1.0 + c.prm.beta));
+    g.t1 = to_f2(0.25 * (1.0 - c.prm.beta));
+    g.beta = to_f2(c.prm.beta);
+    g.sm = to_f2(0.25 * (1.0 - c.prm.beta));
+    g.alpha = to_f2(shifted ? c.prm.alpha : 0.0);
+    g.mu = c.ff_mu.as<df::f2>();
+    g.mun = c.ff_mun.as<df::f2>();
+    g.cp = c.ff_cp.as<df::f2>();
+    g.m1 = c.ff_m1.as<ff2::c2>();
+    g.m2 = c.ff_m2.as<ff2::c2>();
+    if (x32) launch_apply_ff2<float>(g, (const cx<float>*)x, b, bscale, y, c.st);
+    else launch_apply_ff2<double>(g, (const cx<double>*)x, b, bscale, y, c.st);
+    CKL();
+    LAUNCHED(c);
+    return;
+  }
+  Grid<double> g = make_grid<double>(c, 0, shifted, c.mu64.p, c.rho64.p, c.cp64.p);
   ProfScope ps(c, EMG_K_APPLY64, 0, (double)c.lv[0].ncell * ((c.dim + 1) * ((x32 ? 8.0 : 16.0) + cw + (b ? cw : 0.0)) + 3 * 8.0));
-  launch_apply<double>(c, g, x, x32, b, y);
+  launch_apply<double>(c, g, x, x32, b, bscale, y);
 }
 
 template <typename T>
 void precondition(emg_ctx& c, const cx<double>* v, cx<T>* z) {
-  const size_t n = c.nvec();
   Level& F = c.lv[0];
-  const cx<T>* b;
-  if (std::is_same<T, double>::value) {
-    b = (const cx<T>*)v;
-  } else {
-    kv::cast<T, double><<<vec_blocks(c, n), 256, 0, c.st>>>(F.b.as<cx<T>>(), v, n);
-    CKL();
-  LAUNCHED(c);
-    b = F.b.as<cx<T>>();
-  }
+  // FP32 cycle: its right-hand side was written in FP32 to F.b by the update that produced v
+  const cx<T>* b = std::is_same<T, double>::value ? (const cx<T>*)v : F.b.as<cx<T>>();
   vcycle<T>(c, 0, b, z, true);
 }
 
+// Right-preconditioned restarted FGMRES(m), Saad (1993). Classical Gram-Schmidt with the
+// Pythagorean norm ||w'||^2 = ||w||^2 - sum |h_i|^2 and one re-orthogonalisation pass when it
+// cancels (||w'||^2 < ||w||^2 / 2); the update of the new basis vector is deferred into a fused
+// pass that also normalises it and writes the next cycle's FP32 right-hand side. All vectors are
+// scaled by a power of two so that ||b|| ~ 1 (exact), which keeps them inside the float exponent
+// range of the float-float kernels; x is unscaled on exit.
 template <typename T>
 emg_status solve_impl(emg_ctx& c, const cx<double>* b, cx<double>* x, double tol, int max_iter, int m, emg_stats* st) {
   const size_t n = c.nvec();
   ensure_krylov(c, m);
+  const bool f32 = std::is_same<T, float>::value;
   cx<double>* V = c.V.as<cx<double>>();
   cx<T>* Z = c.Z.as<cx<T>>();
   cx<double>* r = c.wk64.as<cx<double>>();
+  cx<float>* b32 = f32 ? c.lv[0].b.as<cx<float>>() : nullptr;
   int hist = 0;
   auto push_hist = [&](double v) {
     if (st && st->history && hist < st->history_cap) st->history[hist] = v;
     ++hist;
   };
-  const double bnorm = std::sqrt(norm2(c, b, n));
+  std::vector<std::complex<double>> h, h2;
+  double bn2 = 0;
+  mdots(c, false, nullptr, 0, 0, b, n, h, bn2);  // exact FP64 norm of the caller's b
+  const double bnorm = std::sqrt(bn2);
   if (!(bnorm > 0.0)) {
     CK(cudaMemsetAsync(x, 0, n * 16, c.st));
     CK(cudaStreamSynchronize(c.st));
     if (st) { st->iterations = 0; st->restarts = 0; st->rel_residual = 0.0; st->history_len = 0; }
     return EMG_OK;
   }
-  outer_apply(c, x, false, b, r, false);
-  double beta = std::sqrt(norm2(c, r, n));
-  push_hist(beta / bnorm);
-  int its = 0, restarts = 0;
-  std::vector<std::complex<double>> Hh((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), h, h2;
-  while (beta / bnorm > tol && its < max_iter) {
-    kv::scale<<<vec_blocks(c, n), 256, 0, c.st>>>(V, r, 1.0 / beta, n);
-    CKL();
+  const double sc = std::ldexp(1.0, -std::ilogb(bnorm));  // power of two: sc*||b|| in [1, 2)
+  const double bhat = sc * bnorm;
+  kv::scale<<<vec_blocks(c, n), 256, 0, c.st>>>(x, x, sc, n);
+  CKL();
   LAUNCHED(c);
+  auto true_residual = [&]() {
+    outer_apply(c, x, false, b, sc, r, false);  // r = sc*b - H (sc*x)
+    double rn2 = 0;
+    mdots(c, true, nullptr, 0, 0, r, n, h, rn2);
+    return std::sqrt(rn2);
+  };
+  double beta = true_residual();
+  push_hist(beta / bhat);
+  int its = 0, restarts = 0;
+  std::vector<std::complex<double>> Hh((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1);
+  while (beta / bhat > tol && its < max_iter) {
+    // V_0 = r / beta (and its FP32 copy for the first cycle)
+    CK(cudaMemcpyAsync(V, r, n * 16, cudaMemcpyDeviceToDevice, c.st));
+    update_scale(c, V, V, n, {}, 1.0 / beta, n, b32);
     std::fill(Hh.begin(), Hh.end(), 0.0);
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int k = 0;
+    std::vector<std::complex<double>> pend;  // deferred coefficients of V_j
+    double pend_norm = 1.0;
     for (int j = 0; j < m; ++j) {
       cx<double>* vj = V + (size_t)j * n;
+      if (j > 0) update_scale(c, vj, V, n, pend, 1.0 / pend_norm, n, b32);  // finish V_j
       cx<double>* w = V + (size_t)(j + 1) * n;
       precondition<T>(c, vj, Z + (size_t)j * n);
-      outer_apply(c, Z + (size_t)j * n, std::is_same<T, float>::value, nullptr, w, false);
-      // classical Gram-Schmidt with one re-orthogonalisation when cancellation is detected
+      outer_apply(c, Z + (size_t)j * n, f32, nullptr, 0.0, w, false);
       double wn2 = 0;
-      mdots(c, V, n, j + 1, w, n, h, wn2);
-      double nn2 = update(c, w, V, n, h, n);
-      if (nn2 < 0.25 * wn2) {
-        double dummy;
-        mdots(c, V, n, j + 1, w, n, h2, dummy);
-        nn2 = update(c, w, V, n, h2, n);
+      mdots(c, true, V, n, j + 1, w, n, h, wn2);
+      double hh = 0;
+      for (auto& z : h) hh += std::norm(z);
+      double nn2 = wn2 - hh;
+      pend = h;
+      if (nn2 < 0.5 * wn2) {  // cancellation: apply the projection now and orthogonalise again
+        update_scale(c, w, V, n, h, 1.0, n, nullptr);
+        double wn2b = 0;
+        mdots(c, true, V, n, j + 1, w, n, h2, wn2b);
+        double hh2 = 0;
+        for (auto& z : h2) hh2 += std::norm(z);
+        nn2 = wn2b - hh2;
+        if (nn2 < 0.5 * wn2b) {  // still cancelling: materialise and measure exactly
+          nn2 = update_scale(c, w, V, n, h2, 1.0, n, nullptr);
+          h2.assign(j + 1, 0.0);
+        }
         for (int i = 0; i <= j; ++i) h[i] += h2[i];
+        pend = h2;
       }
       const double hn = std::sqrt(std::max(nn2, 0.0));
+      pend_norm = hn > 0.0 ? hn : 1.0;
       for (int i = 0; i <= j; ++i) Hh[(size_t)i * m + j] = h[i];
       Hh[(size_t)(j + 1) * m + j] = hn;
-      if (hn > 0.0) {
-        kv::scale<<<vec_blocks(c, n), 256, 0, c.st>>>(w, w, 1.0 / hn, n);
-        CKL();
-  LAUNCHED(c);
-      }
       for (int i = 0; i < j; ++i) {
         std::complex<double> a = Hh[(size_t)i * m + j], bb = Hh[(size_t)(i + 1) * m + j];
         Hh[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
@@ -667,8 +774,8 @@ emg_status solve_impl(emg_ctx& c, const cx<double>* b, cx<double>* x, double tol
       g[j] = cs[j] * g[j];
       ++its;
       k = j + 1;
-      push_hist(std::abs(g[j + 1]) / bnorm);
-      if (std::abs(g[j + 1]) / bnorm <= tol || its >= max_iter || hn == 0.0) break;
+      push_hist(std::abs(g[j + 1]) / bhat);
+      if (std::abs(g[j + 1]) / bhat <= tol || its >= max_iter || hn == 0.0) break;
     }
     // y = R^{-1} g, x += Z y
     std::vector<std::complex<double>> y(k);
@@ -677,22 +784,28 @@ emg_status solve_impl(emg_ctx& c, const cx<double>* b, cx<double>* x, double tol
       for (int q = i + 1; q < k; ++q) s -= Hh[(size_t)i * m + q] * y[q];
       y[i] = s / Hh[(size_t)i * m + i];
     }
-    kv::Coefs co;
-    for (int i = 0; i < k; ++i) co.c[i] = mkc(y[i].real(), y[i].imag());
-    kv::combine<T><<<vec_blocks(c, n), 256, 0, c.st>>>(x, Z, n, k, co, n);
-    CKL();
-  LAUNCHED(c);
-    outer_apply(c, x, false, b, r, false);
-    beta = std::sqrt(norm2(c, r, n));
+    kf::Coefs co;
+    for (int i = 0; i < k; ++i) co.c[i] = {to_f2(y[i].real()), to_f2(y[i].imag())};
+    {
+      ProfScope ps(c, EMG_K_KRYLOV, 0, (double)n * (32.0 + k * (f32 ? 8.0 : 16.0)));
+      kf::combine<T><<<vec_blocks(c, n), kv::RT, 0, c.st>>>(x, Z, n, k, co, n);
+      CKL();
+      LAUNCHED(c);
+    }
+    beta = true_residual();
     ++restarts;
   }
+  kv::scale<<<vec_blocks(c, n), 256, 0, c.st>>>(x, x, 1.0 / sc, n);
+  CKL();
+  LAUNCHED(c);
+  CK(cudaStreamSynchronize(c.st));
   if (st) {
     st->iterations = its;
     st->restarts = restarts;
-    st->rel_residual = beta / bnorm;
+    st->rel_residual = beta / bhat;
     st->history_len = std::min(hist, st->history ? st->history_cap : 0);
   }
-  return beta / bnorm <= tol ? EMG_OK : EMG_NOT_CONVERGED;
+  return beta / bhat <= tol ? EMG_OK : EMG_NOT_CONVERGED;
 }
 
 void check_params(const emg_params* p) {
@@ -711,6 +824,7 @@ void check_params(const emg_params* p) {
   if (p->abl_cells < 0) raise(EMG_ERR_INVALID, "abl_cells must be >= 0");
   if (p->nu_pre < 0 || p->nu_post < 0) raise(EMG_ERR_INVALID, "negative smoothing count");
   if (p->cycle_precision != 32 && p->cycle_precision != 64) raise(EMG_ERR_INVALID, "cycle_precision must be 32 or 64");
+  if (p->cycle_type != EMG_CYCLE_V && p->cycle_type != EMG_CYCLE_W) raise(EMG_ERR_INVALID, "unknown cycle_type");
   if (p->coarse_solver != EMG_COARSE_DENSE && p->coarse_solver != EMG_COARSE_SMOOTH)
     raise(EMG_ERR_INVALID, "unknown coarse_solver");
   if (p->coarse_solver == EMG_COARSE_SMOOTH && p->coarse_sweeps < 1 && p->levels > 0)
@@ -827,7 +941,7 @@ emg_status emg_apply(emg_handle h, int shifted, const void* x, void* y) {
   emg_ctx& c = *checked(h);
   check_ptr(x, "x");
   check_ptr(y, "y");
-  outer_apply(c, x, false, nullptr, (cx<double>*)y, shifted != 0);
+  outer_apply(c, x, false, nullptr, 0.0, (cx<double>*)y, shifted != 0);
   ABI_CATCH
   return EMG_OK;
 }

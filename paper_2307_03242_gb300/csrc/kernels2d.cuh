@@ -52,10 +52,10 @@ HD void cell_solve(cx<T> a1[4], cx<T> a2[4], const bool ex[4], T ih, T t0, T cp,
   for (int k = 0; k < 4; ++k) d[k] = y1[k] - y2[k] * d[4];
 }
 
-// y = H x (b == nullptr) or y = b - H x. Component pointers: x + c*N.
+// y = H x (b == nullptr) or y = bscale * b - H x. Component pointers: x + c*N.
 template <typename T, typename TI>
 __global__ void __launch_bounds__(BX * BY) apply(Grid<T> g, const cx<TI>* __restrict__ x,
-                                                const cx<T>* __restrict__ b, cx<T>* __restrict__ y) {
+                                                const cx<T>* __restrict__ b, T bscale, cx<T>* __restrict__ y) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
@@ -67,9 +67,9 @@ __global__ void __launch_bounds__(BX * BY) apply(Grid<T> g, const cx<TI>* __rest
   cx<T> y2 = j >= 1 ? s2::row_u2(u2, p, g, i, j) : czero<T>();
   cx<T> yp = s2::row_p(u1, u2, p, g, i, j);
   if (b) {
-    y1 = i >= 1 ? b[k] - y1 : czero<T>();
-    y2 = j >= 1 ? b[N + k] - y2 : czero<T>();
-    yp = b[2 * N + k] - yp;
+    y1 = i >= 1 ? bscale * b[k] - y1 : czero<T>();
+    y2 = j >= 1 ? bscale * b[N + k] - y2 : czero<T>();
+    yp = bscale * b[2 * N + k] - yp;
   }
   y[k] = y1;
   y[N + k] = y2;

@@ -45,7 +45,7 @@ HD void cell_solve(cx<T> a[3][4], const bool ex[6], T ih, T w00, T cp, cx<T> r[7
 
 template <typename T, typename TI>
 __global__ void __launch_bounds__(BX * BY * BZ) apply(Grid<T> g, const cx<TI>* __restrict__ x,
-                                                     const cx<T>* __restrict__ b, cx<T>* __restrict__ y) {
+                                                     const cx<T>* __restrict__ b, T bscale, cx<T>* __restrict__ y) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z * BZ + threadIdx.z;
@@ -57,11 +57,11 @@ __global__ void __launch_bounds__(BX * BY * BZ) apply(Grid<T> g, const cx<TI>* _
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     cx<T> v = idx[c] >= 1 ? s3::row_u(c, u[c], p, g, i, j, k) : czero<T>();
-    if (b) v = idx[c] >= 1 ? b[c * N + q] - v : czero<T>();
+    if (b) v = idx[c] >= 1 ? bscale * b[c * N + q] - v : czero<T>();
     y[c * N + q] = v;
   }
   cx<T> v = s3::row_p(u, p, g, i, j, k);
-  if (b) v = b[3 * N + q] - v;
+  if (b) v = bscale * b[3 * N + q] - v;
   y[3 * N + q] = v;
 }
 

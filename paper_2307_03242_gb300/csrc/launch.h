@@ -2,9 +2,10 @@
 // (launch2d.cu, launch3d.cu) so that the library builds in parallel.
 #pragma once
 #include "emg_types.cuh"
+#include "apply_ff2d.cuh"
 
 template <typename T, typename TI>
-void launch_apply2(const Grid<T>& g, const cx<TI>* x, const cx<T>* b, cx<T>* y, cudaStream_t st);
+void launch_apply2(const Grid<T>& g, const cx<TI>* x, const cx<T>* b, T bscale, cx<T>* y, cudaStream_t st);
 template <typename T>
 void launch_vanka2(const Grid<T>& g, const cx<T>* b, const cx<T>* uin, cx<T>* uout, cx<T>* p, int colour, T w,
                    int zero_in, cudaStream_t st);
@@ -15,7 +16,7 @@ template <typename T>
 void launch_prolong2(const cx<T>* e, cx<T>* x, const int n[3], const int nc[3], cudaStream_t st);
 
 template <typename T, typename TI>
-void launch_apply3(const Grid<T>& g, const cx<TI>* x, const cx<T>* b, cx<T>* y, cudaStream_t st);
+void launch_apply3(const Grid<T>& g, const cx<TI>* x, const cx<T>* b, T bscale, cx<T>* y, cudaStream_t st);
 template <typename T>
 void launch_vanka3(const Grid<T>& g, const cx<T>* b, const cx<T>* uin, cx<T>* uout, cx<T>* p, int colour, T w,
                    int zero_in, cudaStream_t st);
@@ -24,3 +25,7 @@ void launch_restrict3(const Grid<T>& g, const cx<T>* b, const cx<T>* x, cx<T>* b
                       cudaStream_t st);
 template <typename T>
 void launch_prolong3(const cx<T>* e, cx<T>* x, const int n[3], const int nc[3], cudaStream_t st);
+
+template <typename TI>
+void launch_apply_ff2(const ff2::FineFF& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y,
+                      cudaStream_t st);

@@ -1,19 +1,20 @@
 // 2D kernel launchers (explicit instantiations for the FP32 and FP64 cycles and the FP64 apply).
-#include "kernels2d.cuh"
+#include "vanka2d_fast.cuh"
 #include "launch.h"
+#include "apply_ff2d.cuh"
 
 namespace {
 dim3 g2(int nx, int ny) { return dim3((nx + k2::BX - 1) / k2::BX, (ny + k2::BY - 1) / k2::BY); }
 }  // namespace
 
 template <typename T, typename TI>
-void launch_apply2(const Grid<T>& g, const cx<TI>* x, const cx<T>* b, cx<T>* y, cudaStream_t st) {
-  k2::apply<T, TI><<<g2(g.nx, g.ny), dim3(k2::BX, k2::BY), 0, st>>>(g, x, b, y);
+void launch_apply2(const Grid<T>& g, const cx<TI>* x, const cx<T>* b, T bscale, cx<T>* y, cudaStream_t st) {
+  k2::apply<T, TI><<<g2(g.nx, g.ny), dim3(k2::BX, k2::BY), 0, st>>>(g, x, b, bscale, y);
 }
 template <typename T>
 void launch_vanka2(const Grid<T>& g, const cx<T>* b, const cx<T>* uin, cx<T>* uout, cx<T>* p, int colour, T w,
                    int zero_in, cudaStream_t st) {
-  k2::vanka<T><<<g2((g.nx + 1) / 2, g.ny), dim3(k2::BX, k2::BY), 0, st>>>(g, b, uin, uout, p, colour, w, zero_in);
+  k2::vanka_fast<T><<<g2((g.nx + 1) / 2, g.ny), dim3(k2::BX, k2::BY), 0, st>>>(g, b, uin, uout, p, colour, w, zero_in);
 }
 template <typename T>
 void launch_restrict2(const Grid<T>& g, const cx<T>* b, const cx<T>* x, cx<T>* bc, const int nc[3], int zero_x,
@@ -25,12 +26,20 @@ void launch_prolong2(const cx<T>* e, cx<T>* x, const int n[3], const int nc[3], 
   k2::prolong_add<T><<<g2(n[0], n[1]), dim3(k2::BX, k2::BY), 0, st>>>(e, x, n[0], n[1], nc[0], nc[1]);
 }
 
-template void launch_apply2<float, float>(const Grid<float>&, const cx<float>*, const cx<float>*, cx<float>*, cudaStream_t);
-template void launch_apply2<double, double>(const Grid<double>&, const cx<double>*, const cx<double>*, cx<double>*, cudaStream_t);
-template void launch_apply2<double, float>(const Grid<double>&, const cx<float>*, const cx<double>*, cx<double>*, cudaStream_t);
+template void launch_apply2<float, float>(const Grid<float>&, const cx<float>*, const cx<float>*, float, cx<float>*, cudaStream_t);
+template void launch_apply2<double, double>(const Grid<double>&, const cx<double>*, const cx<double>*, double, cx<double>*, cudaStream_t);
+template void launch_apply2<double, float>(const Grid<double>&, const cx<float>*, const cx<double>*, double, cx<double>*, cudaStream_t);
 #define INST(T)                                                                                                   \
   template void launch_vanka2<T>(const Grid<T>&, const cx<T>*, const cx<T>*, cx<T>*, cx<T>*, int, T, int, cudaStream_t); \
   template void launch_restrict2<T>(const Grid<T>&, const cx<T>*, const cx<T>*, cx<T>*, const int*, int, cudaStream_t); \
   template void launch_prolong2<T>(const cx<T>*, cx<T>*, const int*, const int*, cudaStream_t);
 INST(float)
 INST(double)
+
+template <typename TI>
+void launch_apply_ff2(const ff2::FineFF& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y,
+                      cudaStream_t st) {
+  ff2::apply<TI><<<g2(g.nx, g.ny), dim3(ff2::BX, ff2::BY), 0, st>>>(g, x, b, bscale, y);
+}
+template void launch_apply_ff2<float>(const ff2::FineFF&, const cx<float>*, const cx<double>*, double, cx<double>*, cudaStream_t);
+template void launch_apply_ff2<double>(const ff2::FineFF&, const cx<double>*, const cx<double>*, double, cx<double>*, cudaStream_t);

@@ -15,6 +15,7 @@ import numpy as np
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libemg.so")
 MAX_LEVELS = 10
 COARSE_DENSE, COARSE_SMOOTH = 0, 1
+CYCLE_V, CYCLE_W = 0, 1
 K_SMOOTH, K_RESTRICT, K_PROLONG, K_APPLY64, K_KRYLOV = range(5)
 K_ALL = 5
 
@@ -35,7 +36,7 @@ class _Params(ctypes.Structure):
                 ("levels", ctypes.c_int32), ("nu_pre", ctypes.c_int32), ("nu_post", ctypes.c_int32),
                 ("damping", ctypes.c_double * MAX_LEVELS), ("coarse_solver", ctypes.c_int32),
                 ("coarse_sweeps", ctypes.c_int32), ("coarse_damping", ctypes.c_double),
-                ("cycle_precision", ctypes.c_int32)]
+                ("cycle_precision", ctypes.c_int32), ("cycle_type", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -103,6 +104,7 @@ class Params:
     coarse_sweeps: int = 0
     coarse_damping: float = 0.8
     cycle_precision: int = 32
+    cycle_type: int = CYCLE_V
 
     def to_c(self) -> _Params:
         p = _Params()
@@ -117,6 +119,7 @@ class Params:
             p.damping[l] = float(d[l]) if l < len(d) else 0.0
         p.coarse_solver, p.coarse_sweeps = int(self.coarse_solver), int(self.coarse_sweeps)
         p.coarse_damping, p.cycle_precision = float(self.coarse_damping), int(self.cycle_precision)
+        p.cycle_type = int(self.cycle_type)
         return p
 
 
@@ -125,7 +128,8 @@ def params_from_workload(w, cycle_precision=32, **over) -> Params:
               abl_cells=w.abl_cells, abl_gamma_max=w.abl_gamma_max, levels=w.levels, nu_pre=w.nu_pre,
               nu_post=w.nu_post, damping=w.damping,
               coarse_solver=COARSE_DENSE if w.coarse == "dense" else COARSE_SMOOTH,
-              coarse_sweeps=w.coarse_sweeps, coarse_damping=w.coarse_damping, cycle_precision=cycle_precision)
+              coarse_sweeps=w.coarse_sweeps, coarse_damping=w.coarse_damping, cycle_precision=cycle_precision,
+              cycle_type=CYCLE_W if getattr(w, "cycle", "V") == "W" else CYCLE_V)
     kw.update(over)
     return Params(**kw)
 

@@ -15,7 +15,7 @@ def oracle_hierarchy(w, pb=None, damping=None):
     pb = pb or oracle_problem(w)
     return oracle.Hierarchy(pb, w.levels, w.alpha, w.damping if damping is None else damping,
                             nu_pre=w.nu_pre, nu_post=w.nu_post, coarse=w.coarse,
-                            coarse_sweeps=w.coarse_sweeps, coarse_damping=w.coarse_damping)
+                            coarse_sweeps=w.coarse_sweeps, coarse_damping=w.coarse_damping, cycle=w.cycle)
 
 
 def gpu_solver(w, prec, **over):

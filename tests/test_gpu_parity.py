@@ -141,6 +141,26 @@ def test_vcycle_matches_oracle(case, prec, coarse):
 
 
 @pytest.mark.parametrize("case", ["2d", "3d"])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_wcycle_matches_oracle(case, prec):
+    """W-cycle (two recursive calls, Sec. 2.2) with a smoothed coarsest level."""
+    c = dict(CASES[case])
+    levels = 3 if case == "2d" else 2
+    w = small_heterogeneous(c["n"], seed=5, levels=levels, abl_cells=c["abl_cells"], sigma_cells=2.0)
+    w.cycle, w.coarse, w.coarse_sweeps, w.coarse_damping = "W", "smooth", 3, 0.8
+    pb = oracle_problem(w)
+    hier = oracle_hierarchy(w, pb)
+    s = gpu_solver(w, prec)
+    b = random_field(pb, 63)
+    ref = oracle.vcycle(hier, b.ravel())
+    import torch
+    xt = torch.zeros(s.vec_shape(0), dtype=s.cdtype, device="cuda")
+    s.vcycle(to_gpu(b, prec), xt, zero_guess=True)
+    assert rel(to_np(xt).ravel() * oracle.active_mask(pb), ref) < TOL_CYCLE[prec]
+    s.close()
+
+
+@pytest.mark.parametrize("case", ["2d", "3d"])
 def test_vcycle_is_deterministic(case):
     w = _w(case)
     pb = oracle_problem(w)

@@ -178,3 +178,20 @@ def test_windowed_operator_matches_full_operator_away_from_cuts(n):
     full_inner = tuple(slice(lo[a] + inner[d - 1 - a].start, lo[a] + inner[d - 1 - a].stop)
                        for a in reversed(range(d)))
     np.testing.assert_allclose(yw[(slice(None),) + tuple(inner)], y[(slice(None),) + full_inner], atol=1e-12)
+
+
+def test_wcycle_converges_to_dense_direct_solution_in_fewer_iterations():
+    """W-cycle (two recursive calls, Sec. 2.2) as preconditioner: same solution, no more iterations."""
+    w = small_heterogeneous((32, 32), levels=4, abl_cells=3)
+    pb = _problem(w)
+    H = oracle.assemble(pb, 0.0)
+    act = oracle.active_mask(pb)
+    b = w.rhs.ravel() * act
+    xd = _direct(H, b, act)
+    its = {}
+    for cyc in ("V", "W"):
+        hier = oracle.Hierarchy(pb, 4, 0.5, 0.3, coarse="smooth", coarse_sweeps=8, coarse_damping=0.8, cycle=cyc)
+        x, its[cyc], res = oracle.fgmres(lambda v: H @ v, lambda v: oracle.vcycle(hier, v), b, tol=1e-10,
+                                         restart=20, max_iter=400)
+        assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+    assert its["W"] <= its["V"]

@@ -40,6 +40,7 @@ class Workload:
     coarse: str = "dense"          # "dense" or "smooth"
     coarse_sweeps: int = 0
     coarse_damping: float = 1.0
+    cycle: str = "V"               # "V" or "W"
     extra: dict = field(default_factory=dict)
 
     @property

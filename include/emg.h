@@ -78,6 +78,9 @@ typedef struct {
   int32_t cycle_type;       /* EMG_CYCLE_V (one recursive call, Alg. 1) or EMG_CYCLE_W (two calls,
                                the second from the first one's result; Sec. 2.2, the paper's 2D
                                choice); the coarsest level is solved once per visit */
+  double level_alpha[EMG_MAX_LEVELS]; /* shift of level l's cycle operator when > 0, else alpha (the
+                               paper raises the shift as levels are added, Sec. 5.2; a deeper shift on
+                               the coarsest level keeps its smoothing iteration convergent) */
 } emg_params;
 
 typedef struct {

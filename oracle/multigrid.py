@@ -40,7 +40,9 @@ class Hierarchy:
         self.pbs = [pb]
         for _ in range(levels - 1):
             self.pbs.append(coarsen(self.pbs[-1]))
-        self.H = [assemble(p, alpha) for p in self.pbs]
+        # alpha: one shift for every level, or one per level (a deeper shift on coarse levels)
+        self.alphas = list(alpha) if np.ndim(alpha) else [float(alpha)] * levels
+        self.H = [assemble(p, self.alphas[l]) for l, p in enumerate(self.pbs)]
         self.R = [restriction(self.pbs[l], self.pbs[l + 1]) for l in range(levels - 1)]
         self.P = [prolongation(self.pbs[l], self.pbs[l + 1]) for l in range(levels - 1)]
         self.idx = [cell_dofs(p) for p in self.pbs]

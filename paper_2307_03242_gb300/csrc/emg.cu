@@ -130,6 +130,8 @@ double default_damping(int levels) {
   }
 }
 
+double level_alpha(const emg_params& p, int l) { return p.level_alpha[l] > 0.0 ? p.level_alpha[l] : p.alpha; }
+
 template <typename T>
 Grid<T> make_grid(const emg_ctx& c, int l, bool shifted, const void* mu, const void* rho, const void* cp) {
   const Level& L = c.lv[l];
@@ -143,7 +145,7 @@ Grid<T> make_grid(const emg_ctx& c, int l, bool shifted, const void* mu, const v
   g.beta = (T)p.beta;
   g.sm = (T)((1.0 - p.beta) / (2.0 * c.dim));
   g.w2 = (T)(p.omega * p.omega);
-  g.att = (T)(p.gamma + (shifted ? p.alpha : 0.0));
+  g.att = (T)(p.gamma + (shifted ? level_alpha(p, l) : 0.0));
   g.ablL = (T)(p.abl_cells > 0 ? p.abl_cells * p.h : 0.0);
   g.ablG = (T)p.abl_gamma_max;
   g.Lx = (T)(p.n[0] * p.h);
@@ -649,7 +651,7 @@ void outer_apply(emg_ctx& c, const void* x, bool x32, const cx<double>* b, doubl
     g.t1 = to_f2(0.25 * (1.0 - c.prm.beta));
     g.beta = to_f2(c.prm.beta);
     g.sm = to_f2(0.25 * (1.0 - c.prm.beta));
-    g.alpha = to_f2(shifted ? c.prm.alpha : 0.0);
+    g.alpha = to_f2(shifted ? level_alpha(c.prm, 0) : 0.0);
     g.mu = c.ff_mu.as<df::f2>();
     g.mun = c.ff_mun.as<df::f2>();
     g.cp = c.ff_cp.as<df::f2>();
@@ -821,6 +823,8 @@ void check_params(const emg_params* p) {
   if (!(p->h > 0) || !std::isfinite(p->h)) raise(EMG_ERR_INVALID, "h must be positive");
   if (!std::isfinite(p->omega) || !std::isfinite(p->gamma) || !std::isfinite(p->alpha) || !std::isfinite(p->beta))
     raise(EMG_ERR_INVALID, "non-finite omega/gamma/alpha/beta");
+  for (int l = 0; l < EMG_MAX_LEVELS; ++l)
+    if (!std::isfinite(p->level_alpha[l])) raise(EMG_ERR_INVALID, "non-finite level_alpha");
   if (p->abl_cells < 0) raise(EMG_ERR_INVALID, "abl_cells must be >= 0");
   if (p->nu_pre < 0 || p->nu_post < 0) raise(EMG_ERR_INVALID, "negative smoothing count");
   if (p->cycle_precision != 32 && p->cycle_precision != 64) raise(EMG_ERR_INVALID, "cycle_precision must be 32 or 64");

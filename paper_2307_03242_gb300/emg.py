@@ -36,7 +36,8 @@ class _Params(ctypes.Structure):
                 ("levels", ctypes.c_int32), ("nu_pre", ctypes.c_int32), ("nu_post", ctypes.c_int32),
                 ("damping", ctypes.c_double * MAX_LEVELS), ("coarse_solver", ctypes.c_int32),
                 ("coarse_sweeps", ctypes.c_int32), ("coarse_damping", ctypes.c_double),
-                ("cycle_precision", ctypes.c_int32), ("cycle_type", ctypes.c_int32)]
+                ("cycle_precision", ctypes.c_int32), ("cycle_type", ctypes.c_int32),
+                ("level_alpha", ctypes.c_double * MAX_LEVELS)]
 
 
 class _Stats(ctypes.Structure):
@@ -105,6 +106,7 @@ class Params:
     coarse_damping: float = 0.8
     cycle_precision: int = 32
     cycle_type: int = CYCLE_V
+    level_alpha: object = None       # per-level shift list (entries <= 0 mean `alpha`)
 
     def to_c(self) -> _Params:
         p = _Params()
@@ -120,6 +122,9 @@ class Params:
         p.coarse_solver, p.coarse_sweeps = int(self.coarse_solver), int(self.coarse_sweeps)
         p.coarse_damping, p.cycle_precision = float(self.coarse_damping), int(self.cycle_precision)
         p.cycle_type = int(self.cycle_type)
+        la = list(self.level_alpha) if self.level_alpha is not None else []
+        for l in range(MAX_LEVELS):
+            p.level_alpha[l] = float(la[l]) if l < len(la) else 0.0
         return p
 
 
@@ -129,7 +134,8 @@ def params_from_workload(w, cycle_precision=32, **over) -> Params:
               nu_post=w.nu_post, damping=w.damping,
               coarse_solver=COARSE_DENSE if w.coarse == "dense" else COARSE_SMOOTH,
               coarse_sweeps=w.coarse_sweeps, coarse_damping=w.coarse_damping, cycle_precision=cycle_precision,
-              cycle_type=CYCLE_W if getattr(w, "cycle", "V") == "W" else CYCLE_V)
+              cycle_type=CYCLE_W if getattr(w, "cycle", "V") == "W" else CYCLE_V,
+              level_alpha=w.level_alphas() if hasattr(w, "level_alphas") else None)
     kw.update(over)
     return Params(**kw)
 

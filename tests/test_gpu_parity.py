@@ -148,6 +148,7 @@ def test_wcycle_matches_oracle(case, prec):
     levels = 3 if case == "2d" else 2
     w = small_heterogeneous(c["n"], seed=5, levels=levels, abl_cells=c["abl_cells"], sigma_cells=2.0)
     w.cycle, w.coarse, w.coarse_sweeps, w.coarse_damping = "W", "smooth", 3, 0.8
+    w.alpha_coarsest = 1.1  # per-level shift on the coarsest level
     pb = oracle_problem(w)
     hier = oracle_hierarchy(w, pb)
     s = gpu_solver(w, prec)

@@ -41,11 +41,19 @@ class Workload:
     coarse_sweeps: int = 0
     coarse_damping: float = 1.0
     cycle: str = "V"               # "V" or "W"
+    alpha_coarsest: float = 0.0    # shift of the coarsest level (0: alpha)
     extra: dict = field(default_factory=dict)
 
     @property
     def dim(self) -> int:
         return len(self.n)
+
+    def level_alphas(self):
+        """Shift per level: alpha everywhere, alpha_coarsest (if set) on the coarsest level."""
+        a = [self.alpha] * self.levels
+        if self.alpha_coarsest > 0:
+            a[-1] = self.alpha_coarsest
+        return a
 
 
 def lame_from_velocity(vp: np.ndarray, vs: np.ndarray, rho: np.ndarray):
@@ -100,7 +108,8 @@ def config_c1_homogeneous(n: int = 128) -> Workload:
 def config_c2_random2d(n: int = 2048, seed: int = 0, levels: int = 5, source_depth: int = 32) -> Workload:
     """2D smooth random medium: Vp in [1.5, 4.5] (Gaussian filter sigma 32 cells, correlation
     length ~64 cells), Vs = Vp/sqrt(3), rho = 0.31 Vp^0.25; 10 points per minimum shear
-    wavelength; point force in the depth component u2 at (n/2, depth 32)."""
+    wavelength; point force in the depth component u2 at (n/2, depth 32). Solver: W(2,2) on 5
+    levels, shift 0.5, shift 1.0 on the coarsest level (16 red-black sweeps)."""
     shape = (n, n)
     sigma = 32.0 * n / 2048.0 if n < 2048 else 32.0
     vp = gaussian_random_velocity(shape, seed, sigma_cells=sigma)
@@ -112,7 +121,7 @@ def config_c2_random2d(n: int = 2048, seed: int = 0, levels: int = 5, source_dep
     rhs = point_source((n, n), 1, (n // 2, min(source_depth, n - 1)))
     return Workload("c2_random_2d_%d" % n, (n, n), h, lam, mu, rho, omega, rhs,
                     levels=levels, alpha=0.5, damping=0.2, abl_cells=20, coarse="smooth",
-                    coarse_sweeps=16, coarse_damping=0.8)
+                    coarse_sweeps=16, coarse_damping=0.8, cycle="W", alpha_coarsest=1.0)
 
 
 def config_c3_layered3d(n: int = 256, source=(128, 128, 24), levels: int = 4) -> Workload:
@@ -136,7 +145,7 @@ def config_c3_layered3d(n: int = 256, source=(128, 128, 24), levels: int = 4) ->
     rhs = point_source((n, n, n), 2, src)
     return Workload("c3_layered_3d_%d" % n, (n, n, n), h, lam, mu, rho, omega, rhs,
                     levels=levels, alpha=0.4, damping=0.25, abl_cells=max(2, int(round(20 * s))),
-                    coarse="smooth", coarse_sweeps=16, coarse_damping=0.8)
+                    coarse="smooth", coarse_sweeps=16, coarse_damping=0.8, cycle="W", alpha_coarsest=1.0)
 
 
 def small_heterogeneous(n, seed: int = 1, sigma_cells: float = 2.0, abl_cells: int = 2,

@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--damping", type=float, default=None)
     ap.add_argument("--cycle", default=None, choices=["V", "W"])
     ap.add_argument("--coarse-sweeps", type=int, default=None)
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="run this many FGMRES iterations of the configured solve and exit without timing "
+                         "(target for ncu launch lists and kernel captures)")
+    ap.add_argument("--profile-precision", type=int, default=32, choices=[32, 64])
     return ap.parse_args()
 
 
@@ -181,10 +185,27 @@ def config_json(w, args):
         "parallelism": "replicas" if args.gpus > 1 else "single"}
 
 
+def run_profile(args):
+    """K FGMRES iterations of the configured solve, no timing (for ncu)."""
+    import torch
+    from paper_2307_03242_gb300 import emg
+    w = workload(args.config, args)
+    b = torch.from_numpy(w.rhs.astype(np.complex128)).cuda()
+    s = emg.Solver(emg.params_from_workload(w, args.profile_precision), w.lam, w.mu, w.rho)
+    x = torch.zeros_like(b)
+    st = s.solve(b, x, tol=w.tol, max_iter=args.profile_iters, restart=args.restart)
+    torch.cuda.synchronize()
+    s.close()
+    print(json.dumps({"profile_iters": st["iterations"], "rel_residual": st["rel_residual"], "workload": w.name}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile_iters > 0:
+        run_profile(args)
         return
     import torch
     import torch.distributed as dist

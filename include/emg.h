@@ -164,6 +164,32 @@ emg_status emg_profile(emg_handle h, int enable);
 emg_status emg_profile_read(emg_handle h, int kernel_class, double* total_ms, int64_t* launches,
                             double* bytes);
 
+/* ---- Allocation-free smoothing. ----
+ * No counterpart in the paper: this entry point exists for callers that cannot allocate device
+ * memory -- code that runs while a stream is being captured into a CUDA graph and must not
+ * allocate, applications whose device memory is fully reserved by their own allocator, and hosts
+ * that embed a fixed-size smoother. It performs exactly what emg_smooth does on level 0 of the
+ * hierarchy that `params` describes (2D, FP32 cycle vectors): `sweeps` red-black full Vanka
+ * sweeps on H_s x = b, with the damping damping[0] (or the default by depth) and the shift
+ * level_alpha[0] (or alpha). It needs no handle and allocates nothing: the caller passes the
+ * finest-level material in FP32 -- mu, rho and cp = 1/(lambda + mu), n[0]*n[1] device values each
+ * -- and b, x (FP32 cycle vectors, device, 16-byte aligned); the only work array, the ping-pong
+ * copy of the displacement components, is a fixed file-scope device array of
+ * 2 * EMG_NOALLOC_MAX_CELLS complex FP32 values (4 MiB), which every GPU that loads the library
+ * holds until the process exits.
+ * Limits and behaviour: grids with more than EMG_NOALLOC_MAX_CELLS cells, dim != 2 or
+ * cycle_precision != 32 are rejected with EMG_ERR_INVALID before any work. The first call on a
+ * device looks up the device address of the work array (cudaGetSymbolAddress); make that first
+ * call before any stream capture. Every call shares the one work array: calls that overlap on the
+ * GPU (different streams, or other threads) race and give wrong results; serialise them. The
+ * array keeps the last call's contents; nothing in it needs to start at zero, because each
+ * sweep's first half writes every entry before the second half reads it. Enqueued on
+ * cuda_stream (NULL: the legacy default stream); returns without synchronising. */
+#define EMG_NOALLOC_MAX_CELLS 262144
+emg_status emg_smooth_noalloc(const emg_params* params, const float* mu, const float* rho,
+                              const float* cp, const void* b, void* x, int sweeps,
+                              void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

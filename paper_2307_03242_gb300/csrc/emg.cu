@@ -862,6 +862,8 @@ void check_ptr(const void* p, const char* what) {
   catch (const std::bad_alloc&) { g_err = "host allocation failed"; return EMG_ERR_NOMEM; } \
   catch (const std::exception& e) { g_err = e.what(); return EMG_ERR_INVALID; }
 
+void emg_set_last_error(const std::string& msg) { g_err = msg; }
+
 extern "C" {
 
 const char* emg_last_error(void) { return g_err.c_str(); }

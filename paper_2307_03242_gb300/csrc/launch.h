@@ -4,6 +4,11 @@
 #include "emg_types.cuh"
 #include "apply_ff2d.cuh"
 
+#include <string>
+
+// Sets the message that emg_last_error() returns on the calling thread.
+void emg_set_last_error(const std::string& msg);
+
 template <typename T, typename TI>
 void launch_apply2(const Grid<T>& g, const cx<TI>* x, const cx<T>* b, T bscale, cx<T>* y, cudaStream_t st);
 template <typename T>

@@ -23,16 +23,13 @@ __device__ __align__(256) cx<float> g_noalloc_alt[2 * EMG_NOALLOC_MAX_CELLS];
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void* g_alt_addr[kMaxDevices] = {nullptr};
-thread_local std::string g_noalloc_err;
 
 emg_status fail(emg_status s, const std::string& m) {
-  g_noalloc_err = m;
+  emg_set_last_error(m);  // reported by emg_last_error()
   return s;
 }
 
 }  // namespace
-
-extern "C" const char* emg_noalloc_last_error(void) { return g_noalloc_err.c_str(); }
 
 extern "C" emg_status emg_smooth_noalloc(const emg_params* p, const float* mu, const float* rho, const float* cp,
                                          const void* b, void* x, int sweeps, void* cuda_stream) {

@@ -65,6 +65,7 @@ def _load():
         "emg_coarse_solve": [vp, vp, vp],
         "emg_profile": [vp, i32],
         "emg_profile_read": [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(dbl)],
+        "emg_smooth_noalloc": [ctypes.POINTER(_Params), vp, vp, vp, vp, vp, i32, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -78,7 +79,8 @@ def _load():
 LIB = _load()
 EXPORTED = ["emg_create", "emg_destroy", "emg_last_error", "emg_apply", "emg_vcycle", "emg_solve", "emg_solve_host",
             "emg_level_info", "emg_smooth", "emg_residual_restrict", "emg_prolong_correct", "emg_coarse_solve",
-            "emg_profile", "emg_profile_read"]
+            "emg_profile", "emg_profile_read", "emg_smooth_noalloc"]
+NOALLOC_MAX_CELLS = 262144
 
 
 def _check(status, allow=(0,)):
@@ -151,6 +153,22 @@ def _ptr(t, dtype, numel, what):
     if t.numel() != numel:
         raise ValueError("%s has %d elements, expected %d" % (what, t.numel(), numel))
     return ctypes.c_void_p(t.data_ptr())
+
+
+def smooth_noalloc(params: Params, mu, rho, cp, b, x, sweeps, stream=None):
+    """emg_smooth_noalloc: red-black Vanka sweeps on level 0 without a handle and without any
+    allocation (see include/emg.h). mu, rho, cp: float32 CUDA tensors of n[0]*n[1] cells;
+    b, x: complex64 CUDA tensors of 3*n[0]*n[1] entries."""
+    import torch
+    ncell = int(np.prod(params.n))
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    c = params.to_c()
+    _check(LIB.emg_smooth_noalloc(ctypes.byref(c), _ptr(mu, torch.float32, ncell, "mu"),
+                                  _ptr(rho, torch.float32, ncell, "rho"), _ptr(cp, torch.float32, ncell, "cp"),
+                                  _ptr(b, torch.complex64, 3 * ncell, "b"), _ptr(x, torch.complex64, 3 * ncell, "x"),
+                                  int(sweeps), ctypes.c_void_p(stream.cuda_stream)))
+    return x
 
 
 class Solver:

@@ -31,7 +31,7 @@ METRIC = "time-to-1e-6 rel. residual & V-cycle HBM GB/s: FP32-precond vs plain F
 # Iteration count used to extrapolate the oracle's per-iteration time to a full solve in the
 # reference arm (which runs no GPU code): FGMRES(20) iterations of the FP64 solve of the 2048^2
 # configuration (the FP64 GPU solve reproduces the oracle's count within +-1 in the parity tests).
-REF_ITERS = {"c2": 300, "c1": 97, "c3": 60}
+REF_ITERS = {"c2": 226, "c1": 97, "c3": 60}
 
 
 def parse():
@@ -65,6 +65,39 @@ def workload(name, args=None):
             if v is not None:
                 setattr(w, k, v)
     return w
+
+
+# Sources of the dominant kernel (the finest-level 2D red-black half-sweep); the DRAM traffic
+# recorded from an ncu capture is reported only while these files are unchanged.
+HOT_KERNEL_SOURCES = ["paper_2307_03242_gb300/csrc/vanka2d_fast.cuh",
+                      "paper_2307_03242_gb300/csrc/kernels2d.cuh", "paper_2307_03242_gb300/csrc/stencil2d.cuh",
+                      "paper_2307_03242_gb300/csrc/emg_types.cuh"]
+HOT_KERNEL_PROFILE = "profiles/vanka2d_c2_2048.txt"
+
+
+def hot_kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in HOT_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """(bytes per launch, ncu kernel time) from the committed ncu summary, if it matches the source."""
+    try:
+        vals = {}
+        with open(os.path.join(ROOT, HOT_KERNEL_PROFILE)) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    vals[k.strip()] = v.strip()
+        if vals.get("source_hash") != hot_kernel_hash():
+            return None
+        return float(vals["dram_bytes_per_launch"])
+    except Exception:
+        return None
 
 
 def load_peaks():
@@ -139,8 +172,11 @@ def oracle_sample(w, iters=3, crop=512):
     pb = Problem(n, w.h, w.omega, w.gamma, w.beta, w.lam[sl], w.mu[sl], w.rho[sl], abl_length=w.abl_cells * w.h,
                  abl_gamma_max=w.abl_gamma_max)
     coarse = "dense" if (c >> (lv - 1)) ** d * (d + 1) <= 4096 and w.coarse == "dense" else "smooth"
-    hier = oracle.Hierarchy(pb, lv, w.alpha, w.damping, nu_pre=w.nu_pre, nu_post=w.nu_post, coarse=coarse,
-                            coarse_sweeps=max(w.coarse_sweeps, 16), coarse_damping=w.coarse_damping)
+    alphas = [w.alpha] * lv
+    if w.alpha_coarsest > 0:
+        alphas[-1] = w.alpha_coarsest
+    hier = oracle.Hierarchy(pb, lv, alphas, w.damping, nu_pre=w.nu_pre, nu_post=w.nu_post, coarse=coarse,
+                            coarse_sweeps=max(w.coarse_sweeps, 1), coarse_damping=w.coarse_damping, cycle=w.cycle)
     H = oracle.assemble(pb, 0.0)
     b = np.zeros(H.shape[0], complex)
     b[oracle.active_mask(pb)] = 1.0
@@ -149,9 +185,9 @@ def oracle_sample(w, iters=3, crop=512):
                               max_iter=iters)
     dt = (time.perf_counter() - t0) / its
     scale = float(np.prod(w.n)) / float(np.prod(n))
-    desc = ("oracle FGMRES(20)+V(%d,%d) iterations on a %s crop of the same medium (%d levels), %d iterations "
-            "timed, per-iteration time scaled by the cell ratio %.1f" % (w.nu_pre, w.nu_post, "x".join(map(str, n)),
-                                                                         lv, its, scale))
+    desc = ("oracle FGMRES(20)+%s(%d,%d) iterations on a %s crop of the same medium (%d levels), %d iterations "
+            "timed, per-iteration time scaled by the cell ratio %.1f" % (w.cycle, w.nu_pre, w.nu_post,
+                                                                         "x".join(map(str, n)), lv, its, scale))
     threads = int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or os.cpu_count()
     return dt * scale, desc, threads
 
@@ -322,7 +358,7 @@ def main():
                       "frac_of_hbm": v_gbs / peak},
            "roofline": {"kernel": "vanka half-sweep (finest level, FP32)", "bound": "hbm", "achieved": achieved,
                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                        "frac": achieved / peak if achieved else None, "traffic": None,
+                        "frac": achieved / peak if achieved else None, "traffic": recorded_traffic(),
                         "launches": prof["launches"], "avg_launch_ms": prof["ms"] / max(prof["launches"], 1),
                         "bytes_per_launch": prof["bytes"] / max(prof["launches"], 1)},
            "fine_level_ms_per_solve": dict({"smooth": prof["ms"] / args.steps},

@@ -55,7 +55,7 @@ typedef enum {
 } emg_status;
 
 enum { EMG_COARSE_DENSE = 0, EMG_COARSE_SMOOTH = 1 };
-enum { EMG_CYCLE_V = 0, EMG_CYCLE_W = 1 };
+enum { EMG_CYCLE_V = 0, EMG_CYCLE_W = 1, EMG_CYCLE_K = 2 };
 
 /* Solver description. All lengths in the same unit as h. */
 typedef struct {
@@ -75,9 +75,11 @@ typedef struct {
   int32_t coarse_sweeps;    /* red-black sweeps on the coarsest level for EMG_COARSE_SMOOTH */
   double coarse_damping;    /* Vanka damping on the coarsest level for EMG_COARSE_SMOOTH */
   int32_t cycle_precision;  /* 32: FP32 cycle with FP64 outer solve; 64: everything in FP64 */
-  int32_t cycle_type;       /* EMG_CYCLE_V (one recursive call, Alg. 1) or EMG_CYCLE_W (two calls,
-                               the second from the first one's result; Sec. 2.2, the paper's 2D
-                               choice); the coarsest level is solved once per visit */
+  int32_t cycle_type;       /* EMG_CYCLE_V (one recursive call, Alg. 1), EMG_CYCLE_W (two calls, the
+                               second from the first one's result; Sec. 2.2, the paper's 2D choice)
+                               or EMG_CYCLE_K (the two calls precondition two GCR steps for the coarse
+                               problem; Sec. 2.2, the paper's 3D choice); the coarsest level is
+                               solved once per visit */
   double level_alpha[EMG_MAX_LEVELS]; /* shift of level l's cycle operator when > 0, else alpha (the
                                paper raises the shift as levels are added, Sec. 5.2; a deeper shift on
                                the coarsest level keeps its smoothing iteration convergent) */

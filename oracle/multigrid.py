@@ -1,7 +1,10 @@
 """Multigrid V-cycle on the shifted operator (oracle; test infrastructure only).
 
 Algorithm 1 (two-grid cycle) applied recursively (Section 2.2): one recursive call gives the
-V-cycle, two recursive calls (the second starting from the first one's result) the W-cycle: nu_1 pre-relaxations, residual restriction
+V-cycle, two recursive calls (the second starting from the first one's result) the W-cycle, and
+the K-cycle uses the two recursive calls as preconditioners of two steps of a flexible Krylov
+method for the coarse problem (Section 2.2, after Notay and Vassilevski; here generalised
+conjugate residuals, GCR(2), since the operator is not Hermitian): nu_1 pre-relaxations, residual restriction
 r_2h = R(q - A_h u), coarse problem, correction u += P e_2h, nu_2
 post-relaxations. The coarse operators are re-discretisations of the shifted
 operator (Remark 2.1 and Section 3.2: the same stencil on the 2h grid, with the
@@ -30,7 +33,8 @@ class Hierarchy:
                  nu_post: int = 2, coarse: str = "dense", coarse_sweeps: int = 0,
                  coarse_damping: float = 1.0, cycle: str = "V"):
         self.levels = levels
-        self.gamma_cycle = {"V": 1, "W": 2}[cycle]
+        self.cycle = cycle
+        self.gamma_cycle = {"V": 1, "W": 2, "K": 2}[cycle]
         self.alpha = alpha
         self.nu_pre, self.nu_post = nu_pre, nu_post
         self.coarse, self.coarse_sweeps, self.coarse_damping = coarse, coarse_sweeps, coarse_damping
@@ -80,10 +84,33 @@ def vcycle(hier: Hierarchy, b, x=None, level: int = 0):
     x = hier.smooth(level, b, x, hier.nu_pre, hier.w[level])
     r = b - H @ x
     bc = hier.R[level] @ r
-    ec = vcycle(hier, bc, None, level + 1)
-    for _ in range(hier.gamma_cycle - 1):
-        if level + 1 < hier.levels - 1:
-            ec = vcycle(hier, bc, ec, level + 1)
+    if hier.cycle == "K" and level + 1 < hier.levels - 1:
+        ec = kcycle_correction(hier, bc, level + 1)
+    else:
+        ec = vcycle(hier, bc, None, level + 1)
+        for _ in range(hier.gamma_cycle - 1):
+            if level + 1 < hier.levels - 1:
+                ec = vcycle(hier, bc, ec, level + 1)
     x = x + hier.P[level] @ ec
     x = hier.smooth(level, b, x, hier.nu_post, hier.w[level])
     return x
+
+
+def kcycle_correction(hier: Hierarchy, r, level: int):
+    """Two GCR steps for H_s e = r on `level`, each preconditioned by one recursive cycle:
+    z1 = B r, q1 = A z1, a1 = <q1, r>/<q1, q1>, r2 = r - a1 q1;
+    z2 = B r2, q2 = A z2, q2 -= (<q1, q2>/<q1, q1>) q1 (and z2 likewise), a2 = <q2, r2>/<q2, q2>;
+    e = a1 z1 + a2 z2 (<a, b> = sum conj(a) b)."""
+    A = hier.H[level]
+    z1 = vcycle(hier, r, None, level)
+    q1 = A @ z1
+    n1 = np.vdot(q1, q1).real
+    a1 = np.vdot(q1, r) / n1
+    r2 = r - a1 * q1
+    z2 = vcycle(hier, r2, None, level)
+    q2 = A @ z2
+    bt = np.vdot(q1, q2) / n1
+    q2 = q2 - bt * q1
+    z2 = z2 - bt * z1
+    a2 = np.vdot(q2, r2) / np.vdot(q2, q2).real
+    return a1 * z1 + a2 * z2

@@ -39,21 +39,21 @@ struct FineFF {
   const c2* m2;      // nx*ny u2 faces
 };
 
-__device__ __forceinline__ f2 ld(float v) { return {v, 0.f}; }
-__device__ __forceinline__ f2 ld(double v) { return df::split(v); }
-__device__ __forceinline__ f2 fneg(f2 a) { return {-a.hi, -a.lo}; }
+HD f2 ld(float v) { return {v, 0.f}; }
+HD f2 ld(double v) { return df::split(v); }
+HD f2 fneg(f2 a) { return {-a.hi, -a.lo}; }
 
 // float-float product / sum with normalisation (used for the few coefficient combinations)
-__device__ __forceinline__ f2 mul(f2 a, f2 b) {
+HD f2 mul(f2 a, f2 b) {
   float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
+  float e = std::fma(a.hi, b.hi, -p);
+  e = std::fma(a.hi, b.lo, e);
+  e = std::fma(a.lo, b.hi, e);
   f2 r;
   df::two_sum(p, e, r.hi, r.lo);
   return r;
 }
-__device__ __forceinline__ f2 add(f2 a, f2 b) {
+HD f2 add(f2 a, f2 b) {
   float s, t;
   df::two_sum(a.hi, b.hi, s, t);
   t += a.lo + b.lo;
@@ -65,12 +65,12 @@ __device__ __forceinline__ f2 add(f2 a, f2 b) {
 struct cacc {
   df::acc re, im;
   // += c * u (c real)
-  __device__ __forceinline__ void rterm(f2 c, f2 ur, f2 ui) {
+  HD void rterm(f2 c, f2 ur, f2 ui) {
     re.fma_ff(c, ur);
     im.fma_ff(c, ui);
   }
   // += m * u (m complex)
-  __device__ __forceinline__ void cterm(const c2& m, f2 ur, f2 ui) {
+  HD void cterm(const c2& m, f2 ur, f2 ui) {
     re.fma_ff(m.re, ur);
     re.fms_ff(m.im, ui);
     im.fma_ff(m.re, ui);

@@ -19,9 +19,11 @@
 
 #include "emg.h"
 #include "launch.h"
+#include "ff3_setup.h"
 #include "stencil2d.cuh"
 #include "stencil3d.cuh"
 #include "krylov_ff.cuh"
+#include "kcycle_kernels.cuh"
 #include "vector_kernels.cuh"
 
 namespace {
@@ -83,6 +85,8 @@ struct Level {
   std::vector<double> lam_h, mu_h, rho_h;  // host FP64 material (setup, dense coarse assembly)
   DBuf mu, rho, cp;                        // device material in the cycle precision
   DBuf b, x, alt;                          // cycle vectors: b, x hold dim+1 components, alt dim
+  DBuf abl_tab[3];                         // absorbing-layer attenuation per axis (cycle precision)
+  DBuf kz1, kz2, kq1, kq2, kr2, kpart, kcoef;  // K-cycle work vectors (levels 1 .. L-2)
 };
 
 }  // namespace
@@ -94,6 +98,7 @@ struct emg_ctx {
   std::vector<Level> lv;
   DBuf mu64, rho64, cp64;  // finest material in FP64 for the outer operator
   DBuf ff_mu, ff_mun, ff_cp, ff_m1, ff_m2;  // 2D: FP64 coefficients as float-float pairs
+  DBuf ff3_edge[3], ff3_m[3];              // 3D: edge mu per orientation, face masses
   DBuf cinv;               // dense inverse of the coarsest operator (cycle precision)
   int cn = 0;
   // Krylov workspace
@@ -154,12 +159,15 @@ Grid<T> make_grid(const emg_ctx& c, int l, bool shifted, const void* mu, const v
   g.mu = (const T*)mu;
   g.rho = (const T*)rho;
   g.cp = (const T*)cp;
+  g.abl_tab[0] = g.abl_tab[1] = g.abl_tab[2] = nullptr;
   return g;
 }
 
 template <typename T> Grid<T> level_grid(const emg_ctx& c, int l) {
   const Level& L = c.lv[l];
-  return make_grid<T>(c, l, true, L.mu.p, L.rho.p, L.cp.p);
+  Grid<T> g = make_grid<T>(c, l, true, L.mu.p, L.rho.p, L.cp.p);
+  for (int a = 0; a < c.dim; ++a) g.abl_tab[a] = L.abl_tab[a].as<const T>();
+  return g;
 }
 
 // ---------------------------------------------------------------- instrumentation
@@ -293,9 +301,66 @@ void coarse_solve(emg_ctx& c, const cx<T>* b, cx<T>* x) {
     kv::dense_gemv<T><<<(n + 7) / 8, 256, 0, c.st>>>(c.cinv.as<cx<T>>(), b, x, n);
     CKL();
   LAUNCHED(c);
+  } else if (c.dim == 2 && c.prm.coarse_sweeps > 0) {
+    Grid<T> g = level_grid<T>(c, l);
+    CK(launch_coarse_sweeps2<T>(g, b, x, c.lv[l].alt.as<cx<T>>(), c.prm.coarse_sweeps, (T)c.prm.coarse_damping, c.st));
+    LAUNCHED(c);
   } else {
     smooth<T>(c, l, b, x, c.prm.coarse_sweeps, c.prm.coarse_damping, true);
   }
+}
+
+template <typename T>
+void vcycle(emg_ctx& c, int l, const cx<T>* b, cx<T>* x, bool zero_guess);
+
+// coef (device) = <a, b> / <a, a> on level m
+template <typename T>
+void kcoef(emg_ctx& c, int m, const cx<T>* a, const cx<T>* b, double* coef) {
+  Level& M = c.lv[m];
+  const size_t n = (c.dim + 1) * M.ncell;
+  const int nblk = vec_blocks(c, n);
+  kc::dot_parts<T><<<nblk, kc::RT, 0, c.st>>>(a, b, n, M.kpart.as<double>());
+  CKL();
+  LAUNCHED(c);
+  kc::finalize_coef<<<1, kv::RP, 0, c.st>>>(M.kpart.as<double>(), nblk, coef);
+  CKL();
+  LAUNCHED(c);
+}
+
+template <typename T>
+void kaxpy(emg_ctx& c, size_t n, cx<T>* y, const cx<T>* x0, const cx<T>* x, const double* coef, T sgn) {
+  kc::axpy_coef<T><<<vec_blocks(c, n), 256, 0, c.st>>>(y, x0, x, coef, sgn, n);
+  CKL();
+  LAUNCHED(c);
+}
+
+// K-cycle coarse correction on level m (1 <= m < L-1): two GCR steps for H_s e = r, each
+// preconditioned by one recursive cycle on level m; e is written to e_out.
+template <typename T>
+void kcycle_correction(emg_ctx& c, int m, const cx<T>* r, cx<T>* e_out) {
+  Level& M = c.lv[m];
+  const size_t n = (c.dim + 1) * M.ncell;
+  cx<T>* z1 = M.kz1.as<cx<T>>();
+  cx<T>* z2 = M.kz2.as<cx<T>>();
+  cx<T>* q1 = M.kq1.as<cx<T>>();
+  cx<T>* q2 = M.kq2.as<cx<T>>();
+  cx<T>* r2 = M.kr2.as<cx<T>>();
+  double* cf = M.kcoef.as<double>();  // cf[0..1] a1, cf[2..3] beta, cf[4..5] a2
+  Grid<T> g = level_grid<T>(c, m);
+  vcycle<T>(c, m, r, z1, true);
+  launch_apply<T>(c, g, z1, false, nullptr, T(0), q1);
+  LAUNCHED(c);
+  kcoef<T>(c, m, q1, r, cf);
+  kaxpy<T>(c, n, r2, r, q1, cf, T(-1));      // r2 = r - a1 q1
+  kaxpy<T>(c, n, e_out, nullptr, z1, cf, T(1));  // e = a1 z1
+  vcycle<T>(c, m, r2, z2, true);
+  launch_apply<T>(c, g, z2, false, nullptr, T(0), q2);
+  LAUNCHED(c);
+  kcoef<T>(c, m, q1, q2, cf + 2);
+  kaxpy<T>(c, n, q2, q2, q1, cf + 2, T(-1));  // q2 -= beta q1
+  kaxpy<T>(c, n, z2, z2, z1, cf + 2, T(-1));  // z2 -= beta z1
+  kcoef<T>(c, m, q2, r2, cf + 4);
+  kaxpy<T>(c, n, e_out, e_out, z2, cf + 4, T(1));  // e += a2 z2
 }
 
 template <typename T>
@@ -309,8 +374,12 @@ void vcycle(emg_ctx& c, int l, const cx<T>* b, cx<T>* x, bool zero_guess) {
   if (zero_guess && c.prm.nu_pre == 0) CK(cudaMemsetAsync(x, 0, (c.dim + 1) * L.ncell * sizeof(cx<T>), c.st));
   smooth<T>(c, l, b, x, c.prm.nu_pre, L.w, zero_guess);
   residual_restrict<T>(c, l, b, x, C.b.as<cx<T>>(), false);
-  vcycle<T>(c, l + 1, C.b.as<cx<T>>(), C.x.as<cx<T>>(), true);
-  if (c.prm.cycle_type == EMG_CYCLE_W && l + 1 < c.L - 1) vcycle<T>(c, l + 1, C.b.as<cx<T>>(), C.x.as<cx<T>>(), false);
+  if (c.prm.cycle_type == EMG_CYCLE_K && l + 1 < c.L - 1) {
+    kcycle_correction<T>(c, l + 1, C.b.as<cx<T>>(), C.x.as<cx<T>>());
+  } else {
+    vcycle<T>(c, l + 1, C.b.as<cx<T>>(), C.x.as<cx<T>>(), true);
+    if (c.prm.cycle_type == EMG_CYCLE_W && l + 1 < c.L - 1) vcycle<T>(c, l + 1, C.b.as<cx<T>>(), C.x.as<cx<T>>(), false);
+  }
   prolong_correct<T>(c, l, C.x.as<cx<T>>(), x);
   smooth<T>(c, l, b, x, c.prm.nu_post, L.w, false);
 }
@@ -499,6 +568,45 @@ void build_ff2(emg_ctx& c) {
   up(c.ff_m2, m2.data(), m2.size() * sizeof(ff2::c2));
 }
 
+// FP64 coefficients of the finest 3D operator as float-float pairs for ff3::apply.
+void build_ff3(emg_ctx& c) {
+  const Level& F = c.lv[0];
+  const emg_params& p = c.prm;
+  ff3::HostFF3 o;
+  const double L[3] = {p.n[0] * p.h, p.n[1] * p.h, p.n[2] * p.h};
+  ff3::build_host(o, F.n[0], F.n[1], F.n[2], F.h, F.lam_h.data(), F.mu_h.data(), F.rho_h.data(), p.omega, p.gamma,
+                  p.abl_cells > 0 ? p.abl_cells * p.h : 0.0, p.abl_gamma_max, L);
+  auto up = [&](DBuf& d, const void* src, size_t bytes) {
+    d.alloc(bytes);
+    CK(cudaMemcpy(d.p, src, bytes, cudaMemcpyHostToDevice));
+  };
+  up(c.ff_mu, o.mu.data(), o.mu.size() * sizeof(df::f2));
+  up(c.ff_cp, o.cp.data(), o.cp.size() * sizeof(df::f2));
+  for (int r = 0; r < 3; ++r) {
+    up(c.ff3_edge[r], o.edge[r].data(), o.edge[r].size() * sizeof(df::f2));
+    up(c.ff3_m[r], o.m[r].data(), o.m[r].size() * sizeof(ff2::c2));
+  }
+}
+
+// Absorbing-layer attenuation along axis a of a level, at k h and (k + 1/2) h for k = -2 .. n+2.
+template <typename T>
+void upload_abl_tables(emg_ctx& c, Level& L) {
+  const emg_params& p = c.prm;
+  const double Lab = p.abl_cells > 0 ? p.abl_cells * p.h : 0.0;
+  for (int a = 0; a < c.dim; ++a) {
+    const int n = L.n[a];
+    const double X = p.n[a] * p.h;
+    std::vector<T> tab(2 * (n + 5));
+    for (int k = -2; k <= n + 2; ++k)
+      for (int half = 0; half < 2; ++half) {
+        const double x = (k + 0.5 * half) * L.h;
+        tab[2 * (k + 2) + half] = (T)(Lab > 0.0 ? p.abl_gamma_max * abl_axis(x, Lab, X) / (Lab * Lab) : 0.0);
+      }
+    L.abl_tab[a].alloc(tab.size() * sizeof(T));
+    CK(cudaMemcpy(L.abl_tab[a].p, tab.data(), tab.size() * sizeof(T), cudaMemcpyHostToDevice));
+  }
+}
+
 template <typename T>
 void build(emg_ctx& c) {
   const int d = c.dim;
@@ -506,9 +614,20 @@ void build(emg_ctx& c) {
     Level& L = c.lv[l];
     if (l > 0) coarsen_material(c, c.lv[l - 1], L);
     upload_material<T>(c, L);
+    upload_abl_tables<T>(c, L);
     L.b.alloc((d + 1) * L.ncell * sizeof(cx<T>));
     L.x.alloc((d + 1) * L.ncell * sizeof(cx<T>));
     L.alt.alloc(d * L.ncell * sizeof(cx<T>));
+    if (c.prm.cycle_type == EMG_CYCLE_K && l >= 1 && l < c.L - 1) {
+      const size_t vb = (d + 1) * L.ncell * sizeof(cx<T>);
+      L.kz1.alloc(vb);
+      L.kz2.alloc(vb);
+      L.kq1.alloc(vb);
+      L.kq2.alloc(vb);
+      L.kr2.alloc(vb);
+      L.kpart.alloc((size_t)vec_blocks(c, (d + 1) * L.ncell) * 3 * sizeof(double));
+      L.kcoef.alloc(8 * sizeof(double));
+    }
     CK(cudaMemset(L.b.p, 0, L.b.bytes));
     CK(cudaMemset(L.x.p, 0, L.x.bytes));
     CK(cudaMemset(L.alt.p, 0, L.alt.bytes));
@@ -524,6 +643,7 @@ void build(emg_ctx& c) {
   CK(cudaMemcpy(c.rho64.p, F.rho_h.data(), F.ncell * 8, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c.cp64.p, cp.data(), F.ncell * 8, cudaMemcpyHostToDevice));
   if (c.dim == 2) build_ff2(c);
+  else build_ff3(c);
   if (c.prm.coarse_solver == EMG_COARSE_DENSE) {
     std::vector<std::complex<double>> A, Ainv;
     std::vector<int> act;
@@ -588,11 +708,19 @@ void mdots(emg_ctx& c, bool ff, const cx<double>* V, size_t ldv, int cnt, const 
         case 5: launch_mdot<5>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
         case 6: launch_mdot<6>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
         case 7: launch_mdot<7>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
-        default: launch_mdot<8>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
+        case 8: launch_mdot<8>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
+        case 9: launch_mdot<9>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
+        case 10: launch_mdot<10>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
+        case 11: launch_mdot<11>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
+        case 12: launch_mdot<12>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
+        case 13: launch_mdot<13>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
+        case 14: launch_mdot<14>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
+        case 15: launch_mdot<15>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
+        default: launch_mdot<16>(c, ff, V + s * ldv, ldv, w, n, part, nblk); break;
       }
     }
     const int nr = 2 * nv + 1;
-    kv::reduce_parts<<<1, 128, 0, c.st>>>(part, nblk, nr, red + off);
+    kv::reduce_parts<<<nr, kv::RP, 0, c.st>>>(part, nblk, nr, red + off);
     CKL();
     LAUNCHED(c);
     chunks.push_back({s, nv});
@@ -626,7 +754,7 @@ double update_scale(emg_ctx& c, cx<double>* w, const cx<double>* V, size_t ldv,
     CKL();
     LAUNCHED(c);
   }
-  kv::reduce_parts<<<1, 128, 0, c.st>>>(c.part.as<double>(), nblk, 1, c.red.as<double>());
+  kv::reduce_parts<<<1, kv::RP, 0, c.st>>>(c.part.as<double>(), nblk, 1, c.red.as<double>());
   CKL();
   LAUNCHED(c);
   CK(cudaMemcpyAsync(c.hred, c.red.p, sizeof(double), cudaMemcpyDeviceToHost, c.st));
@@ -663,9 +791,18 @@ void outer_apply(emg_ctx& c, const void* x, bool x32, const cx<double>* b, doubl
     LAUNCHED(c);
     return;
   }
-  Grid<double> g = make_grid<double>(c, 0, shifted, c.mu64.p, c.rho64.p, c.cp64.p);
-  ProfScope ps(c, EMG_K_APPLY64, 0, (double)c.lv[0].ncell * ((c.dim + 1) * ((x32 ? 8.0 : 16.0) + cw + (b ? cw : 0.0)) + 3 * 8.0));
-  launch_apply<double>(c, g, x, x32, b, bscale, y);
+  // 3D: float-float evaluation from precomputed FP64 coefficients
+  ProfScope ps(c, EMG_K_APPLY64, 0, (double)c.lv[0].ncell * (4 * ((x32 ? 8.0 : 16.0) + cw + (b ? cw : 0.0)) + 2 * 8.0 + 3 * 8.0 + 3 * 16.0));
+  const Level& F = c.lv[0];
+  const df::f2* ed[3] = {c.ff3_edge[0].as<df::f2>(), c.ff3_edge[1].as<df::f2>(), c.ff3_edge[2].as<df::f2>()};
+  const ff2::c2* ms[3] = {c.ff3_m[0].as<ff2::c2>(), c.ff3_m[1].as<ff2::c2>(), c.ff3_m[2].as<ff2::c2>()};
+  ff3::HostFF3 none;
+  ff3::FineFF3 g = ff3::make(none, c.ff_mu.as<df::f2>(), c.ff_cp.as<df::f2>(), ed, ms, F.n[0], F.n[1], F.n[2], F.h,
+                             c.prm.beta, shifted ? level_alpha(c.prm, 0) : 0.0);
+  if (x32) launch_apply_ff3<float>(g, (const cx<float>*)x, b, bscale, y, c.st);
+  else launch_apply_ff3<double>(g, (const cx<double>*)x, b, bscale, y, c.st);
+  CKL();
+  LAUNCHED(c);
 }
 
 template <typename T>
@@ -828,7 +965,8 @@ void check_params(const emg_params* p) {
   if (p->abl_cells < 0) raise(EMG_ERR_INVALID, "abl_cells must be >= 0");
   if (p->nu_pre < 0 || p->nu_post < 0) raise(EMG_ERR_INVALID, "negative smoothing count");
   if (p->cycle_precision != 32 && p->cycle_precision != 64) raise(EMG_ERR_INVALID, "cycle_precision must be 32 or 64");
-  if (p->cycle_type != EMG_CYCLE_V && p->cycle_type != EMG_CYCLE_W) raise(EMG_ERR_INVALID, "unknown cycle_type");
+  if (p->cycle_type != EMG_CYCLE_V && p->cycle_type != EMG_CYCLE_W && p->cycle_type != EMG_CYCLE_K)
+    raise(EMG_ERR_INVALID, "unknown cycle_type");
   if (p->coarse_solver != EMG_COARSE_DENSE && p->coarse_solver != EMG_COARSE_SMOOTH)
     raise(EMG_ERR_INVALID, "unknown coarse_solver");
   if (p->coarse_solver == EMG_COARSE_SMOOTH && p->coarse_sweeps < 1 && p->levels > 0)

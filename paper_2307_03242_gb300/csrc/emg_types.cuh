@@ -12,6 +12,23 @@ struct alignas(2 * sizeof(T)) cx {
 };
 
 template <typename T> HD cx<T> mkc(T r, T i) { cx<T> z; z.re = r; z.im = i; return z; }
+// read-only loads of complex values (one 8- or 16-byte load)
+HD cx<float> ldg(const cx<float>* p) {
+#ifdef __CUDA_ARCH__
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return mkc<float>(v.x, v.y);
+#else
+  return *p;
+#endif
+}
+HD cx<double> ldg(const cx<double>* p) {
+#ifdef __CUDA_ARCH__
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  return mkc<double>(v.x, v.y);
+#else
+  return *p;
+#endif
+}
 template <typename T> HD cx<T> czero() { return mkc<T>(T(0), T(0)); }
 template <typename T> HD cx<T> operator+(cx<T> a, cx<T> b) { return mkc<T>(a.re + b.re, a.im + b.im); }
 template <typename T> HD cx<T> operator-(cx<T> a, cx<T> b) { return mkc<T>(a.re - b.re, a.im - b.im); }
@@ -30,6 +47,15 @@ template <typename T, typename S> HD cx<T> ccast(cx<S> a) { return mkc<T>((T)a.r
 
 HD int iclamp(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+// Read-only load: the texture/read-only path on the device, a plain load on the host.
+template <typename T> HD T ldg(const T* p) {
+#ifdef __CUDA_ARCH__
+  return __ldg(p);
+#else
+  return *p;
+#endif
+}
+
 // Geometry and coefficients of one level, by value in every kernel launch.
 //   t0 = (1+beta)/2, t1 = (1-beta)/4: weights of the beta-spread derivative across one axis
 //     (2D, Eq. 3.5: beta*[-1 1] + (1-beta)/4*[1 2 1] x [-1 1]);
@@ -47,6 +73,10 @@ struct Grid {
   const T* mu;              // cell-centred mu
   const T* rho;             // cell-centred rho
   const T* cp;              // cell-centred 1/(lambda + mu)
+  // Absorbing-layer attenuation along each axis, tabulated per level (nullptr: evaluate the
+  // profile): tab[a][2*(k+2)] at the lattice position k h, tab[a][2*(k+2)+1] at (k+1/2) h, for
+  // k = -2 .. n_a+2 (the values outside the domain only ever multiply zero displacements).
+  const T* abl_tab[3];
 };
 
 // Absorbing-layer attenuation at a physical position: gamma_max * sum_a (delta_a / L)^2.

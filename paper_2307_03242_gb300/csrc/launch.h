@@ -3,6 +3,7 @@
 #pragma once
 #include "emg_types.cuh"
 #include "apply_ff2d.cuh"
+#include "apply_ff3d.cuh"
 
 #include <string>
 
@@ -33,4 +34,12 @@ void launch_prolong3(const cx<T>* e, cx<T>* x, const int n[3], const int nc[3], 
 
 template <typename TI>
 void launch_apply_ff2(const ff2::FineFF& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y,
+                      cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_coarse_sweeps2(const Grid<T>& g, const cx<T>* b, cx<T>* x, cx<T>* alt, int sweeps, T w,
+                                  cudaStream_t st);
+
+template <typename TI>
+void launch_apply_ff3(const ff3::FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y,
                       cudaStream_t st);

@@ -1,5 +1,6 @@
 // 2D kernel launchers (explicit instantiations for the FP32 and FP64 cycles and the FP64 apply).
-#include "vanka2d_fast.cuh"
+#include "restrict2d_fast.cuh"
+#include "coarse2d_coop.cuh"
 #include "launch.h"
 #include "apply_ff2d.cuh"
 
@@ -19,7 +20,10 @@ void launch_vanka2(const Grid<T>& g, const cx<T>* b, const cx<T>* uin, cx<T>* uo
 template <typename T>
 void launch_restrict2(const Grid<T>& g, const cx<T>* b, const cx<T>* x, cx<T>* bc, const int nc[3], int zero_x,
                       cudaStream_t st) {
-  k2::restrict_residual<T><<<g2(nc[0], nc[1]), dim3(k2::BX, k2::BY), 0, st>>>(g, b, x, bc, nc[0], nc[1], zero_x);
+  if (zero_x)
+    k2::restrict_residual<T><<<g2(nc[0], nc[1]), dim3(k2::BX, k2::BY), 0, st>>>(g, b, x, bc, nc[0], nc[1], zero_x);
+  else
+    k2::restrict_fast<T><<<g2(nc[0], nc[1]), dim3(k2::BX, k2::BY), 0, st>>>(g, b, x, bc, nc[0], nc[1]);
 }
 template <typename T>
 void launch_prolong2(const cx<T>* e, cx<T>* x, const int n[3], const int nc[3], cudaStream_t st) {
@@ -43,3 +47,28 @@ void launch_apply_ff2(const ff2::FineFF& g, const cx<TI>* x, const cx<double>* b
 }
 template void launch_apply_ff2<float>(const ff2::FineFF&, const cx<float>*, const cx<double>*, double, cx<double>*, cudaStream_t);
 template void launch_apply_ff2<double>(const ff2::FineFF&, const cx<double>*, const cx<double>*, double, cx<double>*, cudaStream_t);
+
+// All sweeps of one coarsest-level solve in one cooperative launch (x starts from zero).
+template <typename T>
+cudaError_t launch_coarse_sweeps2(const Grid<T>& g, const cx<T>* b, cx<T>* x, cx<T>* alt, int sweeps, T w,
+                                  cudaStream_t st) {
+  const long long items = (long long)((g.nx + 1) / 2) * g.ny;
+  const int threads = k2::BX * k2::BY;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2::coarse_sweeps_coop<T>, threads, 0);
+  long long want = (items + threads - 1) / threads;
+  long long cap = (long long)sms * (per_sm > 0 ? per_sm : 1);
+  int blocks = (int)(want < cap ? want : cap);
+  Grid<T> gg = g;
+  const cx<T>* bb = b;
+  cx<T>* xx = x;
+  cx<T>* aa = alt;
+  int sw = sweeps;
+  T ww = w;
+  void* args[] = {&gg, &bb, &xx, &aa, &sw, &ww};
+  return cudaLaunchCooperativeKernel((const void*)k2::coarse_sweeps_coop<T>, dim3(blocks), dim3(k2::BX, k2::BY), args, 0, st);
+}
+template cudaError_t launch_coarse_sweeps2<float>(const Grid<float>&, const cx<float>*, cx<float>*, cx<float>*, int, float, cudaStream_t);
+template cudaError_t launch_coarse_sweeps2<double>(const Grid<double>&, const cx<double>*, cx<double>*, cx<double>*, int, double, cudaStream_t);

@@ -1,5 +1,5 @@
 // 3D kernel launchers (explicit instantiations for the FP32 and FP64 cycles and the FP64 apply).
-#include "kernels3d.cuh"
+#include "vanka3d_tile.cuh"
 #include "launch.h"
 
 namespace {
@@ -16,7 +16,18 @@ void launch_apply3(const Grid<T>& g, const cx<TI>* x, const cx<T>* b, T bscale, 
 template <typename T>
 void launch_vanka3(const Grid<T>& g, const cx<T>* b, const cx<T>* uin, cx<T>* uout, cx<T>* p, int colour, T w,
                    int zero_in, cudaStream_t st) {
-  k3::vanka<T><<<g3((g.nx + 1) / 2, g.ny, g.nz), b3(), 0, st>>>(g, b, uin, uout, p, colour, w, zero_in);
+  if (g.nx >= 16 && g.ny >= 8 && g.nz >= 4) {
+    static bool attr_set[2] = {false, false};
+    const size_t smem = sizeof(k3t::Tile<T>);
+    if (!attr_set[sizeof(T) == 8]) {
+      cudaFuncSetAttribute(k3t::vanka_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr_set[sizeof(T) == 8] = true;
+    }
+    dim3 grid((g.nx + k3t::TX - 1) / k3t::TX, (g.ny + k3t::TY - 1) / k3t::TY, (g.nz + k3t::TZ - 1) / k3t::TZ);
+    k3t::vanka_tile<T><<<grid, k3t::NT, smem, st>>>(g, b, uin, uout, p, colour, w, zero_in);
+  } else {
+    k3::vanka<T><<<g3((g.nx + 1) / 2, g.ny, g.nz), b3(), 0, st>>>(g, b, uin, uout, p, colour, w, zero_in);
+  }
 }
 template <typename T>
 void launch_restrict3(const Grid<T>& g, const cx<T>* b, const cx<T>* x, cx<T>* bc, const int nc[3], int zero_x,
@@ -37,3 +48,12 @@ template void launch_apply3<double, float>(const Grid<double>&, const cx<float>*
   template void launch_prolong3<T>(const cx<T>*, cx<T>*, const int*, const int*, cudaStream_t);
 INST(float)
 INST(double)
+
+template <typename TI>
+void launch_apply_ff3(const ff3::FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y,
+                      cudaStream_t st) {
+  dim3 grid((g.nx + ff3::BX - 1) / ff3::BX, (g.ny + ff3::BY - 1) / ff3::BY, (g.nz + ff3::BZ - 1) / ff3::BZ);
+  ff3::apply<TI><<<grid, dim3(ff3::BX, ff3::BY, ff3::BZ), 0, st>>>(g, x, b, bscale, y);
+}
+template void launch_apply_ff3<float>(const ff3::FineFF3&, const cx<float>*, const cx<double>*, double, cx<double>*, cudaStream_t);
+template void launch_apply_ff3<double>(const ff3::FineFF3&, const cx<double>*, const cx<double>*, double, cx<double>*, cudaStream_t);

@@ -14,12 +14,17 @@ template <typename T> HD T abl_term(const Grid<T>& g, T x, T L) {
   return g.ablL > T(0) ? g.ablG * abl_axis(x, g.ablL, L) / (g.ablL * g.ablL) : T(0);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(BX * BY, sizeof(T) == 4 ? 2 : 1) vanka_fast(Grid<T> g, const cx<T>* __restrict__ b,
-                                                        const cx<T>* __restrict__ uin, cx<T>* __restrict__ uout,
-                                                        cx<T>* p, int colour, T w, int zero_in) {
-  const int ip = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
+// ABL attenuation along axis a at lattice position k (half = 0) or k + 1/2 (half = 1).
+template <typename T> HD T abl_at(const Grid<T>& g, int a, int k, int half, T L) {
+  if (g.abl_tab[a]) return ldg(g.abl_tab[a] + 2 * (k + 2) + half);
+  return abl_term(g, (T(k) + (half ? T(0.5) : T(0))) * g.h, L);
+}
+
+// INTERIOR: the caller guarantees 2 <= i <= nx-3 and 2 <= j <= ny-3 (no bounds checks, no clamps,
+// no excluded faces).
+template <typename T, bool INTERIOR = false>
+HD void vanka_cell(const Grid<T>& g, const cx<T>* __restrict__ b, const cx<T>* __restrict__ uin,
+                   cx<T>* __restrict__ uout, cx<T>* p, int colour, T w, int zero_in, int ip, int j) {
   const int nx = g.nx, ny = g.ny;
   if (j >= ny) return;
   const int par = (colour + j) & 1;
@@ -34,15 +39,19 @@ __global__ void __launch_bounds__(BX * BY, sizeof(T) == 4 ? 2 : 1) vanka_fast(Gr
   const cx<T>* u2 = uin + N;
   const T t0 = T(0.5) * (T(1) + g.beta), t1 = T(0.25) * (T(1) - g.beta);
   const T ih = g.ih, ih2 = g.ih * g.ih;
-  const bool exW = i == 0, exE = i + 1 >= nx, exS = j == 0, exN = j + 1 >= ny;
+  const bool exW = INTERIOR ? false : i == 0, exE = INTERIOR ? false : i + 1 >= nx;
+  const bool exS = INTERIOR ? false : j == 0, exN = INTERIOR ? false : j + 1 >= ny;
 
   // ---- material: mu on the 3x3 cells around (i, j); rho on the cells the face masses need
-  auto cl = [&](int ii, int jj) -> size_t { return (size_t)iclamp(jj, 0, ny - 1) * nx + iclamp(ii, 0, nx - 1); };
+  auto cl = [&](int ii, int jj) -> size_t {
+    if (INTERIOR) return (size_t)jj * nx + ii;
+    return (size_t)iclamp(jj, 0, ny - 1) * nx + iclamp(ii, 0, nx - 1);
+  };
   T mu9[3][3];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) mu9[r][c] = g.mu[cl(i - 1 + c, j - 1 + r)];
+    for (int c = 0; c < 3; ++c) mu9[r][c] = ldg(g.mu + cl(i - 1 + c, j - 1 + r));
   // node mu at (X, Y), X in {i, i+1}, Y in {j, j+1}: mean of cells (X-1..X, Y-1..Y)
   const T mnA = T(0.25) * (mu9[0][0] + mu9[0][1] + mu9[1][0] + mu9[1][1]);  // (i,   j)
   const T mnB = T(0.25) * (mu9[0][1] + mu9[0][2] + mu9[1][1] + mu9[1][2]);  // (i+1, j)
@@ -50,24 +59,24 @@ __global__ void __launch_bounds__(BX * BY, sizeof(T) == 4 ? 2 : 1) vanka_fast(Gr
   const T mnD = T(0.25) * (mu9[1][1] + mu9[1][2] + mu9[2][1] + mu9[2][2]);  // (i+1, j+1)
   T R0[5], Rm[3], Rp[3];
 #pragma unroll
-  for (int c = 0; c < 5; ++c) R0[c] = g.rho[cl(i - 2 + c, j)];
+  for (int c = 0; c < 5; ++c) R0[c] = ldg(g.rho + cl(i - 2 + c, j));
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    Rm[c] = g.rho[cl(i - 1 + c, j - 1)];
-    Rp[c] = g.rho[cl(i - 1 + c, j + 1)];
+    Rm[c] = ldg(g.rho + cl(i - 1 + c, j - 1));
+    Rp[c] = ldg(g.rho + cl(i - 1 + c, j + 1));
   }
-  const T rS2 = g.rho[cl(i, j - 2)], rN2 = g.rho[cl(i, j + 2)];
+  const T rS2 = ldg(g.rho + cl(i, j - 2)), rN2 = ldg(g.rho + cl(i, j + 2));
   // absorbing layer, separable in x and y: gx at face (X h) and cell ((X+1/2) h) positions, etc.
   T gxf[4], gxc[3], gyf[4], gyc[3];
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    gxf[c] = abl_term(g, T(i - 1 + c) * g.h, g.Lx);
-    gyf[c] = abl_term(g, T(j - 1 + c) * g.h, g.Ly);
+    gxf[c] = abl_at(g, 0, i - 1 + c, 0, g.Lx);
+    gyf[c] = abl_at(g, 1, j - 1 + c, 0, g.Ly);
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    gxc[c] = abl_term(g, (T(i - 1 + c) + T(0.5)) * g.h, g.Lx);
-    gyc[c] = abl_term(g, (T(j - 1 + c) + T(0.5)) * g.h, g.Ly);
+    gxc[c] = abl_at(g, 0, i - 1 + c, 1, g.Lx);
+    gyc[c] = abl_at(g, 1, j - 1 + c, 1, g.Ly);
   }
   const T w2 = g.w2, att = g.att;
   // m1 at u1 face (X, Y) with rho_f = (rho(X-1,Y) + rho(X,Y))/2; offsets relative to (i, j)
@@ -93,8 +102,8 @@ __global__ void __launch_bounds__(BX * BY, sizeof(T) == 4 ? 2 : 1) vanka_fast(Gr
     r[4] = b[2 * N + k];
   } else {
     const cx<T> pC = p[k];
-    const cx<T> pW = i > 0 ? p[k - 1] : z, pE = i + 1 < nx ? p[k + 1] : z;
-    const cx<T> pS = j > 0 ? p[k - nx] : z, pN = j + 1 < ny ? p[k + nx] : z;
+    const cx<T> pW = (INTERIOR || i > 0) ? p[k - 1] : z, pE = (INTERIOR || i + 1 < nx) ? p[k + 1] : z;
+    const cx<T> pS = (INTERIOR || j > 0) ? p[k - nx] : z, pN = (INTERIOR || j + 1 < ny) ? p[k + nx] : z;
     cx<T> G1m, G1c, G1p;  // d1 u1 at cells i-1, i, i+1 (needed by the p row too)
     {
       // u1 on faces i-1..i+2, rows j-1..j+1
@@ -105,7 +114,7 @@ __global__ void __launch_bounds__(BX * BY, sizeof(T) == 4 ? 2 : 1) vanka_fast(Gr
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const int ii = i - 1 + c;
-          A[rr][c] = (ii >= 1 && ii < nx && jj >= 0 && jj < ny) ? u1[(size_t)jj * nx + ii] : z;
+          A[rr][c] = (INTERIOR || (ii >= 1 && ii < nx && jj >= 0 && jj < ny)) ? ldg(u1 + (size_t)jj * nx + ii) : z;
         }
       }
       auto g1 = [&](int c) { return ih * (t1 * ((A[0][c + 1] - A[0][c]) + (A[2][c + 1] - A[2][c])) + t0 * (A[1][c + 1] - A[1][c])); };
@@ -142,7 +151,7 @@ __global__ void __launch_bounds__(BX * BY, sizeof(T) == 4 ? 2 : 1) vanka_fast(Gr
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const int ii = i - 1 + c;
-          B[rr][c] = (jj >= 1 && jj < ny && ii >= 0 && ii < nx) ? u2[(size_t)jj * nx + ii] : z;
+          B[rr][c] = (INTERIOR || (jj >= 1 && jj < ny && ii >= 0 && ii < nx)) ? ldg(u2 + (size_t)jj * nx + ii) : z;
         }
       }
       // d2 u2 at cell (i, Y): rows ry+1 (Y+1) and ry (Y)
@@ -169,7 +178,7 @@ __global__ void __launch_bounds__(BX * BY, sizeof(T) == 4 ? 2 : 1) vanka_fast(Gr
       r[2] = exS ? z : b[N + k] - (lapS - massS + ih * (pC - pS));
       r[3] = exN ? z : b[N + k + nx] - (lapN - massN + ih * (pN - pC));
     }
-    r[4] = b[2 * N + k] - (G1c + H2c + g.cp[k] * pC);
+    r[4] = b[2 * N + k] - (G1c + H2c + ldg(g.cp + k) * pC);
   }
 
   // ---- the cell's block (same entries as s2::block_u1 / block_u2)
@@ -184,7 +193,7 @@ __global__ void __launch_bounds__(BX * BY, sizeof(T) == 4 ? 2 : 1) vanka_fast(Gr
   a2[1] = mkc<T>(ih2 * (-t0 * mc + t1 * (mnA + mnB)), T(0)) - g.sm * mN;
   a2[2] = mkc<T>(ih2 * (-t0 * mc + t1 * (mnC + mnD)), T(0)) - g.sm * mS;
   const bool ex[4] = {exW, exE, exS, exN};
-  cell_solve(a1, a2, ex, ih, t0, g.cp[k], r, d);
+  cell_solve(a1, a2, ex, ih, t0, ldg(g.cp + k), r, d);
 
   cx<T>* o1 = uout;
   cx<T>* o2 = uout + N;
@@ -201,8 +210,22 @@ __global__ void __launch_bounds__(BX * BY, sizeof(T) == 4 ? 2 : 1) vanka_fast(Gr
     if (!exN) o2[k + nx] = u2[k + nx] + w * d[3];
     p[k] = p[k] + w * d[4];
   }
-  if (i == 1) o1[k - 1] = z;
-  if (j == 1) o2[k - nx] = z;
+  if (!INTERIOR && i == 1) o1[k - 1] = z;
+  if (!INTERIOR && j == 1) o2[k - nx] = z;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX * BY, sizeof(T) == 4 ? 2 : 1) vanka_fast(Grid<T> g, const cx<T>* __restrict__ b,
+                                                                             const cx<T>* __restrict__ uin,
+                                                                             cx<T>* __restrict__ uout, cx<T>* p, int colour,
+                                                                             T w, int zero_in) {
+  const int ip = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int i = 2 * ip + ((colour + j) & 1);
+  if (!zero_in && i >= 2 && i + 3 <= g.nx && j >= 2 && j + 3 <= g.ny)
+    vanka_cell<T, true>(g, b, uin, uout, p, colour, w, zero_in, ip, j);
+  else
+    vanka_cell<T, false>(g, b, uin, uout, p, colour, w, zero_in, ip, j);
 }
 
 }  // namespace k2

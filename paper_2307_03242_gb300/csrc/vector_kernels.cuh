@@ -6,7 +6,7 @@
 namespace kv {
 
 constexpr int RT = 256;           // threads per reduction block
-constexpr int MAXV = 8;           // vectors per multi-dot pass
+constexpr int MAXV = 16;          // vectors per multi-dot pass
 
 template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -71,12 +71,22 @@ __global__ void __launch_bounds__(RT) update_norm(cx<double>* __restrict__ w, co
   block_reduce_store<1>(acc, part);
 }
 
-// Sum per-block partials column-wise (fixed order): out[r] = sum_b part[b*nr + r].
-__global__ void reduce_parts(const double* __restrict__ part, int nblk, int nr, double* __restrict__ out) {
-  for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * nr + r];
-    out[r] = s;
+// Sum per-block partials column-wise: out[r] = sum_b part[b*nr + r]. One block per column; each
+// thread sums a fixed strided subset, then a fixed tree combines them (deterministic).
+constexpr int RP = 256;
+__global__ void __launch_bounds__(RP) reduce_parts(const double* __restrict__ part, int nblk, int nr,
+                                                   double* __restrict__ out) {
+  const int r = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += RP) s += part[(size_t)b * nr + r];
+  __shared__ double sh[RP / 32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < RP / 32 ? sh[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) out[r] = v;
   }
 }
 

@@ -15,7 +15,7 @@ import numpy as np
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libemg.so")
 MAX_LEVELS = 10
 COARSE_DENSE, COARSE_SMOOTH = 0, 1
-CYCLE_V, CYCLE_W = 0, 1
+CYCLE_V, CYCLE_W, CYCLE_K = 0, 1, 2
 K_SMOOTH, K_RESTRICT, K_PROLONG, K_APPLY64, K_KRYLOV = range(5)
 K_ALL = 5
 
@@ -136,7 +136,7 @@ def params_from_workload(w, cycle_precision=32, **over) -> Params:
               nu_post=w.nu_post, damping=w.damping,
               coarse_solver=COARSE_DENSE if w.coarse == "dense" else COARSE_SMOOTH,
               coarse_sweeps=w.coarse_sweeps, coarse_damping=w.coarse_damping, cycle_precision=cycle_precision,
-              cycle_type=CYCLE_W if getattr(w, "cycle", "V") == "W" else CYCLE_V,
+              cycle_type={"V": CYCLE_V, "W": CYCLE_W, "K": CYCLE_K}[getattr(w, "cycle", "V")],
               level_alpha=w.level_alphas() if hasattr(w, "level_alphas") else None)
     kw.update(over)
     return Params(**kw)

@@ -142,12 +142,13 @@ def test_vcycle_matches_oracle(case, prec, coarse):
 
 @pytest.mark.parametrize("case", ["2d", "3d"])
 @pytest.mark.parametrize("prec", [64, 32])
-def test_wcycle_matches_oracle(case, prec):
-    """W-cycle (two recursive calls, Sec. 2.2) with a smoothed coarsest level."""
+@pytest.mark.parametrize("cycle", ["W", "K"])
+def test_wcycle_and_kcycle_match_oracle(case, prec, cycle):
+    """W-cycle (two recursive calls) and K-cycle (the two calls precondition two GCR steps of the
+    coarse problem), Sec. 2.2, with a smoothed coarsest level."""
     c = dict(CASES[case])
-    levels = 3 if case == "2d" else 2
-    w = small_heterogeneous(c["n"], seed=5, levels=levels, abl_cells=c["abl_cells"], sigma_cells=2.0)
-    w.cycle, w.coarse, w.coarse_sweeps, w.coarse_damping = "W", "smooth", 3, 0.8
+    w = small_heterogeneous(c["n"], seed=5, levels=3, abl_cells=c["abl_cells"], sigma_cells=2.0)
+    w.cycle, w.coarse, w.coarse_sweeps, w.coarse_damping = cycle, "smooth", 3, 0.8
     w.alpha_coarsest = 1.1  # per-level shift on the coarsest level
     pb = oracle_problem(w)
     hier = oracle_hierarchy(w, pb)

@@ -195,3 +195,28 @@ def test_wcycle_converges_to_dense_direct_solution_in_fewer_iterations():
                                          restart=20, max_iter=400)
         assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
     assert its["W"] <= its["V"]
+
+
+def test_kcycle_gcr_steps_minimise_the_coarse_residual_and_converge():
+    """K-cycle (Sec. 2.2): the GCR(2) correction leaves a residual orthogonal to both search
+    directions A z1, A z2, and the preconditioned solve converges to the direct solution."""
+    from oracle.multigrid import kcycle_correction
+    w = small_heterogeneous((32, 32), levels=4, abl_cells=3)
+    pb = _problem(w)
+    hier = oracle.Hierarchy(pb, 4, 0.5, 0.3, coarse="smooth", coarse_sweeps=8, coarse_damping=0.8, cycle="K")
+    rng = np.random.default_rng(8)
+    act = oracle.active_mask(hier.pbs[1])
+    r = (rng.standard_normal(act.size) + 1j * rng.standard_normal(act.size)) * act
+    e = kcycle_correction(hier, r, 1)
+    A = hier.H[1]
+    res = r - A @ e
+    z1 = oracle.vcycle(hier, r, None, 1)
+    q1 = A @ z1
+    assert abs(np.vdot(q1, res)) <= 1e-10 * np.linalg.norm(q1) * np.linalg.norm(r)
+    assert np.linalg.norm(res) <= np.linalg.norm(r - (np.vdot(q1, r) / np.vdot(q1, q1)) * q1) * (1 + 1e-12)
+    H = oracle.assemble(pb, 0.0)
+    b = w.rhs.ravel() * oracle.active_mask(pb)
+    xd = _direct(H, b, oracle.active_mask(pb))
+    x, its, res2 = oracle.fgmres(lambda v: H @ v, lambda v: oracle.vcycle(hier, v), b, tol=1e-10, restart=20,
+                                 max_iter=300)
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)

@@ -29,9 +29,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time-to-1e-6 rel. residual & V-cycle HBM GB/s: FP32-precond vs plain FP64, 1 GB300"
 # Iteration count used to extrapolate the oracle's per-iteration time to a full solve in the
-# reference arm (which runs no GPU code): FGMRES(20) iterations of the FP64 solve of the 2048^2
-# configuration (the FP64 GPU solve reproduces the oracle's count within +-1 in the parity tests).
-REF_ITERS = {"c2": 226, "c1": 97, "c3": 60}
+# reference arm (which runs no GPU code): iterations of the FP64 solve of each configuration with
+# its own FGMRES restart (the FP64 GPU solve reproduces the oracle's count within +-1 in the
+# parity tests).
+REF_ITERS = {"c2": 232, "c1": 97, "c3": 193}
 
 
 def parse():
@@ -41,13 +42,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="emg", choices=["emg", "reference"])
     ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3"])
-    ap.add_argument("--restart", type=int, default=20)
+    ap.add_argument("--restart", type=int, default=None, help="FGMRES restart length (default: the workload's)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed plain-FP64 solves (after 1 warm-up)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--levels", type=int, default=None)
     ap.add_argument("--alpha", type=float, default=None)
     ap.add_argument("--damping", type=float, default=None)
-    ap.add_argument("--cycle", default=None, choices=["V", "W"])
+    ap.add_argument("--cycle", default=None, choices=["V", "W", "K"])
     ap.add_argument("--coarse-sweeps", type=int, default=None)
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="run this many FGMRES iterations of the configured solve and exit without timing "
@@ -60,10 +61,11 @@ def workload(name, args=None):
     from workloads import config_c1_homogeneous, config_c2_random2d, config_c3_layered3d
     w = {"c1": config_c1_homogeneous, "c2": config_c2_random2d, "c3": config_c3_layered3d}[name]()
     if args is not None:
-        for k in ("levels", "alpha", "damping", "cycle", "coarse_sweeps"):
+        for k in ("levels", "alpha", "damping", "cycle", "coarse_sweeps", "restart"):
             v = getattr(args, k, None)
             if v is not None:
                 setattr(w, k, v)
+        args.restart = w.restart
     return w
 
 
@@ -181,12 +183,12 @@ def oracle_sample(w, iters=3, crop=512):
     b = np.zeros(H.shape[0], complex)
     b[oracle.active_mask(pb)] = 1.0
     t0 = time.perf_counter()
-    _, its, _ = oracle.fgmres(lambda v: H @ v, lambda v: oracle.vcycle(hier, v), b, tol=1e-30, restart=20,
+    _, its, _ = oracle.fgmres(lambda v: H @ v, lambda v: oracle.vcycle(hier, v), b, tol=1e-30, restart=w.restart,
                               max_iter=iters)
     dt = (time.perf_counter() - t0) / its
     scale = float(np.prod(w.n)) / float(np.prod(n))
-    desc = ("oracle FGMRES(20)+%s(%d,%d) iterations on a %s crop of the same medium (%d levels), %d iterations "
-            "timed, per-iteration time scaled by the cell ratio %.1f" % (w.cycle, w.nu_pre, w.nu_post,
+    desc = ("oracle FGMRES(%d)+%s(%d,%d) iterations on a %s crop of the same medium (%d levels), %d iterations "
+            "timed, per-iteration time scaled by the cell ratio %.1f" % (w.restart, w.cycle, w.nu_pre, w.nu_post,
                                                                          "x".join(map(str, n)), lv, its, scale))
     threads = int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or os.cpu_count()
     return dt * scale, desc, threads

@@ -29,6 +29,24 @@ HD cx<double> ldg(const cx<double>* p) {
   return *p;
 #endif
 }
+// L2-coherent loads (cached in L2 only): for values that other blocks of the same launch wrote
+// before a grid-wide barrier, which the read-only path may not see.
+HD cx<float> ldcg(const cx<float>* p) {
+#ifdef __CUDA_ARCH__
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return mkc<float>(v.x, v.y);
+#else
+  return *p;
+#endif
+}
+HD cx<double> ldcg(const cx<double>* p) {
+#ifdef __CUDA_ARCH__
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return mkc<double>(v.x, v.y);
+#else
+  return *p;
+#endif
+}
 template <typename T> HD cx<T> czero() { return mkc<T>(T(0), T(0)); }
 template <typename T> HD cx<T> operator+(cx<T> a, cx<T> b) { return mkc<T>(a.re + b.re, a.im + b.im); }
 template <typename T> HD cx<T> operator-(cx<T> a, cx<T> b) { return mkc<T>(a.re - b.re, a.im - b.im); }
@@ -77,6 +95,11 @@ struct Grid {
   // profile): tab[a][2*(k+2)] at the lattice position k h, tab[a][2*(k+2)+1] at (k+1/2) h, for
   // k = -2 .. n_a+2 (the values outside the domain only ever multiply zero displacements).
   const T* abl_tab[3];
+  // Per axis, the lattice range [zlo, zhi] on which the tabulated attenuation is exactly zero at
+  // both k h and (k+1/2) h (empty when zlo > zhi). Kernels whose whole window lies inside it take
+  // a variant that skips the absorbing-layer terms; the result is the same.
+  int zlo[3] = {1, 1, 1}, zhi[3] = {0, 0, 0};
+  HD bool abl_free(int a, int lo, int hi) const { return lo >= zlo[a] && hi <= zhi[a]; }
 };
 
 // Absorbing-layer attenuation at a physical position: gamma_max * sum_a (delta_a / L)^2.

@@ -1,5 +1,6 @@
-// 2D kernels of the V-cycle and of the FP64 operator apply. One thread per cell (apply,
-// prolongation), per cell of one colour (Vanka), or per coarse cell (restriction).
+// 2D building blocks: the Vanka cell solve, the operator apply (one thread per cell) and the
+// prolongation + correction (one thread per fine cell). The half-sweep is in vanka2d_fast.cuh,
+// the residual and restriction in residual2d_fast.cuh.
 #pragma once
 #include "stencil2d.cuh"
 
@@ -74,111 +75,6 @@ __global__ void __launch_bounds__(BX * BY) apply(Grid<T> g, const cx<TI>* __rest
   y[k] = y1;
   y[N + k] = y2;
   y[2 * N + k] = yp;
-}
-
-// One red-black half-sweep of colour `colour` (Jacobi within the colour): reads u from uin,
-// writes every u face to uout, updates p of the colour's cells in place (each such p is read
-// and written by its own thread only; the other pressures it reads belong to the other colour).
-template <typename T>
-__global__ void __launch_bounds__(BX * BY) vanka(Grid<T> g, const cx<T>* __restrict__ b,
-                                                const cx<T>* __restrict__ uin, cx<T>* __restrict__ uout,
-                                                cx<T>* p, int colour, T w, int zero_in) {
-  const int ip = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const int i = 2 * ip + ((colour + j) & 1);
-  if (j >= g.ny) return;
-  const int nx = g.nx, ny = g.ny;
-  if (zero_in) {  // the zero initial guess also holds for the other colour's pressure
-    const int io = 2 * ip + 1 - ((colour + j) & 1);
-    if (io < nx) p[(size_t)j * nx + io] = czero<T>();
-  }
-  if (i >= nx) return;
-  const size_t N = (size_t)nx * ny, k = (size_t)j * nx + i;
-  const cx<T>* u1 = uin;
-  const cx<T>* u2 = uin + N;
-  const T t0 = T(0.5) * (T(1) + g.beta);
-  bool ex[4] = {i == 0, i + 1 >= nx, j == 0, j + 1 >= ny};
-  cx<T> r[5];
-  if (zero_in) {  // x == 0: the residual is b
-    r[0] = ex[0] ? czero<T>() : b[k];
-    r[1] = ex[1] ? czero<T>() : b[k + 1];
-    r[2] = ex[2] ? czero<T>() : b[N + k];
-    r[3] = ex[3] ? czero<T>() : b[N + k + nx];
-    r[4] = b[2 * N + k];
-  } else {
-    r[0] = ex[0] ? czero<T>() : b[k] - s2::row_u1(u1, (const cx<T>*)p, g, i, j);
-    r[1] = ex[1] ? czero<T>() : b[k + 1] - s2::row_u1(u1, (const cx<T>*)p, g, i + 1, j);
-    r[2] = ex[2] ? czero<T>() : b[N + k] - s2::row_u2(u2, (const cx<T>*)p, g, i, j);
-    r[3] = ex[3] ? czero<T>() : b[N + k + nx] - s2::row_u2(u2, (const cx<T>*)p, g, i, j + 1);
-    r[4] = b[2 * N + k] - s2::row_p(u1, u2, (const cx<T>*)p, g, i, j);
-  }
-  cx<T> a1[4], a2[4], d[5];
-  s2::block_u1(g, i, j, a1[0], a1[1], a1[2], a1[3]);
-  s2::block_u2(g, i, j, a2[0], a2[1], a2[2], a2[3]);
-  cell_solve(a1, a2, ex, g.ih, t0, s2::mat(g.cp, g, i, j), r, d);
-  cx<T> z = czero<T>();
-  cx<T>* o1 = uout;
-  cx<T>* o2 = uout + N;
-  if (zero_in) {
-    o1[k] = ex[0] ? z : w * d[0];
-    if (!ex[1]) o1[k + 1] = w * d[1];
-    o2[k] = ex[2] ? z : w * d[2];
-    if (!ex[3]) o2[k + nx] = w * d[3];
-    p[k] = w * d[4];
-  } else {
-    o1[k] = ex[0] ? z : u1[k] + w * d[0];
-    if (!ex[1]) o1[k + 1] = u1[k + 1] + w * d[1];
-    o2[k] = ex[2] ? z : u2[k] + w * d[2];
-    if (!ex[3]) o2[k + nx] = u2[k + nx] + w * d[3];
-    p[k] = p[k] + w * d[4];
-  }
-  // boundary faces whose only cell has the other colour are written here
-  if (i == 1) o1[k - 1] = z;
-  if (j == 1) o2[k - nx] = z;
-}
-
-// Coarse right-hand side b_c = R (b - H_s x), one thread per coarse cell (I, J).
-// R_u1: [1 2 1]/4 along x1 (faces 2I-1, 2I, 2I+1) x [1 1]/2 along x2; R_u2 rotated; R_p: mean of
-// the four children (Eq. 2.11, 2.12).
-template <typename T>
-__global__ void __launch_bounds__(BX * BY) restrict_residual(Grid<T> g, const cx<T>* __restrict__ b,
-                                                            const cx<T>* __restrict__ x, cx<T>* __restrict__ bc,
-                                                            int nxc, int nyc, int zero_x) {
-  const int I = blockIdx.x * BX + threadIdx.x;
-  const int J = blockIdx.y * BY + threadIdx.y;
-  if (I >= nxc || J >= nyc) return;
-  const size_t N = (size_t)g.nx * g.ny, Nc = (size_t)nxc * nyc, kc = (size_t)J * nxc + I;
-  const cx<T>* u1 = x;
-  const cx<T>* u2 = x + N;
-  const cx<T>* p = x + 2 * N;
-  auto r1 = [&](int i, int j) -> cx<T> {
-    cx<T> v = b[(size_t)j * g.nx + i];
-    return zero_x ? v : v - s2::row_u1(u1, p, g, i, j);
-  };
-  auto r2 = [&](int i, int j) -> cx<T> {
-    cx<T> v = b[N + (size_t)j * g.nx + i];
-    return zero_x ? v : v - s2::row_u2(u2, p, g, i, j);
-  };
-  auto rp = [&](int i, int j) -> cx<T> {
-    cx<T> v = b[2 * N + (size_t)j * g.nx + i];
-    return zero_x ? v : v - s2::row_p(u1, u2, p, g, i, j);
-  };
-  const int i0 = 2 * I, j0 = 2 * J;
-  cx<T> c1 = czero<T>(), c2 = czero<T>();
-  if (I >= 1) {
-    for (int bb = 0; bb < 2; ++bb)
-      c1 = c1 + r1(i0 - 1, j0 + bb) + T(2) * r1(i0, j0 + bb) + r1(i0 + 1, j0 + bb);
-    c1 = T(0.125) * c1;
-  }
-  if (J >= 1) {
-    for (int a = 0; a < 2; ++a)
-      c2 = c2 + r2(i0 + a, j0 - 1) + T(2) * r2(i0 + a, j0) + r2(i0 + a, j0 + 1);
-    c2 = T(0.125) * c2;
-  }
-  cx<T> cpv = T(0.25) * (rp(i0, j0) + rp(i0 + 1, j0) + rp(i0, j0 + 1) + rp(i0 + 1, j0 + 1));
-  bc[kc] = c1;
-  bc[Nc + kc] = c2;
-  bc[2 * Nc + kc] = cpv;
 }
 
 // x += P e, one thread per fine cell (i, j). P_u1: linear along x1 ([1 2 1]/2 transposed) x

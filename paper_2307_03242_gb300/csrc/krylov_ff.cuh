@@ -10,25 +10,50 @@ namespace kf {
 using df::f2;
 constexpr int RT = kv::RT;
 
+// Elements per thread and loop iteration: their loads are issued together, so that enough bytes
+// are in flight per thread to cover the HBM latency (the vectors are 100s of MB).
+constexpr int UPD = 4;
+
 // part[blk][2i], [2i+1] = Re, Im of sum conj(V_i) w (i < NV); part[blk][2NV] = sum |w|^2.
 template <int NV>
 __global__ void __launch_bounds__(RT) mdot(const cx<double>* __restrict__ V, size_t ldv,
                                            const cx<double>* __restrict__ w, size_t n, double* part) {
+  constexpr int U = NV <= 2 ? 4 : (NV <= 6 ? 2 : 1);
   df::acc are[NV > 0 ? NV : 1], aim[NV > 0 ? NV : 1], ann;
-  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < n; e += (size_t)gridDim.x * RT) {
-    const cx<double> we = w[e];
-    const f2 wr = df::split(we.re), wi = df::split(we.im);
+  const size_t stride = (size_t)gridDim.x * RT;
+  const cx<double> z = czero<double>();
+  for (size_t e0 = (size_t)blockIdx.x * RT + threadIdx.x; e0 < n; e0 += U * stride) {
+    cx<double> we[U], a[U][NV > 0 ? NV : 1];
+    // every load is issued before any arithmetic (indices clamped into the vector); elements
+    // past the end are then replaced by zeros, which add nothing
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const cx<double> a = V[v * ldv + e];
-      const f2 ar = df::split(a.re), ai = df::split(a.im);
-      are[v].fma_ff(ar, wr);
-      are[v].fma_ff(ai, wi);
-      aim[v].fma_ff(ar, wi);
-      aim[v].fms_ff(ai, wr);
+    for (int u = 0; u < U; ++u) {
+      const size_t e = e0 + u * stride < n ? e0 + u * stride : n - 1;
+      we[u] = w[e];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) a[u][v] = V[v * ldv + e];
     }
-    ann.fma_ff(wr, wr);
-    ann.fma_ff(wi, wi);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (e0 + u * stride < n) continue;
+      we[u] = z;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) a[u][v] = z;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const f2 wr = df::split(we[u].re), wi = df::split(we[u].im);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const f2 ar = df::split(a[u][v].re), ai = df::split(a[u][v].im);
+        are[v].fma_ff(ar, wr);
+        are[v].fma_ff(ai, wi);
+        aim[v].fma_ff(ar, wi);
+        aim[v].fms_ff(ai, wr);
+      }
+      ann.fma_ff(wr, wr);
+      ann.fma_ff(wi, wi);
+    }
   }
   double acc[2 * NV + 1];
 #pragma unroll
@@ -54,29 +79,48 @@ __global__ void __launch_bounds__(RT) update_scale(cx<double>* __restrict__ w, c
                                                    size_t ldv, int cnt, Coefs h, f2 s, size_t n,
                                                    cx<float>* __restrict__ out32, double* part) {
   df::acc nn;
-  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < n; e += (size_t)gridDim.x * RT) {
-    const cx<double> we = w[e];
-    df::acc re, im;
-    re.add(df::split(we.re));
-    im.add(df::split(we.im));
-    for (int v = 0; v < cnt; ++v) {
-      const cx<double> a = V[v * ldv + e];
-      const f2 ar = df::split(a.re), ai = df::split(a.im);
-      const c2 hv = h.c[v];
-      // (hr + i hi)(ar + i ai) = (hr ar - hi ai) + i (hr ai + hi ar)
-      re.fms_ff(hv.re, ar);
-      re.fma_ff(hv.im, ai);
-      im.fms_ff(hv.re, ai);
-      im.fms_ff(hv.im, ar);
+  const size_t stride = (size_t)gridDim.x * RT;
+  const cx<double> z = czero<double>();
+  for (size_t e0 = (size_t)blockIdx.x * RT + threadIdx.x; e0 < n; e0 += UPD * stride) {
+    df::acc re[UPD], im[UPD];
+#pragma unroll
+    for (int u = 0; u < UPD; ++u) {
+      const size_t e = e0 + u * stride;
+      const cx<double> we = e < n ? w[e] : z;
+      re[u].add(df::split(we.re));
+      im[u].add(df::split(we.im));
     }
-    df::acc ore, oim;
-    ore.fma_ff(re.norm(), s);
-    oim.fma_ff(im.norm(), s);
-    const f2 fr = ore.norm(), fi = oim.norm();
-    w[e] = mkc<double>((double)fr.hi + (double)fr.lo, (double)fi.hi + (double)fi.lo);
-    if (out32) out32[e] = mkc<float>(fr.hi, fi.hi);
-    nn.fma_ff(fr, fr);
-    nn.fma_ff(fi, fi);
+    for (int v = 0; v < cnt; ++v) {
+      cx<double> a[UPD];
+#pragma unroll
+      for (int u = 0; u < UPD; ++u) a[u] = V[v * ldv + (e0 + u * stride < n ? e0 + u * stride : n - 1)];
+#pragma unroll
+      for (int u = 0; u < UPD; ++u)
+        if (e0 + u * stride >= n) a[u] = z;
+      const c2 hv = h.c[v];
+#pragma unroll
+      for (int u = 0; u < UPD; ++u) {
+        const f2 ar = df::split(a[u].re), ai = df::split(a[u].im);
+        // (hr + i hi)(ar + i ai) = (hr ar - hi ai) + i (hr ai + hi ar)
+        re[u].fms_ff(hv.re, ar);
+        re[u].fma_ff(hv.im, ai);
+        im[u].fms_ff(hv.re, ai);
+        im[u].fms_ff(hv.im, ar);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UPD; ++u) {
+      const size_t e = e0 + u * stride;
+      if (e >= n) break;
+      df::acc ore, oim;
+      ore.fma_ff(re[u].norm(), s);
+      oim.fma_ff(im[u].norm(), s);
+      const f2 fr = ore.norm(), fi = oim.norm();
+      w[e] = mkc<double>((double)fr.hi + (double)fr.lo, (double)fi.hi + (double)fi.lo);
+      if (out32) out32[e] = mkc<float>(fr.hi, fi.hi);
+      nn.fma_ff(fr, fr);
+      nn.fma_ff(fi, fi);
+    }
   }
   double acc[1] = {nn.to_double()};
   kv::block_reduce_store<1>(acc, part);
@@ -86,29 +130,47 @@ __global__ void __launch_bounds__(RT) update_scale(cx<double>* __restrict__ w, c
 template <typename TZ>
 __global__ void __launch_bounds__(RT) combine(cx<double>* __restrict__ x, const cx<TZ>* __restrict__ Z, size_t ldz,
                                               int cnt, Coefs y, size_t n) {
-  for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < n; e += (size_t)gridDim.x * RT) {
-    const cx<double> xe = x[e];
-    df::acc re, im;
-    re.add(df::split(xe.re));
-    im.add(df::split(xe.im));
-    for (int v = 0; v < cnt; ++v) {
-      const cx<TZ> z = Z[v * ldz + e];
-      f2 zr, zi;
-      if constexpr (sizeof(TZ) == 4) {
-        zr = {(float)z.re, 0.f};
-        zi = {(float)z.im, 0.f};
-      } else {
-        zr = df::split((double)z.re);
-        zi = df::split((double)z.im);
-      }
-      const c2 yv = y.c[v];
-      re.fma_ff(yv.re, zr);
-      re.fms_ff(yv.im, zi);
-      im.fma_ff(yv.re, zi);
-      im.fma_ff(yv.im, zr);
+  const size_t stride = (size_t)gridDim.x * RT;
+  for (size_t e0 = (size_t)blockIdx.x * RT + threadIdx.x; e0 < n; e0 += UPD * stride) {
+    df::acc re[UPD], im[UPD];
+#pragma unroll
+    for (int u = 0; u < UPD; ++u) {
+      const size_t e = e0 + u * stride;
+      const cx<double> xe = e < n ? x[e] : czero<double>();
+      re[u].add(df::split(xe.re));
+      im[u].add(df::split(xe.im));
     }
-    const f2 fr = re.norm(), fi = im.norm();
-    x[e] = mkc<double>((double)fr.hi + (double)fr.lo, (double)fi.hi + (double)fi.lo);
+    for (int v = 0; v < cnt; ++v) {
+      cx<TZ> zv[UPD];
+#pragma unroll
+      for (int u = 0; u < UPD; ++u) zv[u] = Z[v * ldz + (e0 + u * stride < n ? e0 + u * stride : n - 1)];
+#pragma unroll
+      for (int u = 0; u < UPD; ++u)
+        if (e0 + u * stride >= n) zv[u] = czero<TZ>();
+      const c2 yv = y.c[v];
+#pragma unroll
+      for (int u = 0; u < UPD; ++u) {
+        f2 zr, zi;
+        if constexpr (sizeof(TZ) == 4) {
+          zr = {(float)zv[u].re, 0.f};
+          zi = {(float)zv[u].im, 0.f};
+        } else {
+          zr = df::split((double)zv[u].re);
+          zi = df::split((double)zv[u].im);
+        }
+        re[u].fma_ff(yv.re, zr);
+        re[u].fms_ff(yv.im, zi);
+        im[u].fma_ff(yv.re, zi);
+        im[u].fma_ff(yv.im, zr);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UPD; ++u) {
+      const size_t e = e0 + u * stride;
+      if (e >= n) break;
+      const f2 fr = re[u].norm(), fi = im[u].norm();
+      x[e] = mkc<double>((double)fr.hi + (double)fr.lo, (double)fi.hi + (double)fi.lo);
+    }
   }
 }
 

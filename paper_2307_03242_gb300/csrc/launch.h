@@ -16,8 +16,8 @@ template <typename T>
 void launch_vanka2(const Grid<T>& g, const cx<T>* b, const cx<T>* uin, cx<T>* uout, cx<T>* p, int colour, T w,
                    int zero_in, cudaStream_t st);
 template <typename T>
-void launch_restrict2(const Grid<T>& g, const cx<T>* b, const cx<T>* x, cx<T>* bc, const int nc[3], int zero_x,
-                      cudaStream_t st);
+void launch_restrict2(const Grid<T>& g, const cx<T>* b, const cx<T>* x, cx<T>* bc, const int nc[3], cx<T>* r,
+                      cudaStream_t st);  // r: fine-level scratch of (d+1) n_x n_y values (the residual)  // r: fine-level scratch for the two-kernel path, or nullptr
 template <typename T>
 void launch_prolong2(const cx<T>* e, cx<T>* x, const int n[3], const int nc[3], cudaStream_t st);
 
@@ -37,8 +37,8 @@ void launch_apply_ff2(const ff2::FineFF& g, const cx<TI>* x, const cx<double>* b
                       cudaStream_t st);
 
 template <typename T>
-cudaError_t launch_coarse_sweeps2(const Grid<T>& g, const cx<T>* b, cx<T>* x, cx<T>* alt, int sweeps, T w,
-                                  cudaStream_t st);
+cudaError_t launch_sweeps_coop2(const Grid<T>& g, const cx<T>* b, cx<T>* x, cx<T>* alt, int sweeps, T w,
+                                int zero_first, cudaStream_t st);
 
 template <typename TI>
 void launch_apply_ff3(const ff3::FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y,

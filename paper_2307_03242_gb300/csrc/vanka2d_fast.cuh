@@ -21,8 +21,11 @@ template <typename T> HD T abl_at(const Grid<T>& g, int a, int k, int half, T L)
 }
 
 // INTERIOR: the caller guarantees 2 <= i <= nx-3 and 2 <= j <= ny-3 (no bounds checks, no clamps,
-// no excluded faces).
-template <typename T, bool INTERIOR = false>
+// no excluded faces). NOABL: the caller guarantees the attenuation is zero on lattice positions
+// i-1 .. i+2 and j-1 .. j+2 (Grid::abl_free), so the absorbing-layer terms are dropped.
+// COH: u and p are read through L2 (ldcg) because other blocks of the same launch wrote them
+// before a grid-wide barrier (the cooperative coarse solve); otherwise u takes the read-only path.
+template <typename T, bool INTERIOR = false, bool NOABL = false, bool COH = false>
 HD void vanka_cell(const Grid<T>& g, const cx<T>* __restrict__ b, const cx<T>* __restrict__ uin,
                    cx<T>* __restrict__ uout, cx<T>* p, int colour, T w, int zero_in, int ip, int j) {
   const int nx = g.nx, ny = g.ny;
@@ -35,6 +38,8 @@ HD void vanka_cell(const Grid<T>& g, const cx<T>* __restrict__ b, const cx<T>* _
   }
   if (i >= nx) return;
   const size_t N = (size_t)nx * ny, k = (size_t)j * nx + i;
+  auto ldu = [](const cx<T>* q) { return COH ? ldcg(q) : ldg(q); };
+  auto ldp = [](const cx<T>* q) { return COH ? ldcg(q) : *q; };
   const cx<T>* u1 = uin;
   const cx<T>* u2 = uin + N;
   const T t0 = T(0.5) * (T(1) + g.beta), t1 = T(0.25) * (T(1) - g.beta);
@@ -70,13 +75,13 @@ HD void vanka_cell(const Grid<T>& g, const cx<T>* __restrict__ b, const cx<T>* _
   T gxf[4], gxc[3], gyf[4], gyc[3];
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    gxf[c] = abl_at(g, 0, i - 1 + c, 0, g.Lx);
-    gyf[c] = abl_at(g, 1, j - 1 + c, 0, g.Ly);
+    gxf[c] = NOABL ? T(0) : abl_at(g, 0, i - 1 + c, 0, g.Lx);
+    gyf[c] = NOABL ? T(0) : abl_at(g, 1, j - 1 + c, 0, g.Ly);
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    gxc[c] = abl_at(g, 0, i - 1 + c, 1, g.Lx);
-    gyc[c] = abl_at(g, 1, j - 1 + c, 1, g.Ly);
+    gxc[c] = NOABL ? T(0) : abl_at(g, 0, i - 1 + c, 1, g.Lx);
+    gyc[c] = NOABL ? T(0) : abl_at(g, 1, j - 1 + c, 1, g.Ly);
   }
   const T w2 = g.w2, att = g.att;
   // m1 at u1 face (X, Y) with rho_f = (rho(X-1,Y) + rho(X,Y))/2; offsets relative to (i, j)
@@ -101,9 +106,9 @@ HD void vanka_cell(const Grid<T>& g, const cx<T>* __restrict__ b, const cx<T>* _
     r[3] = exN ? z : b[N + k + nx];
     r[4] = b[2 * N + k];
   } else {
-    const cx<T> pC = p[k];
-    const cx<T> pW = (INTERIOR || i > 0) ? p[k - 1] : z, pE = (INTERIOR || i + 1 < nx) ? p[k + 1] : z;
-    const cx<T> pS = (INTERIOR || j > 0) ? p[k - nx] : z, pN = (INTERIOR || j + 1 < ny) ? p[k + nx] : z;
+    const cx<T> pC = ldp(p + k);
+    const cx<T> pW = (INTERIOR || i > 0) ? ldp(p + k - 1) : z, pE = (INTERIOR || i + 1 < nx) ? ldp(p + k + 1) : z;
+    const cx<T> pS = (INTERIOR || j > 0) ? ldp(p + k - nx) : z, pN = (INTERIOR || j + 1 < ny) ? ldp(p + k + nx) : z;
     cx<T> G1m, G1c, G1p;  // d1 u1 at cells i-1, i, i+1 (needed by the p row too)
     {
       // u1 on faces i-1..i+2, rows j-1..j+1
@@ -114,7 +119,7 @@ HD void vanka_cell(const Grid<T>& g, const cx<T>* __restrict__ b, const cx<T>* _
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const int ii = i - 1 + c;
-          A[rr][c] = (INTERIOR || (ii >= 1 && ii < nx && jj >= 0 && jj < ny)) ? ldg(u1 + (size_t)jj * nx + ii) : z;
+          A[rr][c] = (INTERIOR || (ii >= 1 && ii < nx && jj >= 0 && jj < ny)) ? ldu(u1 + (size_t)jj * nx + ii) : z;
         }
       }
       auto g1 = [&](int c) { return ih * (t1 * ((A[0][c + 1] - A[0][c]) + (A[2][c + 1] - A[2][c])) + t0 * (A[1][c + 1] - A[1][c])); };
@@ -151,7 +156,7 @@ HD void vanka_cell(const Grid<T>& g, const cx<T>* __restrict__ b, const cx<T>* _
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const int ii = i - 1 + c;
-          B[rr][c] = (INTERIOR || (jj >= 1 && jj < ny && ii >= 0 && ii < nx)) ? ldg(u2 + (size_t)jj * nx + ii) : z;
+          B[rr][c] = (INTERIOR || (jj >= 1 && jj < ny && ii >= 0 && ii < nx)) ? ldu(u2 + (size_t)jj * nx + ii) : z;
         }
       }
       // d2 u2 at cell (i, Y): rows ry+1 (Y+1) and ry (Y)
@@ -204,11 +209,11 @@ HD void vanka_cell(const Grid<T>& g, const cx<T>* __restrict__ b, const cx<T>* _
     if (!exN) o2[k + nx] = w * d[3];
     p[k] = w * d[4];
   } else {
-    o1[k] = exW ? z : u1[k] + w * d[0];
-    if (!exE) o1[k + 1] = u1[k + 1] + w * d[1];
-    o2[k] = exS ? z : u2[k] + w * d[2];
-    if (!exN) o2[k + nx] = u2[k + nx] + w * d[3];
-    p[k] = p[k] + w * d[4];
+    o1[k] = exW ? z : ldu(u1 + k) + w * d[0];
+    if (!exE) o1[k + 1] = ldu(u1 + k + 1) + w * d[1];
+    o2[k] = exS ? z : ldu(u2 + k) + w * d[2];
+    if (!exN) o2[k + nx] = ldu(u2 + k + nx) + w * d[3];
+    p[k] = ldp(p + k) + w * d[4];
   }
   if (!INTERIOR && i == 1) o1[k - 1] = z;
   if (!INTERIOR && j == 1) o2[k - nx] = z;
@@ -222,9 +227,12 @@ __global__ void __launch_bounds__(BX * BY, sizeof(T) == 4 ? 2 : 1) vanka_fast(Gr
   const int ip = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int i = 2 * ip + ((colour + j) & 1);
-  if (!zero_in && i >= 2 && i + 3 <= g.nx && j >= 2 && j + 3 <= g.ny)
-    vanka_cell<T, true>(g, b, uin, uout, p, colour, w, zero_in, ip, j);
-  else
+  if (!zero_in && i >= 2 && i + 3 <= g.nx && j >= 2 && j + 3 <= g.ny) {
+    if (g.abl_free(0, i - 1, i + 2) && g.abl_free(1, j - 1, j + 2))
+      vanka_cell<T, true, true>(g, b, uin, uout, p, colour, w, zero_in, ip, j);
+    else
+      vanka_cell<T, true>(g, b, uin, uout, p, colour, w, zero_in, ip, j);
+  } else
     vanka_cell<T, false>(g, b, uin, uout, p, colour, w, zero_in, ip, j);
 }
 

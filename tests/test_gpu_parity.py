@@ -45,21 +45,63 @@ def test_apply_fp64_matches_oracle(case, shifted):
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("sweeps", [1, 2])
-def test_red_black_vanka_matches_oracle(case, prec, sweeps):
+@pytest.mark.parametrize("level", [0, 1])
+def test_red_black_vanka_matches_oracle(case, prec, sweeps, level):
+    # level 0 runs one launch per half-sweep; the small coarse levels of these cases run all
+    # half-sweeps in one cooperative launch (2D)
     w = _w(case)
     pb = oracle_problem(w)
     hier = oracle_hierarchy(w, pb)
     s = gpu_solver(w, prec)
-    b = random_field(pb, 21)
-    x = random_field(pb, 22)
+    pl = hier.pbs[level]
+    b = random_field(pl, 21)
+    x = random_field(pl, 22)
     ref = x.ravel()
     for _ in range(sweeps):
-        ref = oracle.red_black_sweep(hier.H[0], hier.V[0], hier.idx[0], hier.colour[0], b.ravel(), ref, hier.w[0])
+        ref = oracle.red_black_sweep(hier.H[level], hier.V[level], hier.idx[level], hier.colour[level], b.ravel(), ref,
+                                     hier.w[level])
     xt = to_gpu(x, prec)
-    s.smooth(0, to_gpu(b, prec), xt, sweeps)
+    s.smooth(level, to_gpu(b, prec), xt, sweeps)
     tol = TOL[prec] * (10 if prec == 64 else 5)
     assert rel_max(to_np(xt), ref) < tol
     s.close()
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_cooperative_sweeps_match_per_launch_sweeps(prec):
+    """Level 1 of a 1024x800 grid whose material is constant on 2x2 blocks is, cell for cell, the
+    level 0 of a 512x400 grid with twice the spacing (same physical absorbing layer, shift and
+    damping). Its sweeps run in one cooperative launch whose threads each take several cells
+    (102 400 cells per colour); the 512x400 level 0 runs one launch per half-sweep, the path
+    the oracle parity tests pin."""
+    from paper_2307_03242_gb300 import emg
+    import torch
+    rng = np.random.default_rng(7)
+    nb = (512, 400)
+    shape_b = (nb[1], nb[0])
+    mu_b = rng.uniform(0.5, 2.0, shape_b)
+    rho_b = rng.uniform(0.8, 1.5, shape_b)
+    lam_b = mu_b * rng.uniform(1.0, 2.0, shape_b)
+    up = lambda a: np.repeat(np.repeat(a, 2, axis=0), 2, axis=1)
+    common = dict(omega=0.3, gamma=0.01, alpha=0.5, beta=2.0 / 3.0, abl_gamma_max=2.0, damping=[0.3, 0.3],
+                  cycle_precision=prec, coarse_solver=emg.COARSE_SMOOTH, coarse_sweeps=2)
+    sa = emg.Solver(emg.Params(n=(2 * nb[0], 2 * nb[1]), h=1.0, abl_cells=12, levels=2, **common),
+                    up(lam_b), up(mu_b), up(rho_b))
+    sb = emg.Solver(emg.Params(n=nb, h=2.0, abl_cells=6, levels=1, **common), lam_b, mu_b, rho_b)
+    assert sa.vec_shape(1) == sb.vec_shape(0)
+    dt = sa.cdtype
+    g = torch.Generator(device="cuda").manual_seed(3)
+    b = torch.randn(sb.vec_shape(0), dtype=dt, device="cuda", generator=g)
+    x0 = torch.randn(sb.vec_shape(0), dtype=dt, device="cuda", generator=g)
+    x0[0, :, 0] = 0  # faces on the boundary are not unknowns
+    x0[1, 0, :] = 0
+    for sweeps in (1, 2):
+        xa, xb = x0.clone(), x0.clone()
+        sa.smooth(1, b, xa, sweeps)
+        sb.smooth(0, b, xb, sweeps)
+        assert rel_max(to_np(xa), to_np(xb)) < TOL[prec]
+    sa.close()
+    sb.close()
 
 
 @pytest.mark.parametrize("case", list(CASES))

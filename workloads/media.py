@@ -109,7 +109,7 @@ def config_c2_random2d(n: int = 2048, seed: int = 0, levels: int = 5, source_dep
     """2D smooth random medium: Vp in [1.5, 4.5] (Gaussian filter sigma 32 cells, correlation
     length ~64 cells), Vs = Vp/sqrt(3), rho = 0.31 Vp^0.25; 10 points per minimum shear
     wavelength; point force in the depth component u2 at (n/2, depth 32). Solver: W(2,2) on 5
-    levels, shift 0.5, shift 1.0 on the coarsest level (8 red-black sweeps)."""
+    levels, shift 0.5, shift 1.0 on the coarsest level (4 red-black sweeps), FGMRES(5)."""
     shape = (n, n)
     sigma = 32.0 * n / 2048.0 if n < 2048 else 32.0
     vp = gaussian_random_velocity(shape, seed, sigma_cells=sigma)
@@ -121,14 +121,15 @@ def config_c2_random2d(n: int = 2048, seed: int = 0, levels: int = 5, source_dep
     rhs = point_source((n, n), 1, (n // 2, min(source_depth, n - 1)))
     return Workload("c2_random_2d_%d" % n, (n, n), h, lam, mu, rho, omega, rhs,
                     levels=levels, alpha=0.5, damping=0.2, abl_cells=20, coarse="smooth",
-                    coarse_sweeps=8, coarse_damping=0.8, cycle="W", alpha_coarsest=1.0)
+                    coarse_sweeps=4, coarse_damping=0.8, cycle="W", alpha_coarsest=1.0, restart=5)
 
 
 def config_c3_layered3d(n: int = 256, source=(128, 128, 24), levels: int = 3) -> Workload:
     """3D three-layer medium (Vp 2.0/3.0/4.0 for depth fractions [0,80)/[80,170)/[170,256) of
     256) plus a Gaussian inclusion Vp*(1 + 0.2 exp(-r^2/24^2)) at the centre; Vs = Vp/sqrt(3),
     rho 1.0/1.2/1.4 by layer; 10 points per minimum shear wavelength; u3 point force. Solver:
-    W(1,1) on 3 levels, shift 0.4 (2.5 on the coarsest level, 16 red-black sweeps), damping 0.15."""
+    K(1,1) on 3 levels, shift 0.4 (2.5 on the coarsest level, 16 red-black sweeps), damping 0.15,
+    FGMRES(8)."""
     s = n / 256.0
     z = (np.arange(n) + 0.5)
     vp1 = np.where(z < 80 * s, 2.0, np.where(z < 170 * s, 3.0, 4.0))
@@ -146,8 +147,8 @@ def config_c3_layered3d(n: int = 256, source=(128, 128, 24), levels: int = 3) ->
     rhs = point_source((n, n, n), 2, src)
     return Workload("c3_layered_3d_%d" % n, (n, n, n), h, lam, mu, rho, omega, rhs,
                     levels=levels, alpha=0.4, damping=0.15, abl_cells=max(2, int(round(20 * s))),
-                    coarse="smooth", coarse_sweeps=16, coarse_damping=0.8, cycle="W", alpha_coarsest=2.5,
-                    nu_pre=1, nu_post=1)
+                    coarse="smooth", coarse_sweeps=16, coarse_damping=0.8, cycle="K", alpha_coarsest=2.5,
+                    nu_pre=1, nu_post=1, restart=8)
 
 
 def small_heterogeneous(n, seed: int = 1, sigma_cells: float = 2.0, abl_cells: int = 2,

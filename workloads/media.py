@@ -109,7 +109,7 @@ def config_c2_random2d(n: int = 2048, seed: int = 0, levels: int = 5, source_dep
     """2D smooth random medium: Vp in [1.5, 4.5] (Gaussian filter sigma 32 cells, correlation
     length ~64 cells), Vs = Vp/sqrt(3), rho = 0.31 Vp^0.25; 10 points per minimum shear
     wavelength; point force in the depth component u2 at (n/2, depth 32). Solver: W(2,2) on 5
-    levels, shift 0.5, shift 1.0 on the coarsest level (4 red-black sweeps), FGMRES(5)."""
+    levels, shift 0.5, shift 1.0 on the coarsest level (2 red-black sweeps), FGMRES(5)."""
     shape = (n, n)
     sigma = 32.0 * n / 2048.0 if n < 2048 else 32.0
     vp = gaussian_random_velocity(shape, seed, sigma_cells=sigma)
@@ -121,7 +121,7 @@ def config_c2_random2d(n: int = 2048, seed: int = 0, levels: int = 5, source_dep
     rhs = point_source((n, n), 1, (n // 2, min(source_depth, n - 1)))
     return Workload("c2_random_2d_%d" % n, (n, n), h, lam, mu, rho, omega, rhs,
                     levels=levels, alpha=0.5, damping=0.2, abl_cells=20, coarse="smooth",
-                    coarse_sweeps=4, coarse_damping=0.8, cycle="W", alpha_coarsest=1.0, restart=5)
+                    coarse_sweeps=2, coarse_damping=0.8, cycle="W", alpha_coarsest=1.0, restart=5)
 
 
 def config_c3_layered3d(n: int = 256, source=(128, 128, 24), levels: int = 3) -> Workload:

@@ -132,6 +132,21 @@ emg_status emg_solve(emg_handle h, const void* b, void* x, double tol, int max_i
 emg_status emg_solve_host(emg_handle h, const double* b_host, double* x_host, double tol,
                           int max_iter, int restart, emg_stats* stats);
 
+/* A batch of independent solves, each exactly emg_solve(handles[k], b[k], x[k], ...): many
+ * grids, media, frequencies or sources at once (the batched use the paper's Sec. 5 experiments
+ * imply -- one solve per source and frequency -- but do not describe; no counterpart in the
+ * paper's solver itself). Small grids cannot fill the GPU on their own, so the solves run
+ * concurrently: up to `workers` host threads (0: one per distinct handle, at most 64) each drive
+ * a handle's solves on that handle's own stream, and the GPU interleaves their kernels. Give
+ * every handle its own stream to get the overlap; handles may repeat (several right-hand sides
+ * of one system), and then their jobs run one after another. b[k], x[k]: FP64 device vectors of
+ * handle k's size; stats and status: arrays of count entries, or NULL. Returns EMG_OK, the first
+ * (lowest k) error, or EMG_NOT_CONVERGED if any job stopped at max_iter; status[k] holds each
+ * job's own result. The handles must not be used by other threads during the call. */
+emg_status emg_solve_batch(const emg_handle* handles, int count, const void* const* b,
+                           void* const* x, double tol, int max_iter, int restart,
+                           emg_stats* stats, int workers, emg_status* status);
+
 /* ---- Per-step entry points (one row of the cycle each; used for parity checks). ----
  * `level` 0 is the finest. Vectors are cycle vectors of that level's size. */
 

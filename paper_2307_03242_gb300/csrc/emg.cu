@@ -17,6 +17,9 @@
 #include <string>
 #include <vector>
 #include <cstdlib>
+#include <atomic>
+#include <map>
+#include <thread>
 
 #include "emg.h"
 #include "launch.h"
@@ -96,6 +99,7 @@ struct Level {
 struct emg_ctx {
   emg_params prm{};
   int dim = 2, L = 1, prec = 32, sms = 148;
+  int dev = 0;  // the device the handle was created on
   cudaStream_t st = nullptr;
   std::vector<Level> lv;
   DBuf mu64, rho64, cp64;  // finest material in FP64 for the outer operator
@@ -1060,9 +1064,8 @@ emg_status emg_create(const emg_params* params, const double* lam, const double*
   c->L = params->levels;
   c->prec = params->cycle_precision;
   c->st = (cudaStream_t)cuda_stream;
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
-  CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaGetDevice(&c->dev));
+  CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev));
   c->lv.resize(c->L);
   for (int l = 0; l < c->L; ++l) {
     Level& L = c->lv[l];
@@ -1202,6 +1205,78 @@ emg_status emg_solve(emg_handle h, const void* b, void* x, double tol, int max_i
   if (!(tol >= 0.0)) raise(EMG_ERR_INVALID, "tol must be >= 0");
   if (c.prec == 32) return solve_impl<float>(c, (const cx<double>*)b, (cx<double>*)x, tol, max_iter, restart, stats);
   return solve_impl<double>(c, (const cx<double>*)b, (cx<double>*)x, tol, max_iter, restart, stats);
+  ABI_CATCH
+}
+
+emg_status emg_solve_batch(const emg_handle* handles, int count, const void* const* b, void* const* x, double tol,
+                           int max_iter, int restart, emg_stats* stats, int workers, emg_status* status) {
+  ABI_TRY
+  if (count < 0) raise(EMG_ERR_INVALID, "count < 0");
+  if (count == 0) return EMG_OK;
+  if (!handles || !b || !x) raise(EMG_ERR_INVALID, "handles, b or x is NULL");
+  if (restart < 1 || restart > 64) raise(EMG_ERR_INVALID, "restart must be in 1..64");
+  if (max_iter < 0) raise(EMG_ERR_INVALID, "max_iter < 0");
+  if (!(tol >= 0.0)) raise(EMG_ERR_INVALID, "tol must be >= 0");
+  if (workers < 0) raise(EMG_ERR_INVALID, "workers < 0");
+  // Jobs that share a handle run one after another on one worker (they share its workspaces).
+  std::map<emg_ctx*, std::vector<int>> by_handle;
+  std::vector<std::vector<int>> groups;
+  for (int k = 0; k < count; ++k) {
+    emg_ctx* c = checked(handles[k]);
+    check_ptr(b[k], "b[k]");
+    check_ptr(x[k], "x[k]");
+    by_handle[c].push_back(k);
+  }
+  for (auto& kv : by_handle) groups.push_back(kv.second);
+  // The largest systems first, so that the last ones to start are short.
+  std::sort(groups.begin(), groups.end(), [&](const std::vector<int>& a, const std::vector<int>& g) {
+    return handles[a[0]]->nvec() * a.size() > handles[g[0]]->nvec() * g.size();
+  });
+  const int nw = std::max(1, std::min<int>(workers > 0 ? workers : (int)groups.size(), std::min<int>((int)groups.size(), 64)));
+  std::vector<emg_status> st(count, EMG_OK);
+  std::vector<std::string> msg(count);
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    for (int gi = next.fetch_add(1); gi < (int)groups.size(); gi = next.fetch_add(1)) {
+      for (int k : groups[gi]) {
+        emg_ctx& c = *handles[k];
+        try {
+          CK(cudaSetDevice(c.dev));
+          emg_stats* sk = stats ? &stats[k] : nullptr;
+          st[k] = c.prec == 32 ? solve_impl<float>(c, (const cx<double>*)b[k], (cx<double>*)x[k], tol, max_iter, restart, sk)
+                               : solve_impl<double>(c, (const cx<double>*)b[k], (cx<double>*)x[k], tol, max_iter, restart, sk);
+        } catch (const EmgError& e) {
+          st[k] = e.s;
+          msg[k] = e.msg;
+        } catch (const std::bad_alloc&) {
+          st[k] = EMG_ERR_NOMEM;
+          msg[k] = "host allocation failed";
+        } catch (const std::exception& e) {
+          st[k] = EMG_ERR_INVALID;
+          msg[k] = e.what();
+        }
+      }
+    }
+  };
+  int dev0 = 0;
+  CK(cudaGetDevice(&dev0));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nw; ++t) pool.emplace_back(work);
+  work();  // the calling thread is one of the workers
+  for (auto& t : pool) t.join();
+  CK(cudaSetDevice(dev0));
+  if (status)
+    for (int k = 0; k < count; ++k) status[k] = st[k];
+  // the first error (by job index) wins; otherwise EMG_NOT_CONVERGED if any job did not converge
+  emg_status worst = EMG_OK;
+  for (int k = 0; k < count; ++k) {
+    if (st[k] != EMG_OK && st[k] != EMG_NOT_CONVERGED) {
+      g_err = "job " + std::to_string(k) + ": " + msg[k];
+      return st[k];
+    }
+    if (st[k] == EMG_NOT_CONVERGED) worst = EMG_NOT_CONVERGED;
+  }
+  return worst;
   ABI_CATCH
 }
 

@@ -66,6 +66,8 @@ def _load():
         "emg_profile": [vp, i32],
         "emg_profile_read": [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(dbl)],
         "emg_smooth_noalloc": [ctypes.POINTER(_Params), vp, vp, vp, vp, vp, i32, vp],
+        "emg_solve_batch": [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(vp), dbl, i32, i32,
+                            ctypes.POINTER(_Stats), i32, ctypes.POINTER(ctypes.c_int)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -79,7 +81,7 @@ def _load():
 LIB = _load()
 EXPORTED = ["emg_create", "emg_destroy", "emg_last_error", "emg_apply", "emg_vcycle", "emg_solve", "emg_solve_host",
             "emg_level_info", "emg_smooth", "emg_residual_restrict", "emg_prolong_correct", "emg_coarse_solve",
-            "emg_profile", "emg_profile_read", "emg_smooth_noalloc"]
+            "emg_profile", "emg_profile_read", "emg_smooth_noalloc", "emg_solve_batch"]
 NOALLOC_MAX_CELLS = 262144
 
 
@@ -153,6 +155,35 @@ def _ptr(t, dtype, numel, what):
     if t.numel() != numel:
         raise ValueError("%s has %d elements, expected %d" % (what, t.numel(), numel))
     return ctypes.c_void_p(t.data_ptr())
+
+
+def solve_batch(jobs, tol=1e-6, max_iter=1000, restart=20, workers=0, raise_errors=True):
+    """emg_solve_batch: jobs is a list of (Solver, b, x) with complex128 CUDA tensors; the solves
+    run concurrently, one host worker per distinct solver (give each solver its own stream).
+    Returns one stats dict per job (with its own "status"); with raise_errors, raises on the first
+    job error instead."""
+    import torch
+    count = len(jobs)
+    hs = (ctypes.c_void_p * count)()
+    bs = (ctypes.c_void_p * count)()
+    xs = (ctypes.c_void_p * count)()
+    for k, (s, b, x) in enumerate(jobs):
+        n = s._n()
+        hs[k] = s.h
+        bs[k] = _ptr(b, torch.complex128, n, "b[%d]" % k)
+        xs[k] = _ptr(x, torch.complex128, n, "x[%d]" % k)
+    st = (_Stats * count)()
+    status = (ctypes.c_int * count)()
+    torch.cuda.current_stream().synchronize()  # b, x were produced on the caller's stream
+    rc = LIB.emg_solve_batch(hs, count, bs, xs, tol, max_iter, restart, st, workers, status)
+    if raise_errors:
+        _check(rc, allow=(0, 5))
+    out = []
+    for k in range(count):
+        d = Solver._stats(st[k], None, status[k])
+        d["status"] = status[k]
+        out.append(d)
+    return out
 
 
 def smooth_noalloc(params: Params, mu, rho, cp, b, x, sweeps, stream=None):

@@ -51,3 +51,15 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     assert st == 1 and b"divisible" in emg.LIB.emg_last_error()
     assert emg.LIB.emg_solve(None, None, None, 1e-6, 10, 20, None) == 1
     assert emg.LIB.emg_destroy(None) == 0
+
+
+def test_batch_arguments_are_rejected_without_a_gpu():
+    import ctypes
+    from paper_2307_03242_gb300 import emg
+    vp = ctypes.c_void_p
+    arr = (vp * 1)()
+    assert emg.LIB.emg_solve_batch(arr, -1, arr, arr, 1e-6, 10, 5, None, 0, None) == 1
+    assert emg.LIB.emg_solve_batch(None, 0, None, None, 1e-6, 10, 5, None, 0, None) == 0
+    assert emg.LIB.emg_solve_batch(arr, 1, arr, arr, 1e-6, 10, 5, None, 0, None) == 1  # NULL handle
+    assert b"NULL handle" in emg.LIB.emg_last_error()
+    assert emg.LIB.emg_solve_batch(None, 1, arr, arr, 1e-6, 10, 5, None, 0, None) == 1

@@ -124,6 +124,39 @@ def config_c2_random2d(n: int = 2048, seed: int = 0, levels: int = 5, source_dep
                     coarse_sweeps=2, coarse_damping=0.8, cycle="W", alpha_coarsest=1.0, restart=5)
 
 
+def config_c4_batch(count: int = 64, seed0: int = 1000, sizes=(256, 384, 512, 768, 1024),
+                    abl_cells: int = 20) -> list:
+    """Batch of independent 2D solves: instance i draws its square grid side uniformly from
+    `sizes` and its medium from the 2D random-field generator with seed seed0 + i (Gaussian
+    filter sigma 32 cells, Vp in [1.5, 4.5], Vs = Vp/sqrt(3), rho = 0.31 Vp^0.25), omega for 10
+    points per minimum shear wavelength, and 1-4 unit point forces in the depth component at
+    random positions outside the absorbing layer (extra["sources"], the first also in rhs).
+    Solver: the 2048^2 configuration's, whose level spacings h_l = 2^l h it shares: W(2,2) on 5
+    levels (coarsest n/16, 16^2 to 64^2), shift 0.5 (1.0 and 2 red-black sweeps on the
+    coarsest level), FGMRES(5)."""
+    out = []
+    for k in range(count):
+        rng = np.random.default_rng(seed0 + k)
+        n = int(rng.choice(sizes))
+        shape = (n, n)
+        vp = gaussian_random_velocity(shape, seed0 + k, sigma_cells=32.0)
+        vs = vp / np.sqrt(3.0)
+        rho = 0.31 * vp ** 0.25
+        lam, mu = lame_from_velocity(vp, vs, rho)
+        h = 1.0
+        omega = omega_for_points_per_wavelength(float(vs.min()), h)
+        nsrc = int(rng.integers(1, 5))
+        lo, hi = abl_cells + 2, n - abl_cells - 2
+        sources = [point_source((n, n), 1, (int(rng.integers(lo, hi)), int(rng.integers(lo, hi))))
+                   for _ in range(nsrc)]
+        w = Workload("c4_%02d_%d" % (k, n), (n, n), h, lam, mu, rho, omega, sources[0],
+                     levels=5, alpha=0.5, damping=0.2, abl_cells=abl_cells, coarse="smooth", coarse_sweeps=2,
+                     coarse_damping=0.8, cycle="W", alpha_coarsest=1.0, restart=5)
+        w.extra["sources"] = sources
+        out.append(w)
+    return out
+
+
 def config_c3_layered3d(n: int = 256, source=(128, 128, 24), levels: int = 3) -> Workload:
     """3D three-layer medium (Vp 2.0/3.0/4.0 for depth fractions [0,80)/[80,170)/[170,256) of
     256) plus a Gaussian inclusion Vp*(1 + 0.2 exp(-r^2/24^2)) at the centre; Vs = Vp/sqrt(3),

@@ -41,7 +41,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="emg", choices=["emg", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4"],
+                    help="c4: the 64-instance batch of 2D solves (emg_solve_batch)")
+    ap.add_argument("--instances", type=int, default=64, help="c4: number of instances")
     ap.add_argument("--restart", type=int, default=None, help="FGMRES restart length (default: the workload's)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed plain-FP64 solves (after 1 warm-up)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -258,6 +260,9 @@ def main():
     if args.profile_iters > 0:
         run_profile(args)
         return
+    if args.config == "c4":
+        run_batch(args)
+        return
     import torch
     import torch.distributed as dist
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -323,8 +328,7 @@ def main():
     barrier()
     vms = e0.elapsed_time(e1) / nv
     ncell = float(np.prod(w.n))
-    # algorithmic bytes per fine cell per V(2,2) cycle over all levels (unfused half-sweeps counted
-    # at their own minimum): see the design doc section 8
+    # algorithmic bytes per finest cell of one cycle over all level visits (vcycle_bytes_per_cell)
     per_cell = vcycle_bytes_per_cell(w, 8, 4)
     v_gbs = per_cell * ncell / (vms * 1e-3) / 1e9
 
@@ -387,25 +391,146 @@ def main():
         dist.destroy_process_group()
 
 
+BATCH_METRIC = "time to solve a batch of independent 2D systems to 1e-6 rel. residual (FP32 cycle, FP64 FGMRES), 1 GB300"
+
+
+def run_batch(args):
+    """The 2D batch (config_c4_batch): every (instance, source) system solved to 1e-6, all of them
+    in one emg_solve_batch call per step (each instance on a stream of its own). Reported: the
+    batch time (wall clock between device synchronisations, since the work spans every
+    instance's stream and the host threads that drive them), the same systems solved one after
+    another, and the finest-level half-sweep's bandwidth from per-launch CUDA events of that
+    sequential pass."""
+    import torch
+    import torch.distributed as dist
+    from paper_2307_03242_gb300 import emg
+    from workloads import config_c4_batch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ws = config_c4_batch(args.instances)
+    solvers, jobs = [], []
+    for w in ws:
+        s = emg.Solver(emg.params_from_workload(w, 32), w.lam, w.mu, w.rho, stream=torch.cuda.Stream(dev))
+        solvers.append(s)
+        for q in w.extra["sources"]:
+            b = torch.from_numpy(q).to(dev)
+            jobs.append((s, b, torch.zeros_like(b)))
+    tol, restart = ws[0].tol, ws[0].restart
+    mcells = sum(s.ncell for s, _, _ in jobs) / 1e6
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def batch():
+        for _, _, x in jobs:
+            x.zero_()
+        return emg.solve_batch(jobs, tol=tol, max_iter=2000, restart=restart)
+
+    for _ in range(args.warmup):
+        res = batch()
+    for s in solvers:
+        s.profile_read(emg.K_ALL)
+    barrier()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            res = batch()
+        barrier()
+        tb = (time.perf_counter() - t0) / args.steps
+    launches = sum(s.profile_read(emg.K_ALL)["launches"] for s in solvers) // args.steps
+    tb = max_over_ranks(tb, device=dev)
+    # the same systems one after another, with per-launch instrumentation
+    smooth = {"ms": 0.0, "launches": 0, "bytes": 0.0}
+    barrier()
+    t0 = time.perf_counter()
+    seq = []
+    for s, b, x in jobs:
+        s.profile(True)
+        x.zero_()
+        seq.append(s.solve(b, x, tol=tol, max_iter=2000, restart=restart))
+        p = s.profile_read(emg.K_SMOOTH)
+        s.profile(False)
+        for k in smooth:
+            smooth[k] += p[k]
+    barrier()
+    tseq = time.perf_counter() - t0
+    # end to end: right-hand sides from pinned host memory in, solutions out, inside the timing
+    hb = [torch.from_numpy(q).pin_memory() for w in ws for q in w.extra["sources"]]
+    hx = [torch.empty_like(h).pin_memory() for h in hb]
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for h, (_, b, _) in zip(hb, jobs):
+            b.copy_(h, non_blocking=True)
+        batch()
+        for h, (_, _, x) in zip(hx, jobs):
+            h.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+    te2e = (time.perf_counter() - t0) / args.steps
+    nbytes = int(sum(h.numel() for h in hb) * 16)
+    its = [r["iterations"] for r in res]
+    peak, peak_kind = load_peaks()
+    achieved = smooth["bytes"] / (smooth["ms"] * 1e-3) / 1e9 if smooth["ms"] > 0 else None
+    sizes = sorted(set(w.n[0] for w in ws))
+    out = {"metric": BATCH_METRIC, "value": tb, "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": tb * 1e3, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "c64 cycle / c128 outer", "data": "synthetic",
+           "config": {"workload": "c4_batch_%d" % len(ws), "instances": len(ws), "systems": len(jobs),
+                      "grids": "%s (squares)" % "/".join(map(str, sizes)), "mcell_systems": round(mcells, 2),
+                      "cycle": "W(2,2)", "levels": 5, "krylov": "FGMRES(%d)" % restart, "tol": tol,
+                      "concurrency": "one stream and host worker per instance",
+                      "timing": "wall clock between device synchronisations",
+                      "l2": "inputs larger than L2 (%.0f MB of FP64 right-hand sides)" % (16 * mcells * 3),
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "throughput_mcell_systems_per_s": mcells / tb,
+           "iterations": {"min": int(min(its)), "median": int(np.median(its)), "max": int(max(its)),
+                          "all_converged": all(r["converged"] for r in res)},
+           "sequential": {"value": tseq, "unit": "s", "speedup_of_batch": tseq / tb},
+           "roofline": {"kernel": "vanka half-sweep (finest level of every instance, FP32, sequential pass)",
+                        "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                        "frac": achieved / peak if achieved else None, "traffic": None,
+                        "launches": smooth["launches"]},
+           "e2e": {"value": te2e, "unit": "s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+           "gpu_launches": int(launches)}
+    out["clocks"] = clk.summary()
+    for s in solvers:
+        s.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def vcycle_bytes_per_cell(w, cw, rw):
-    """Algorithmic bytes per finest cell of one V(nu1,nu2) cycle (unfused red/black half-sweeps):
-    per level with c = complex word, r = real word, S = (d+1)c:
-      half-sweep   = S (x) + (d+1/2)c (b) + 3r + (d+1/2)c (writes)
-      restriction  = 2S + 3r + S/2^d,  prolongation = 2S/... (read e, read+write x) = 2S + S/2^d
-    summed over levels with the 2^-d cell ratio; the coarsest level's sweeps counted likewise."""
+    """Algorithmic bytes per finest cell of one preconditioner cycle (unfused red/black
+    half-sweeps), with c = complex word, r = real word, S = (d+1)c per cell of a level:
+      half-sweep     S (read x) + (d+1/2)c (read b) + 3r + (d+1/2)c (write faces, p of the colour)
+      residual + R   2S + 3r (read x, b, material) + S/2^d (write the coarse b)
+      P + correction 2S (read and write x) + S/2^d (read the coarse e)
+    Level l has 2^-dl of the finest cells. A V-cycle visits every level once; a W- or K-cycle
+    visits level l <= L-2 2^l times and the coarsest level 2^(L-2) times."""
     d = w.dim
     S = (d + 1) * cw
     half = S + 2 * (d + 0.5) * cw + 3 * rw
-    tot, frac = 0.0, 1.0
+    g = 1 if w.cycle == "V" else 2
+    tot = 0.0
     for l in range(w.levels):
+        cells = 2.0 ** (-d * l)
         if l < w.levels - 1:
             lvl = 2 * (w.nu_pre + w.nu_post) * half + (2 * S + 3 * rw + S / 2 ** d) + (2 * S + S / 2 ** d)
+            visits = g ** l
         else:
             lvl = 2 * w.coarse_sweeps * half if w.coarse == "smooth" else 0.0
-        tot += frac * lvl
-        frac /= 2 ** d
+            visits = g ** max(l - 1, 0)
+        tot += visits * cells * lvl
     return tot
-
 
 if __name__ == "__main__":
     main()

@@ -122,9 +122,23 @@ struct emg_ctx {
   int64_t pn[EMG_K_COUNT] = {0};
   double pbytes[EMG_K_COUNT] = {0};
   int64_t launches = 0;  // every kernel launch, any level
+  // The preconditioner cycle as CUDA graphs, one per (right-hand side, output) pair: the cycle's
+  // launch sequence depends only on the parameters, so it is captured once and replayed, one
+  // graph launch instead of ~50-170 kernel launches per FGMRES iteration.
+  struct CycleGraph {
+    const void* b;
+    void* z;
+    int uses;                   // eager runs before capture (the first one warms lazy set-up)
+    cudaGraphExec_t exec;
+    int64_t kernels;            // kernel launches one replay stands for
+  };
+  std::vector<CycleGraph> graphs;
+  bool graphs_ok = true;       // false once a capture failed: the cycle then runs eagerly
 
   size_t nvec() const { return (size_t)(dim + 1) * lv[0].ncell; }
   ~emg_ctx() {
+    for (auto& g : graphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
     if (hred) cudaFreeHost(hred);
     for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : pool) cudaEventDestroy(e);
@@ -844,11 +858,56 @@ void outer_apply(emg_ctx& c, const void* x, bool x32, const cx<double>* b, doubl
   LAUNCHED(c);
 }
 
+// Capture vcycle(0, b, z) into a graph; nullptr (and graphs off for this handle) if the capture
+// or the instantiation fails, e.g. because the runtime cannot capture a launch kind.
+template <typename T>
+cudaGraphExec_t capture_cycle(emg_ctx& c, const cx<T>* b, cx<T>* z, int64_t& kernels) {
+  const int64_t l0 = c.launches;
+  if (cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  bool ok = true;
+  try {
+    vcycle<T>(c, 0, b, z, true);
+  } catch (const EmgError&) {
+    ok = false;
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c.st, &g);
+  kernels = c.launches - l0;
+  c.launches = l0;  // nothing ran yet
+  cudaGraphExec_t exec = nullptr;
+  if (ok && e == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();  // a failed capture leaves no error behind for the next call
+  return exec;
+}
+
 template <typename T>
 void precondition(emg_ctx& c, const cx<double>* v, cx<T>* z) {
   Level& F = c.lv[0];
   // FP32 cycle: its right-hand side was written in FP32 to F.b by the update that produced v
   const cx<T>* b = std::is_same<T, double>::value ? (const cx<T>*)v : F.b.as<cx<T>>();
+  if (c.graphs_ok && !c.prof) {  // the per-launch instrumentation needs the eager path
+    emg_ctx::CycleGraph* cg = nullptr;
+    for (auto& g : c.graphs)
+      if (g.b == b && g.z == z) cg = &g;
+    if (!cg) {
+      c.graphs.push_back({b, z, 0, nullptr, 0});
+      cg = &c.graphs.back();
+    }
+    if (!cg->exec && cg->uses >= 1) {
+      cg->exec = capture_cycle<T>(c, b, z, cg->kernels);
+      if (!cg->exec) c.graphs_ok = false;
+    }
+    if (cg->exec) {
+      CK(cudaGraphLaunch(cg->exec, c.st));
+      c.launches += cg->kernels;
+      return;
+    }
+    ++cg->uses;
+  }
   vcycle<T>(c, 0, b, z, true);
 }
 

@@ -87,3 +87,30 @@ def test_batch_reports_a_failing_job_without_disturbing_the_others():
         emg.solve_batch(jobs, tol=1e-8, max_iter=400, restart=5)
     for s in solvers:
         s.close()
+
+
+def test_graph_replayed_cycles_match_eager_cycles():
+    """On a stream of its own a handle replays the preconditioner cycle as a captured CUDA graph
+    (from the second use of each Krylov slot on); with the per-launch instrumentation on it runs
+    the same cycle eagerly. Both give the same iterate, bit for bit, and the same count of kernels."""
+    import torch
+    from paper_2307_03242_gb300 import emg
+    w, srcs = _instances()[0]
+    s = emg.Solver(emg.params_from_workload(w, 32), w.lam, w.mu, w.rho, stream=torch.cuda.Stream())
+    b = torch.from_numpy(srcs[0]).cuda()
+    torch.cuda.synchronize()
+    xg, xe = torch.zeros_like(b), torch.zeros_like(b)
+    s.solve(b, xg, tol=1e-8, max_iter=60, restart=5)  # captures the graphs
+    xg.zero_()
+    torch.cuda.synchronize()
+    s.profile_read(emg.K_ALL)
+    st_g = s.solve(b, xg, tol=1e-8, max_iter=60, restart=5)
+    n_g = s.profile_read(emg.K_ALL)["launches"]
+    s.profile(True)
+    st_e = s.solve(b, xe, tol=1e-8, max_iter=60, restart=5)
+    s.profile(False)
+    n_e = s.profile_read(emg.K_ALL)["launches"]
+    assert st_g["iterations"] == st_e["iterations"]
+    assert torch.equal(xg, xe)
+    assert n_g == n_e
+    s.close()

@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4"],
                     help="c4: the 64-instance batch of 2D solves (emg_solve_batch)")
     ap.add_argument("--instances", type=int, default=64, help="c4: number of instances")
+    ap.add_argument("--workers", type=int, default=0, help="c4: host worker threads (0: one per instance)")
     ap.add_argument("--restart", type=int, default=None, help="FGMRES restart length (default: the workload's)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed plain-FP64 solves (after 1 warm-up)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -431,7 +432,7 @@ def run_batch(args):
     def batch():
         for _, _, x in jobs:
             x.zero_()
-        return emg.solve_batch(jobs, tol=tol, max_iter=2000, restart=restart)
+        return emg.solve_batch(jobs, tol=tol, max_iter=2000, restart=restart, workers=args.workers)
 
     for _ in range(args.warmup):
         res = batch()

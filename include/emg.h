@@ -123,7 +123,11 @@ emg_status emg_vcycle(emg_handle h, const void* b, void* x, int zero_guess);
  * V-cycle as preconditioner (Sec. 3.2, 5). x: in = initial guess, out = solution. Stops when the
  * true relative residual ||b - H x|| / ||b|| <= tol or after max_iter iterations
  * (EMG_NOT_CONVERGED; x then holds the last iterate). restart in 1..64. b, x: FP64 vectors.
- * stats may be NULL. Synchronises the stream. */
+ * stats may be NULL. Synchronises the stream. On a stream other than the legacy default stream
+ * the preconditioner cycle is captured into a CUDA graph on the second use of each Krylov slot
+ * and replayed from then on (same kernels, bitwise the same result); while profiling is on, or
+ * if a capture fails, it runs launch by launch. So no other thread may launch work into the
+ * handle's stream during the call. */
 emg_status emg_solve(emg_handle h, const void* b, void* x, double tol, int max_iter, int restart,
                      emg_stats* stats);
 
@@ -136,10 +140,11 @@ emg_status emg_solve_host(emg_handle h, const double* b_host, double* x_host, do
  * grids, media, frequencies or sources at once (the batched use the paper's Sec. 5 experiments
  * imply -- one solve per source and frequency -- but do not describe; no counterpart in the
  * paper's solver itself). Small grids cannot fill the GPU on their own, so the solves run
- * concurrently: up to `workers` host threads (0: one per distinct handle, at most 64) each drive
- * a handle's solves on that handle's own stream, and the GPU interleaves their kernels. Give
- * every handle its own stream to get the overlap; handles may repeat (several right-hand sides
- * of one system), and then their jobs run one after another. b[k], x[k]: FP64 device vectors of
+ * concurrently: up to `workers` host threads (0: one per distinct stream, at most 64) each drive
+ * the solves of one stream's handles, and the GPU interleaves the kernels of the streams. Give
+ * every handle its own stream to get the overlap; jobs whose handles share a stream, and
+ * repeated handles (several right-hand sides of one system), run one after another on one
+ * worker. b[k], x[k]: FP64 device vectors of
  * handle k's size; stats and status: arrays of count entries, or NULL. Returns EMG_OK, the first
  * (lowest k) error, or EMG_NOT_CONVERGED if any job stopped at max_iter; status[k] holds each
  * job's own result. The handles must not be used by other threads during the call. */

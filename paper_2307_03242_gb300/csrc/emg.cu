@@ -106,7 +106,7 @@ struct emg_ctx {
   DBuf ff_mu, ff_mun, ff_cp, ff_m1, ff_m2;  // 2D: FP64 coefficients as float-float pairs
   DBuf ff3_edge[3], ff3_m[3];              // 3D: edge mu per orientation, face masses
   DBuf cinv;               // dense inverse of the coarsest operator (cycle precision)
-  DBuf rscr;               // 2D: the fine residual between the residual and restriction kernels
+  DBuf rscr;               // the fine residual between the residual and restriction kernels
   int cn = 0;
   // Krylov workspace
   int km = 0;
@@ -310,13 +310,10 @@ void residual_restrict(emg_ctx& c, int l, const cx<T>* b, const cx<T>* x, cx<T>*
   Grid<T> g = level_grid<T>(c, l);
   const double cw = 2.0 * sizeof(T);
   ProfScope ps(c, EMG_K_RESTRICT, l, (double)L.ncell * (2 * (c.dim + 1) * cw + 3 * sizeof(T)) + C.ncell * (c.dim + 1) * cw);
-  if (c.dim == 2) {
-    launch_restrict2<T>(g, b, x, bc, C.n, c.rscr.as<cx<T>>(), c.st);
-    LAUNCHED(c);  // residual, then restriction
-  } else {
-    launch_restrict3<T>(g, b, x, bc, C.n, 0, c.st);
-  }
+  if (c.dim == 2) launch_restrict2<T>(g, b, x, bc, C.n, c.rscr.as<cx<T>>(), c.st);
+  else launch_restrict3<T>(g, b, x, bc, C.n, c.rscr.as<cx<T>>(), c.st);
   CKL();
+  LAUNCHED(c);  // residual, then restriction
   LAUNCHED(c);
 }
 
@@ -681,7 +678,7 @@ void build(emg_ctx& c) {
     CK(cudaMemset(L.x.p, 0, L.x.bytes));
     CK(cudaMemset(L.alt.p, 0, L.alt.bytes));
   }
-  if (d == 2 && c.L > 1) c.rscr.alloc((d + 1) * c.lv[0].ncell * sizeof(cx<T>));
+  if (c.L > 1) c.rscr.alloc((d + 1) * c.lv[0].ncell * sizeof(cx<T>));
   // finest material in FP64 for the outer operator
   Level& F = c.lv[0];
   std::vector<double> cp(F.ncell);
@@ -1106,6 +1103,8 @@ void check_ptr(const void* p, const char* what) {
 
 void emg_set_last_error(const std::string& msg) { g_err = msg; }
 
+
+
 extern "C" {
 
 const char* emg_last_error(void) { return g_err.c_str(); }
@@ -1277,16 +1276,18 @@ emg_status emg_solve_batch(const emg_handle* handles, int count, const void* con
   if (max_iter < 0) raise(EMG_ERR_INVALID, "max_iter < 0");
   if (!(tol >= 0.0)) raise(EMG_ERR_INVALID, "tol must be >= 0");
   if (workers < 0) raise(EMG_ERR_INVALID, "workers < 0");
-  // Jobs that share a handle run one after another on one worker (they share its workspaces).
-  std::map<emg_ctx*, std::vector<int>> by_handle;
+  // Jobs whose handles share a stream (in particular jobs of one handle, which also share its
+  // workspaces) run one after another on one worker: a stream is driven by one thread at a time,
+  // and a cycle capture on it must not see another thread's launches.
+  std::map<cudaStream_t, std::vector<int>> by_stream;
   std::vector<std::vector<int>> groups;
   for (int k = 0; k < count; ++k) {
     emg_ctx* c = checked(handles[k]);
     check_ptr(b[k], "b[k]");
     check_ptr(x[k], "x[k]");
-    by_handle[c].push_back(k);
+    by_stream[c->st].push_back(k);
   }
-  for (auto& kv : by_handle) groups.push_back(kv.second);
+  for (auto& kv : by_stream) groups.push_back(kv.second);
   // The largest systems first, so that the last ones to start are short.
   std::sort(groups.begin(), groups.end(), [&](const std::vector<int>& a, const std::vector<int>& g) {
     return handles[a[0]]->nvec() * a.size() > handles[g[0]]->nvec() * g.size();
@@ -1320,7 +1321,12 @@ emg_status emg_solve_batch(const emg_handle* handles, int count, const void* con
   int dev0 = 0;
   CK(cudaGetDevice(&dev0));
   std::vector<std::thread> pool;
-  for (int t = 1; t < nw; ++t) pool.emplace_back(work);
+  pool.reserve(nw);
+  try {
+    for (int t = 1; t < nw; ++t) pool.emplace_back(work);
+  } catch (...) {
+    // fewer threads than asked for: the ones that started and the calling thread do the rest
+  }
   work();  // the calling thread is one of the workers
   for (auto& t : pool) t.join();
   CK(cudaSetDevice(dev0));

@@ -122,57 +122,6 @@ __global__ void __launch_bounds__(BX * BY * BZ) vanka(Grid<T> g, const cx<T>* __
   p[q] = zero_in ? w * d[6] : p[q] + w * d[6];
 }
 
-// b_c = R (b - H_s x): R_u_c = [1 2 1]/4 along c x [1 1]/2 x [1 1]/2; R_p = mean of 8 children.
-template <typename T>
-__global__ void __launch_bounds__(BX * BY * BZ) restrict_residual(Grid<T> g, const cx<T>* __restrict__ b,
-                                                                 const cx<T>* __restrict__ x, cx<T>* __restrict__ bc,
-                                                                 int nxc, int nyc, int nzc, int zero_x) {
-  const int I = blockIdx.x * BX + threadIdx.x;
-  const int J = blockIdx.y * BY + threadIdx.y;
-  const int K = blockIdx.z * BZ + threadIdx.z;
-  if (I >= nxc || J >= nyc || K >= nzc) return;
-  const size_t N = (size_t)g.nx * g.ny * g.nz, Nc = (size_t)nxc * nyc * nzc;
-  const size_t qc = ((size_t)K * nyc + J) * nxc + I;
-  const cx<T>* u[3] = {x, x + N, x + 2 * N};
-  const cx<T>* p = x + 3 * N;
-  const int IC[3] = {I, J, K};
-  for (int c = 0; c < 3; ++c) {
-    cx<T> acc = czero<T>();
-    if (IC[c] >= 1) {
-      int ci, cj, ck;
-      s3::unit(c, ci, cj, ck);
-      for (int s = -1; s <= 1; ++s) {
-        const T ws = s == 0 ? T(2) : T(1);
-        for (int a = 0; a < 2; ++a)
-          for (int bb = 0; bb < 2; ++bb) {
-            // fine face: 2*IC[c]+s along c, 2*IC[o]+{0,1} along the other axes
-            int f[3] = {2 * I, 2 * J, 2 * K};
-            const int o1 = (c + 1) % 3, o2 = (c + 2) % 3;
-            f[c] += s;
-            f[o1] += a;
-            f[o2] += bb;
-            const size_t qf = s3::lin(g, f[0], f[1], f[2]);
-            cx<T> v = b[c * N + qf];
-            if (!zero_x) v = v - s3::row_u(c, u[c], p, g, f[0], f[1], f[2]);
-            acc = acc + ws * v;
-          }
-      }
-      acc = T(0.0625) * acc;
-    }
-    bc[c * Nc + qc] = acc;
-  }
-  cx<T> acc = czero<T>();
-  for (int c3 = 0; c3 < 2; ++c3)
-    for (int c2 = 0; c2 < 2; ++c2)
-      for (int c1 = 0; c1 < 2; ++c1) {
-        const int fi = 2 * I + c1, fj = 2 * J + c2, fk = 2 * K + c3;
-        cx<T> v = b[3 * N + s3::lin(g, fi, fj, fk)];
-        if (!zero_x) v = v - s3::row_p(u, p, g, fi, fj, fk);
-        acc = acc + v;
-      }
-  bc[3 * Nc + qc] = T(0.125) * acc;
-}
-
 // x += P e: P_u_c = [1 2 1]/2 (transposed) along c x [1 3 3 1]/4 (transposed) along the others;
 // P_p trilinear.
 template <typename T>

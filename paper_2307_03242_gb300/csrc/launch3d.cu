@@ -1,6 +1,9 @@
 // 3D kernel launchers (explicit instantiations for the FP32 and FP64 cycles and the FP64 apply).
 #include "vanka3d_tile.cuh"
+#include "residual3d.cuh"
 #include "launch.h"
+
+#include <atomic>
 
 namespace {
 dim3 g3(int nx, int ny, int nz) {
@@ -17,11 +20,14 @@ template <typename T>
 void launch_vanka3(const Grid<T>& g, const cx<T>* b, const cx<T>* uin, cx<T>* uout, cx<T>* p, int colour, T w,
                    int zero_in, cudaStream_t st) {
   if (g.nx >= 16 && g.ny >= 8 && g.nz >= 4) {
-    static bool attr_set[2] = {false, false};
+    // the dynamic shared memory limit is a per-device function attribute: set it once per device
+    static std::atomic<bool> attr_set[64];
     const size_t smem = sizeof(k3t::Tile<T>);
-    if (!attr_set[sizeof(T) == 8]) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev].load()) {
       cudaFuncSetAttribute(k3t::vanka_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr_set[sizeof(T) == 8] = true;
+      if (dev >= 0 && dev < 64) attr_set[dev].store(true);
     }
     dim3 grid((g.nx + k3t::TX - 1) / k3t::TX, (g.ny + k3t::TY - 1) / k3t::TY, (g.nz + k3t::TZ - 1) / k3t::TZ);
     k3t::vanka_tile<T><<<grid, k3t::NT, smem, st>>>(g, b, uin, uout, p, colour, w, zero_in);
@@ -30,9 +36,10 @@ void launch_vanka3(const Grid<T>& g, const cx<T>* b, const cx<T>* uin, cx<T>* uo
   }
 }
 template <typename T>
-void launch_restrict3(const Grid<T>& g, const cx<T>* b, const cx<T>* x, cx<T>* bc, const int nc[3], int zero_x,
+void launch_restrict3(const Grid<T>& g, const cx<T>* b, const cx<T>* x, cx<T>* bc, const int nc[3], cx<T>* r,
                       cudaStream_t st) {
-  k3::restrict_residual<T><<<g3(nc[0], nc[1], nc[2]), b3(), 0, st>>>(g, b, x, bc, nc[0], nc[1], nc[2], zero_x);
+  k3::residual<T><<<g3(g.nx, g.ny, g.nz), b3(), 0, st>>>(g, b, x, r);
+  k3::restrict_r<T><<<g3(nc[0], nc[1], nc[2]), b3(), 0, st>>>(r, bc, g.nx, g.ny, g.nz, nc[0], nc[1], nc[2]);
 }
 template <typename T>
 void launch_prolong3(const cx<T>* e, cx<T>* x, const int n[3], const int nc[3], cudaStream_t st) {
@@ -44,7 +51,7 @@ template void launch_apply3<double, double>(const Grid<double>&, const cx<double
 template void launch_apply3<double, float>(const Grid<double>&, const cx<float>*, const cx<double>*, double, cx<double>*, cudaStream_t);
 #define INST(T)                                                                                                   \
   template void launch_vanka3<T>(const Grid<T>&, const cx<T>*, const cx<T>*, cx<T>*, cx<T>*, int, T, int, cudaStream_t); \
-  template void launch_restrict3<T>(const Grid<T>&, const cx<T>*, const cx<T>*, cx<T>*, const int*, int, cudaStream_t); \
+  template void launch_restrict3<T>(const Grid<T>&, const cx<T>*, const cx<T>*, cx<T>*, const int*, cx<T>*, cudaStream_t); \
   template void launch_prolong3<T>(const cx<T>*, cx<T>*, const int*, const int*, cudaStream_t);
 INST(float)
 INST(double)

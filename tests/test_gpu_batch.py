@@ -114,3 +114,32 @@ def test_graph_replayed_cycles_match_eager_cycles():
     assert torch.equal(xg, xe)
     assert n_g == n_e
     s.close()
+
+
+def test_batch_with_handles_sharing_a_stream():
+    """Handles on one stream (a stream pool hands the same stream to several callers) are driven
+    by one worker, one after another: results equal the individual solves."""
+    import torch
+    from paper_2307_03242_gb300 import emg
+    insts = _instances()
+    shared = torch.cuda.Stream()
+    solvers, jobs = [], []
+    for k, (w, srcs) in enumerate(insts):
+        st = shared if k % 2 == 0 else torch.cuda.Stream()
+        s = emg.Solver(emg.params_from_workload(w, 32), w.lam, w.mu, w.rho, stream=st)
+        solvers.append(s)
+        b = torch.from_numpy(srcs[0]).cuda()
+        jobs.append((s, b, torch.zeros_like(b)))
+    torch.cuda.synchronize()
+    ref = []
+    for s, b, x in jobs:
+        s.solve(b, x, tol=1e-8, max_iter=400, restart=5)
+        ref.append(x.clone())
+        x.zero_()
+    torch.cuda.synchronize()
+    res = emg.solve_batch(jobs, tol=1e-8, max_iter=400, restart=5)
+    for st, r, (_, _, x) in zip(res, ref, jobs):
+        assert st["status"] == 0
+        assert torch.equal(x, r)
+    for s in solvers:
+        s.close()

@@ -89,8 +89,9 @@ def hot_kernel_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """(bytes per launch, ncu kernel time) from the committed ncu summary, if it matches the source."""
+def recorded_profile(key):
+    """A per-launch figure (DRAM bytes, FP32 flops) from the committed ncu summary of the dominant
+    kernel, if its sources still hash to the value recorded there; else None."""
     try:
         vals = {}
         with open(os.path.join(ROOT, HOT_KERNEL_PROFILE)) as f:
@@ -100,9 +101,18 @@ def recorded_traffic():
                     vals[k.strip()] = v.strip()
         if vals.get("source_hash") != hot_kernel_hash():
             return None
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[key])
     except Exception:
         return None
+
+
+def recorded_traffic():
+    return recorded_profile("dram_bytes_per_launch")
+
+
+# FP32 CUDA-core peak from the unit counts and the maximum clock: 152 SMs x 128 FP32 lanes x 2
+# flop (FMA) x 2.07 GHz. (A measured FFMA loop reached 67.8 TFLOP/s on this part.)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def load_peaks():
@@ -376,7 +386,8 @@ def main():
                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                         "frac": achieved / peak if achieved else None, "traffic": recorded_traffic(),
                         "launches": prof["launches"], "avg_launch_ms": prof["ms"] / max(prof["launches"], 1),
-                        "bytes_per_launch": prof["bytes"] / max(prof["launches"], 1)},
+                        "bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
+                        "fp32": fp32_fraction(prof)},
            "fine_level_ms_per_solve": dict({"smooth": prof["ms"] / args.steps},
                                            **{k: v["ms"] / args.steps for k, v in breakdown.items()}),
            "e2e": {"value": te2e, "unit": "s", "h2d_bytes_per_step": 2 * nvec * 16, "d2h_bytes_per_step": nvec * 16},
@@ -507,6 +518,17 @@ def run_batch(args):
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def fp32_fraction(prof):
+    """The dominant kernel's FP32 rate: its flops per launch (ncu FADD + FMUL + 2 FFMA thread
+    instructions of one launch, from the committed summary) over the live mean launch time."""
+    flops = recorded_profile("fp32_flops_per_launch")
+    if not flops or prof["ms"] <= 0:
+        return None
+    tf = flops / (prof["ms"] / max(prof["launches"], 1) * 1e-3) / 1e12
+    return {"achieved_tflops": tf, "peak_tflops": FP32_PEAK_TFLOPS, "peak_kind": "derived (unit counts x max clock)",
+            "frac": tf / FP32_PEAK_TFLOPS, "flops_per_launch": flops}
 
 
 def vcycle_bytes_per_cell(w, cw, rw):

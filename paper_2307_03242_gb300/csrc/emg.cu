@@ -114,8 +114,8 @@ struct emg_ctx {
   double* hred = nullptr;  // pinned
   size_t hb_bytes = 0;
   // instrumentation
-  bool prof = false;
   struct Rec { int cls; cudaEvent_t a, b; double bytes; };
+  bool prof = false;
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   double pms[EMG_K_COUNT] = {0};
@@ -128,17 +128,23 @@ struct emg_ctx {
   struct CycleGraph {
     const void* b;
     void* z;
+    bool timed;                 // captured with the instrumentation's event pairs as graph nodes
     int uses;                   // eager runs before capture (the first one warms lazy set-up)
     cudaGraphExec_t exec;
     int64_t kernels;            // kernel launches one replay stands for
+    std::vector<Rec> recs;      // timed: the event pairs every replay records
+    bool unread;                // timed: the last replay's events have not been read yet
   };
   std::vector<CycleGraph> graphs;
   bool graphs_ok = true;       // false once a capture failed: the cycle then runs eagerly
+  std::vector<Rec>* capture_recs = nullptr;  // during a timed capture: where its event pairs go
 
   size_t nvec() const { return (size_t)(dim + 1) * lv[0].ncell; }
   ~emg_ctx() {
-    for (auto& g : graphs)
+    for (auto& g : graphs) {
       if (g.exec) cudaGraphExecDestroy(g.exec);
+      for (auto& r : g.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    }
     if (hred) cudaFreeHost(hred);
     for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : pool) cudaEventDestroy(e);
@@ -208,7 +214,12 @@ struct ProfScope {
     if (!on) return;
     a = take();
     b = take();
-    CK(cudaEventRecord(a, c.st));
+    CK(record(a));
+  }
+  // In a stream capture a plain event record only expresses a dependency inside the graph; an
+  // external record becomes a node that records the event each time the graph runs.
+  cudaError_t record(cudaEvent_t e) {
+    return c.capture_recs ? cudaEventRecordWithFlags(e, c.st, cudaEventRecordExternal) : cudaEventRecord(e, c.st);
   }
   cudaEvent_t take() {
     if (!c.pool.empty()) { cudaEvent_t e = c.pool.back(); c.pool.pop_back(); return e; }
@@ -218,14 +229,30 @@ struct ProfScope {
   }
   ~ProfScope() {
     if (!on) return;
-    cudaEventRecord(b, c.st);
-    c.recs.push_back({cls, a, b, bytes});
+    record(b);
+    (c.capture_recs ? *c.capture_recs : c.recs).push_back({cls, a, b, bytes});
   }
 };
 
+// Adds the times of a timed graph's last replay (complete: the caller has synchronised since).
+void harvest(emg_ctx& c, emg_ctx::CycleGraph& g) {
+  if (!g.unread) return;
+  for (auto& r : g.recs) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    c.pms[r.cls] += ms;
+    c.pn[r.cls] += 1;
+    c.pbytes[r.cls] += r.bytes;
+  }
+  g.unread = false;
+}
+
 void prof_flush(emg_ctx& c) {
-  if (c.recs.empty()) return;
+  bool any = !c.recs.empty();
+  for (auto& g : c.graphs) any = any || g.unread;
+  if (!any) return;
   CK(cudaStreamSynchronize(c.st));
+  for (auto& g : c.graphs) harvest(c, g);
   for (auto& r : c.recs) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, r.a, r.b));
@@ -858,18 +885,21 @@ void outer_apply(emg_ctx& c, const void* x, bool x32, const cx<double>* b, doubl
 // Capture vcycle(0, b, z) into a graph; nullptr (and graphs off for this handle) if the capture
 // or the instantiation fails, e.g. because the runtime cannot capture a launch kind.
 template <typename T>
-cudaGraphExec_t capture_cycle(emg_ctx& c, const cx<T>* b, cx<T>* z, int64_t& kernels) {
+cudaGraphExec_t capture_cycle(emg_ctx& c, const cx<T>* b, cx<T>* z, int64_t& kernels,
+                              std::vector<emg_ctx::Rec>* recs) {
   const int64_t l0 = c.launches;
   if (cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
   bool ok = true;
+  c.capture_recs = recs;  // with the instrumentation on, its event pairs become graph nodes
   try {
     vcycle<T>(c, 0, b, z, true);
   } catch (const EmgError&) {
     ok = false;
   }
+  c.capture_recs = nullptr;
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(c.st, &g);
   kernels = c.launches - l0;
@@ -886,21 +916,30 @@ void precondition(emg_ctx& c, const cx<double>* v, cx<T>* z) {
   Level& F = c.lv[0];
   // FP32 cycle: its right-hand side was written in FP32 to F.b by the update that produced v
   const cx<T>* b = std::is_same<T, double>::value ? (const cx<T>*)v : F.b.as<cx<T>>();
-  if (c.graphs_ok && !c.prof) {  // the per-launch instrumentation needs the eager path
+  if (c.graphs_ok) {
+    // with the instrumentation on, a graph that records its own event pairs (they are graph
+    // nodes, so every replay times its kernels); otherwise one without
+    const bool timed = c.prof;
     emg_ctx::CycleGraph* cg = nullptr;
     for (auto& g : c.graphs)
-      if (g.b == b && g.z == z) cg = &g;
+      if (g.b == b && g.z == z && g.timed == timed) cg = &g;
     if (!cg) {
-      c.graphs.push_back({b, z, 0, nullptr, 0});
+      c.graphs.push_back({b, z, timed, 0, nullptr, 0, {}, false});
       cg = &c.graphs.back();
     }
     if (!cg->exec && cg->uses >= 1) {
-      cg->exec = capture_cycle<T>(c, b, z, cg->kernels);
-      if (!cg->exec) c.graphs_ok = false;
+      cg->exec = capture_cycle<T>(c, b, z, cg->kernels, timed ? &cg->recs : nullptr);
+      if (!cg->exec) {
+        c.graphs_ok = false;
+        for (auto& r : cg->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        cg->recs.clear();
+      }
     }
     if (cg->exec) {
+      harvest(c, *cg);  // the previous replay of this graph finished: the loop has synchronised since
       CK(cudaGraphLaunch(cg->exec, c.st));
       c.launches += cg->kernels;
+      cg->unread = timed && !cg->recs.empty();
       return;
     }
     ++cg->uses;

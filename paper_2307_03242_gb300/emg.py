@@ -253,41 +253,68 @@ class Solver:
     def _n(self, level=0):
         return int(np.prod(self.vec_shape(level)))
 
+    def _in(self):
+        """Order the handle's stream after the caller's current stream (the caller's tensors may
+        still be in flight there)."""
+        import torch
+        cur = torch.cuda.current_stream()
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
+
+    def _out(self):
+        """Order the caller's current stream after the handle's (its outputs)."""
+        import torch
+        cur = torch.cuda.current_stream()
+        if cur.cuda_stream != self.stream.cuda_stream:
+            cur.wait_stream(self.stream)
+
     # -- entry points
     def apply(self, x, y, shifted=False):
         import torch
         n = self._n()
+        self._in()
         _check(LIB.emg_apply(self.h, 1 if shifted else 0, _ptr(x, torch.complex128, n, "x"),
                              _ptr(y, torch.complex128, n, "y")))
+        self._out()
         return y
 
     def vcycle(self, b, x, zero_guess=True):
         n = self._n()
+        self._in()
         _check(LIB.emg_vcycle(self.h, _ptr(b, self.cdtype, n, "b"), _ptr(x, self.cdtype, n, "x"),
                               1 if zero_guess else 0))
+        self._out()
         return x
 
     def smooth(self, level, b, x, sweeps):
         n = self._n(level)
+        self._in()
         _check(LIB.emg_smooth(self.h, level, _ptr(b, self.cdtype, n, "b"), _ptr(x, self.cdtype, n, "x"), sweeps))
+        self._out()
         return x
 
     def residual_restrict(self, level, b, x, bc):
         n, nc = self._n(level), self._n(level + 1)
+        self._in()
         _check(LIB.emg_residual_restrict(self.h, level, _ptr(b, self.cdtype, n, "b"), _ptr(x, self.cdtype, n, "x"),
                                          _ptr(bc, self.cdtype, nc, "b_coarse")))
+        self._out()
         return bc
 
     def prolong_correct(self, level, ec, x):
         n, nc = self._n(level), self._n(level + 1)
+        self._in()
         _check(LIB.emg_prolong_correct(self.h, level, _ptr(ec, self.cdtype, nc, "e_coarse"),
                                        _ptr(x, self.cdtype, n, "x")))
+        self._out()
         return x
 
     def coarse_solve(self, b, x):
         last = self.params.levels - 1
         n = self._n(last)
+        self._in()
         _check(LIB.emg_coarse_solve(self.h, _ptr(b, self.cdtype, n, "b"), _ptr(x, self.cdtype, n, "x")))
+        self._out()
         return x
 
     def solve(self, b, x, tol=1e-6, max_iter=1000, restart=20, history_cap=0):
@@ -299,8 +326,10 @@ class Solver:
             hist = (ctypes.c_double * history_cap)()
             st.history = hist
             st.history_cap = history_cap
+        self._in()
         s = _check(LIB.emg_solve(self.h, _ptr(b, torch.complex128, n, "b"), _ptr(x, torch.complex128, n, "x"),
                                  tol, max_iter, restart, ctypes.byref(st)), allow=(0, 5))
+        self._out()
         return self._stats(st, hist, s)
 
     def solve_host(self, b, x, tol=1e-6, max_iter=1000, restart=20, history_cap=0):

@@ -90,30 +90,44 @@ def test_batch_reports_a_failing_job_without_disturbing_the_others():
 
 
 def test_graph_replayed_cycles_match_eager_cycles():
-    """On a stream of its own a handle replays the preconditioner cycle as a captured CUDA graph
-    (from the second use of each Krylov slot on); with the per-launch instrumentation on it runs
-    the same cycle eagerly. Both give the same iterate, bit for bit, and the same count of kernels."""
+    """A handle on a stream of its own replays the preconditioner cycle as a captured CUDA graph
+    (from the second use of each Krylov slot on); a handle on the legacy default stream, where
+    capture is not possible, runs it launch by launch. Same iterate bit for bit, same kernel
+    count; with the instrumentation on, the graphs carry its event pairs, so both report the same
+    number of timed launches per kernel class."""
     import torch
     from paper_2307_03242_gb300 import emg
     w, srcs = _instances()[0]
-    s = emg.Solver(emg.params_from_workload(w, 32), w.lam, w.mu, w.rho, stream=torch.cuda.Stream())
+    p = emg.params_from_workload(w, 32)
+    sg = emg.Solver(p, w.lam, w.mu, w.rho, stream=torch.cuda.Stream())
+    se = emg.Solver(p, w.lam, w.mu, w.rho)  # torch's current stream: the legacy default stream
+    assert se.stream.cuda_stream == 0
     b = torch.from_numpy(srcs[0]).cuda()
     torch.cuda.synchronize()
-    xg, xe = torch.zeros_like(b), torch.zeros_like(b)
-    s.solve(b, xg, tol=1e-8, max_iter=60, restart=5)  # captures the graphs
-    xg.zero_()
-    torch.cuda.synchronize()
-    s.profile_read(emg.K_ALL)
-    st_g = s.solve(b, xg, tol=1e-8, max_iter=60, restart=5)
-    n_g = s.profile_read(emg.K_ALL)["launches"]
-    s.profile(True)
-    st_e = s.solve(b, xe, tol=1e-8, max_iter=60, restart=5)
-    s.profile(False)
-    n_e = s.profile_read(emg.K_ALL)["launches"]
-    assert st_g["iterations"] == st_e["iterations"]
+    out = {}
+    for name, s in (("graph", sg), ("eager", se)):
+        x = torch.zeros_like(b)
+        s.solve(b, x, tol=1e-8, max_iter=60, restart=5)  # captures (graph handle)
+        s.profile_read(emg.K_ALL)
+        x.zero_()
+        torch.cuda.synchronize()
+        s.profile(True)
+        st = s.solve(b, x, tol=1e-8, max_iter=60, restart=5)  # timed graphs are captured here
+        s.profile_read(emg.K_SMOOTH)
+        x.zero_()
+        torch.cuda.synchronize()
+        st = s.solve(b, x, tol=1e-8, max_iter=60, restart=5)  # ... and replayed here
+        sm = s.profile_read(emg.K_SMOOTH)
+        s.profile(False)
+        out[name] = (st, x.clone(), s.profile_read(emg.K_ALL)["launches"], sm)
+    (stg, xg, ng, smg), (ste, xe, ne, sme) = out["graph"], out["eager"]
+    assert stg["iterations"] == ste["iterations"]
     assert torch.equal(xg, xe)
-    assert n_g == n_e
-    s.close()
+    assert ng == ne
+    assert smg["launches"] == sme["launches"] > 0 and smg["ms"] > 0
+    assert smg["bytes"] == sme["bytes"]
+    sg.close()
+    se.close()
 
 
 def test_batch_with_handles_sharing_a_stream():

@@ -56,6 +56,7 @@ typedef enum {
 
 enum { EMG_COARSE_DENSE = 0, EMG_COARSE_SMOOTH = 1 };
 enum { EMG_CYCLE_V = 0, EMG_CYCLE_W = 1, EMG_CYCLE_K = 2 };
+enum { EMG_VANKA_FULL = 0, EMG_VANKA_ECONOMIC = 1 };
 
 /* Solver description. All lengths in the same unit as h. */
 typedef struct {
@@ -83,6 +84,10 @@ typedef struct {
   double level_alpha[EMG_MAX_LEVELS]; /* shift of level l's cycle operator when > 0, else alpha (the
                                paper raises the shift as levels are added, Sec. 5.2; a deeper shift on
                                the coarsest level keeps its smoothing iteration convergent) */
+  int32_t smoother;         /* EMG_VANKA_FULL: each cell's whole (2d+1)^2 block is inverted (the
+                               paper's solves); EMG_VANKA_ECONOMIC: its displacement part is replaced
+                               by its diagonal (the paper's LFA variant, Sec. 2.3), in red-black
+                               order here */
 } emg_params;
 
 typedef struct {

@@ -31,7 +31,7 @@ DEFAULT_DAMPING = {1: 0.55, 2: 0.55, 3: 0.35, 4: 0.25, 5: 0.2, 6: 0.2, 7: 0.2, 8
 class Hierarchy:
     def __init__(self, pb: Problem, levels: int, alpha: float, damping=None, nu_pre: int = 2,
                  nu_post: int = 2, coarse: str = "dense", coarse_sweeps: int = 0,
-                 coarse_damping: float = 1.0, cycle: str = "V"):
+                 coarse_damping: float = 1.0, cycle: str = "V", smoother: str = "full"):
         self.levels = levels
         self.cycle = cycle
         self.gamma_cycle = {"V": 1, "W": 2, "K": 2}[cycle]
@@ -51,7 +51,8 @@ class Hierarchy:
         self.P = [prolongation(self.pbs[l], self.pbs[l + 1]) for l in range(levels - 1)]
         self.idx = [cell_dofs(p) for p in self.pbs]
         self.colour = [cell_colour(p) for p in self.pbs]
-        self.V = [cell_blocks(self.H[l], self.idx[l]) for l in range(levels)]
+        self.smoother = smoother
+        self.V = [cell_blocks(self.H[l], self.idx[l], economic=smoother == "economic") for l in range(levels)]
         last = levels - 1
         self.act_c = active_mask(self.pbs[last])
         if coarse == "dense":

@@ -55,8 +55,10 @@ def cell_colour(pb: Problem):
     return (sum(g.ravel() for g in grids) % 2).astype(np.int64)
 
 
-def cell_blocks(H, idx):
-    """(ncell, k, k) local matrices V_cell[a, b] = H[idx[a], idx[b]]; identity where excluded."""
+def cell_blocks(H, idx, economic=False):
+    """(ncell, k, k) local matrices V_cell[a, b] = H[idx[a], idx[b]]; identity where excluded.
+    economic: the displacement part (the first k-1 rows and columns) is replaced by its diagonal
+    ("economic Vanka", Section 2.3); the couplings to the pressure and its diagonal are kept."""
     ncell, k = idx.shape
     V = np.zeros((ncell, k, k), dtype=np.complex128)
     for a in range(k):
@@ -68,6 +70,11 @@ def cell_blocks(H, idx):
         V[idx[:, a] < 0, a, :] = 0.0
         V[:, :, a][idx[:, a] < 0] = 0.0
         V[idx[:, a] < 0, a, a] = 1.0
+    if economic:
+        for a in range(k - 1):
+            for b in range(k - 1):
+                if a != b:
+                    V[:, a, b] = 0.0
     return V
 
 

@@ -188,6 +188,7 @@ Grid<T> make_grid(const emg_ctx& c, int l, bool shifted, const void* mu, const v
   g.cp = (const T*)cp;
   g.abl_tab[0] = g.abl_tab[1] = g.abl_tab[2] = nullptr;
   for (int a = 0; a < 3; ++a) { g.zlo[a] = 1; g.zhi[a] = 0; }
+  g.economic = p.smoother == EMG_VANKA_ECONOMIC ? 1 : 0;
   return g;
 }
 
@@ -1107,6 +1108,7 @@ void check_params(const emg_params* p) {
   if (p->cycle_precision != 32 && p->cycle_precision != 64) raise(EMG_ERR_INVALID, "cycle_precision must be 32 or 64");
   if (p->cycle_type != EMG_CYCLE_V && p->cycle_type != EMG_CYCLE_W && p->cycle_type != EMG_CYCLE_K)
     raise(EMG_ERR_INVALID, "unknown cycle_type");
+  if (p->smoother != EMG_VANKA_FULL && p->smoother != EMG_VANKA_ECONOMIC) raise(EMG_ERR_INVALID, "unknown smoother");
   if (p->coarse_solver != EMG_COARSE_DENSE && p->coarse_solver != EMG_COARSE_SMOOTH)
     raise(EMG_ERR_INVALID, "unknown coarse_solver");
   if (p->coarse_solver == EMG_COARSE_SMOOTH && p->coarse_sweeps < 1 && p->levels > 0)

@@ -99,6 +99,8 @@ struct Grid {
   // both k h and (k+1/2) h (empty when zlo > zhi). Kernels whose whole window lies inside it take
   // a variant that skips the absorbing-layer terms; the result is the same.
   int zlo[3] = {1, 1, 1}, zhi[3] = {0, 0, 0};
+  // Economic Vanka: the cell block's displacement part is replaced by its diagonal (Sec. 2.3).
+  int economic = 0;
   HD bool abl_free(int a, int lo, int hi) const { return lo >= zlo[a] && hi <= zhi[a]; }
 };
 

@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(BX * BY * BZ) vanka(Grid<T> g, const cx<T>* __
                                    : b[c * N + q + stride[c]] - s3::row_u(c, u[c], (const cx<T>*)p, g, i + ci, j + cj, k + ck);
     }
     s3::block_u(g, c, i, j, k, a[c][0], a[c][1], a[c][2], a[c][3]);
+    if (g.economic) a[c][1] = a[c][2] = czero<T>();
   }
   r[6] = zero_in ? b[3 * N + q] : b[3 * N + q] - s3::row_p(u, (const cx<T>*)p, g, i, j, k);
   cell_solve(a, ex, g.ih, s3::wt(g.beta, 0, 0), s3::mat(g.cp, g, i, j, k), r, d);

@@ -82,6 +82,7 @@ extern "C" emg_status emg_smooth_noalloc(const emg_params* p, const float* mu, c
   g.rho = rho;
   g.cp = cp;
   g.abl_tab[0] = g.abl_tab[1] = g.abl_tab[2] = nullptr;  // profile evaluated in the kernel
+  g.economic = p->smoother == EMG_VANKA_ECONOMIC ? 1 : 0;
   double w = p->damping[0];
   if (!(w > 0.0)) w = p->levels <= 2 ? 0.55 : p->levels == 3 ? 0.35 : p->levels == 4 ? 0.25 : 0.2;
   cudaStream_t st = (cudaStream_t)cuda_stream;

@@ -197,6 +197,7 @@ HD void vanka_cell(const Grid<T>& g, const cx<T>* __restrict__ b, const cx<T>* _
   a2[3] = mkc<T>(t0 * ih2 * (mnC + mnD + mc + mu9[2][1]), T(0)) - g.beta * mN;
   a2[1] = mkc<T>(ih2 * (-t0 * mc + t1 * (mnA + mnB)), T(0)) - g.sm * mN;
   a2[2] = mkc<T>(ih2 * (-t0 * mc + t1 * (mnC + mnD)), T(0)) - g.sm * mS;
+  if (g.economic) a1[1] = a1[2] = a2[1] = a2[2] = czero<T>();
   const bool ex[4] = {exW, exE, exS, exN};
   cell_solve(a1, a2, ex, ih, t0, ldg(g.cp + k), r, d);
 

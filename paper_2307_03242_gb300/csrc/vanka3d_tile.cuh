@@ -205,6 +205,7 @@ HD void tile_compute(const Tile<T>& s, const Grid<T>& g, cx<T>* uout, cx<T>* p, 
     a[c][3] = mkc<T>(ih2 * w00 * (mq + MU(sc[0], sc[1], sc[2]) + ehi), T(0)) - g.beta * mhi;
     a[c][1] = mkc<T>(ih2 * (-w00 * mq + w10 * elo), T(0)) - g.sm * mhi;
     a[c][2] = mkc<T>(ih2 * (-w00 * mq + w10 * ehi), T(0)) - g.sm * mlo;
+    if (g.economic) a[c][1] = a[c][2] = czero<T>();
     (void)t1;
     (void)t2;
   }

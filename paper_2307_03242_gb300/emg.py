@@ -17,6 +17,7 @@ MAX_LEVELS = 10
 COARSE_DENSE, COARSE_SMOOTH = 0, 1
 CYCLE_V, CYCLE_W, CYCLE_K = 0, 1, 2
 K_SMOOTH, K_RESTRICT, K_PROLONG, K_APPLY64, K_KRYLOV = range(5)
+VANKA_FULL, VANKA_ECONOMIC = 0, 1
 K_ALL = 5
 
 STATUS = {0: "EMG_OK", 1: "EMG_ERR_INVALID", 2: "EMG_ERR_NOMEM", 3: "EMG_ERR_CUDA", 4: "EMG_ERR_NONFINITE",
@@ -37,7 +38,7 @@ class _Params(ctypes.Structure):
                 ("damping", ctypes.c_double * MAX_LEVELS), ("coarse_solver", ctypes.c_int32),
                 ("coarse_sweeps", ctypes.c_int32), ("coarse_damping", ctypes.c_double),
                 ("cycle_precision", ctypes.c_int32), ("cycle_type", ctypes.c_int32),
-                ("level_alpha", ctypes.c_double * MAX_LEVELS)]
+                ("level_alpha", ctypes.c_double * MAX_LEVELS), ("smoother", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -111,6 +112,7 @@ class Params:
     cycle_precision: int = 32
     cycle_type: int = CYCLE_V
     level_alpha: object = None       # per-level shift list (entries <= 0 mean `alpha`)
+    smoother: int = 0                # VANKA_FULL or VANKA_ECONOMIC
 
     def to_c(self) -> _Params:
         p = _Params()
@@ -129,6 +131,7 @@ class Params:
         la = list(self.level_alpha) if self.level_alpha is not None else []
         for l in range(MAX_LEVELS):
             p.level_alpha[l] = float(la[l]) if l < len(la) else 0.0
+        p.smoother = int(self.smoother)
         return p
 
 
@@ -139,7 +142,8 @@ def params_from_workload(w, cycle_precision=32, **over) -> Params:
               coarse_solver=COARSE_DENSE if w.coarse == "dense" else COARSE_SMOOTH,
               coarse_sweeps=w.coarse_sweeps, coarse_damping=w.coarse_damping, cycle_precision=cycle_precision,
               cycle_type={"V": CYCLE_V, "W": CYCLE_W, "K": CYCLE_K}[getattr(w, "cycle", "V")],
-              level_alpha=w.level_alphas() if hasattr(w, "level_alphas") else None)
+              level_alpha=w.level_alphas() if hasattr(w, "level_alphas") else None,
+              smoother=VANKA_ECONOMIC if getattr(w, "smoother", "full") == "economic" else VANKA_FULL)
     kw.update(over)
     return Params(**kw)
 

@@ -15,7 +15,8 @@ def oracle_hierarchy(w, pb=None, damping=None):
     pb = pb or oracle_problem(w)
     return oracle.Hierarchy(pb, w.levels, w.level_alphas(), w.damping if damping is None else damping,
                             nu_pre=w.nu_pre, nu_post=w.nu_post, coarse=w.coarse,
-                            coarse_sweeps=w.coarse_sweeps, coarse_damping=w.coarse_damping, cycle=w.cycle)
+                            coarse_sweeps=w.coarse_sweeps, coarse_damping=w.coarse_damping, cycle=w.cycle,
+                            smoother=w.smoother)
 
 
 def gpu_solver(w, prec, **over):

@@ -67,6 +67,37 @@ def test_red_black_vanka_matches_oracle(case, prec, sweeps, level):
     s.close()
 
 
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("level", [0, 1])
+def test_economic_vanka_matches_oracle(case, prec, level):
+    """Economic Vanka (the displacement part of each cell block replaced by its diagonal,
+    Sec. 2.3) in the red-black order of the full smoother."""
+    w = _w(case)
+    w.smoother = "economic"
+    pb = oracle_problem(w)
+    hier = oracle_hierarchy(w, pb)
+    s = gpu_solver(w, prec)
+    pl = hier.pbs[level]
+    b = random_field(pl, 23)
+    x = random_field(pl, 24)
+    ref = x.ravel()
+    for _ in range(2):
+        ref = oracle.red_black_sweep(hier.H[level], hier.V[level], hier.idx[level], hier.colour[level], b.ravel(), ref,
+                                     hier.w[level])
+    xt = to_gpu(x, prec)
+    s.smooth(level, to_gpu(b, prec), xt, 2)
+    assert rel_max(to_np(xt), ref) < TOL[prec] * (10 if prec == 64 else 5)
+    # and a whole cycle
+    bb = random_field(pb, 25)
+    ref_c = oracle.vcycle(hier, bb.ravel())
+    import torch
+    xc = torch.zeros(s.vec_shape(0), dtype=s.cdtype, device="cuda")
+    s.vcycle(to_gpu(bb, prec), xc, zero_guess=True)
+    assert rel(to_np(xc).ravel() * oracle.active_mask(pb), ref_c) < TOL_CYCLE[prec]
+    s.close()
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_cooperative_sweeps_match_per_launch_sweeps(prec):
     """Level 1 of a 1024x800 grid whose material is constant on 2x2 blocks is, cell for cell, the

@@ -220,3 +220,54 @@ def test_kcycle_gcr_steps_minimise_the_coarse_residual_and_converge():
     x, its, res2 = oracle.fgmres(lambda v: H @ v, lambda v: oracle.vcycle(hier, v), b, tol=1e-10, restart=20,
                                  max_iter=300)
     assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("n", [(8, 6), (4, 4, 4)])
+def test_economic_vanka_keeps_the_pressure_coupling_and_solves_the_pressure_row(n):
+    """Economic Vanka (Section 2.3): the displacement part of the cell block becomes its diagonal,
+    the couplings to the pressure stay. With w = 1 one cell update therefore zeroes the cell's
+    pressure residual exactly, and leaves on its faces the residual of the dropped off-diagonal
+    displacement couplings, -(V_full - V_econ) delta."""
+    w = small_heterogeneous(n, levels=1)
+    pb = _problem(w)
+    H = oracle.assemble(pb, 0.4)
+    idx = oracle.cell_dofs(pb)
+    Vf = oracle.cell_blocks(H, idx)
+    Ve = oracle.cell_blocks(H, idx, economic=True)
+    k = idx.shape[1]
+    off = ~np.eye(k - 1, dtype=bool)
+    assert np.all(Ve[:, :k - 1, :k - 1][:, off] == 0)
+    assert np.allclose(np.diagonal(Ve, axis1=1, axis2=2), np.diagonal(Vf, axis1=1, axis2=2))
+    assert np.array_equal(Ve[:, k - 1, :], Vf[:, k - 1, :]) and np.array_equal(Ve[:, :, k - 1], Vf[:, :, k - 1])
+    assert np.abs(Vf[:, :k - 1, :k - 1][:, off]).max() > 0  # something was dropped
+    rng = np.random.default_rng(1)
+    act = oracle.active_mask(pb)
+    b = w.rhs.ravel() * act
+    x = (rng.standard_normal(b.size) + 1j * rng.standard_normal(b.size)) * act
+    for cell in (0, pb.ncell // 2 + 1, pb.ncell - 1):
+        y = oracle.vanka_cell_update(H, Ve, idx, cell, b, x, 1.0)
+        ii = idx[cell]
+        ok = ii >= 0
+        r = b - H @ x
+        rl = np.where(ok, r[np.maximum(ii, 0)], 0.0)
+        delta = np.linalg.solve(Ve[cell], rl)
+        r_new = b - H @ y
+        assert abs(r_new[ii[-1]]) < 1e-12 * np.abs(b).max()
+        expect = -(Vf[cell] - Ve[cell]) @ delta
+        assert np.allclose(r_new[ii[:-1][ok[:-1]]], expect[:-1][ok[:-1]], atol=1e-12 * np.abs(b).max())
+
+
+def test_economic_vanka_cycle_fixes_the_solution_and_converges():
+    w = small_heterogeneous((16, 16), levels=2)
+    pb = _problem(w)
+    H = oracle.assemble(pb, 0.0)
+    act = oracle.active_mask(pb)
+    b = w.rhs.ravel() * act
+    xs = _direct(H, b, act)
+    hier = oracle.Hierarchy(pb, 2, 0.3, smoother="economic")
+    idx, col = hier.idx[0], hier.colour[0]
+    y = oracle.red_black_sweep(hier.H[0], hier.V[0], idx, col, hier.H[0] @ xs, xs, 0.5)
+    assert np.linalg.norm(y - xs) < 1e-12 * np.linalg.norm(xs)
+    x, its, res = oracle.fgmres(lambda v: H @ v, lambda v: oracle.vcycle(hier, v), b, tol=1e-10, restart=30,
+                                max_iter=300)
+    assert res <= 1e-10 and np.linalg.norm(x - xs) < 1e-8 * np.linalg.norm(xs)

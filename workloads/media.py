@@ -42,6 +42,7 @@ class Workload:
     coarse_damping: float = 1.0
     cycle: str = "V"               # "V" or "W"
     alpha_coarsest: float = 0.0    # shift of the coarsest level (0: alpha)
+    smoother: str = "full"         # "full" or "economic" Vanka
     extra: dict = field(default_factory=dict)
 
     @property

@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4"],
                     help="c4: the 64-instance batch of 2D solves (emg_solve_batch)")
     ap.add_argument("--instances", type=int, default=64, help="c4: number of instances")
+    ap.add_argument("--grid", type=int, default=None,
+                    help="cells per axis instead of the configuration's own (c1-c3; smaller cases for kernel captures)")
     ap.add_argument("--workers", type=int, default=0, help="c4: host worker threads (0: one per instance)")
     ap.add_argument("--restart", type=int, default=None, help="FGMRES restart length (default: the workload's)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed plain-FP64 solves (after 1 warm-up)")
@@ -62,7 +64,9 @@ def parse():
 
 def workload(name, args=None):
     from workloads import config_c1_homogeneous, config_c2_random2d, config_c3_layered3d
-    w = {"c1": config_c1_homogeneous, "c2": config_c2_random2d, "c3": config_c3_layered3d}[name]()
+    make = {"c1": config_c1_homogeneous, "c2": config_c2_random2d, "c3": config_c3_layered3d}[name]
+    grid = getattr(args, "grid", None) if args is not None else None
+    w = make(grid) if grid else make()
     if args is not None:
         for k in ("levels", "alpha", "damping", "cycle", "coarse_sweeps", "restart"):
             v = getattr(args, k, None)

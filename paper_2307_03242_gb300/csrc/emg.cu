@@ -1163,8 +1163,6 @@ emg_status emg_create(const emg_params* params, const double* lam, const double*
   c->L = params->levels;
   c->prec = params->cycle_precision;
   c->st = (cudaStream_t)cuda_stream;
-  CK(cudaGetDevice(&c->dev));
-  CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev));
   c->lv.resize(c->L);
   for (int l = 0; l < c->L; ++l) {
     Level& L = c->lv[l];
@@ -1195,6 +1193,9 @@ emg_status emg_create(const emg_params* params, const double* lam, const double*
         !(F.rho_h[k] > 0) || !(F.lam_h[k] + F.mu_h[k] > 0))
       raise(EMG_ERR_INVALID, "material must be finite with mu > 0, rho > 0, lambda + mu > 0 (cell " + std::to_string(k) + ")");
   }
+  // every argument check above needs no device; from here on the device is used
+  CK(cudaGetDevice(&c->dev));
+  CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev));
   if (c->prec == 32) build<float>(*c);
   else build<double>(*c);
   *out = c.release();

@@ -63,3 +63,22 @@ def test_batch_arguments_are_rejected_without_a_gpu():
     assert emg.LIB.emg_solve_batch(arr, 1, arr, arr, 1e-6, 10, 5, None, 0, None) == 1  # NULL handle
     assert b"NULL handle" in emg.LIB.emg_last_error()
     assert emg.LIB.emg_solve_batch(None, 1, arr, arr, 1e-6, 10, 5, None, 0, None) == 1
+
+
+def test_invalid_material_is_rejected_before_any_device_work():
+    import ctypes
+    import numpy as np
+    from paper_2307_03242_gb300 import emg
+    c = emg.Params(n=(8, 8), levels=2).to_c()
+    h = ctypes.c_void_p()
+    good = np.ones(64)
+    for bad_field in range(3):
+        mats = [good.copy(), good.copy(), good.copy()]
+        mats[bad_field][17] = np.nan if bad_field == 0 else -1.0
+        st = emg.LIB.emg_create(ctypes.byref(c), mats[0].ctypes.data, mats[1].ctypes.data, mats[2].ctypes.data, 0,
+                                None, ctypes.byref(h))
+        assert st == 1 and b"material" in emg.LIB.emg_last_error() and b"cell 17" in emg.LIB.emg_last_error()
+    c.smoother = 7
+    st = emg.LIB.emg_create(ctypes.byref(c), good.ctypes.data, good.ctypes.data, good.ctypes.data, 0, None,
+                            ctypes.byref(h))
+    assert st == 1 and b"smoother" in emg.LIB.emg_last_error()

@@ -299,3 +299,52 @@ def test_solve_host_buffers_match_device_solve():
     assert st["iterations"] == sh["iterations"]
     np.testing.assert_array_equal(xh, to_np(xt).ravel())
     s.close()
+
+
+def test_solve_edge_cases():
+    """Zero right-hand side (x = 0 at once, 0 iterations); max_iter = 0 (the initial guess comes
+    back untouched, EMG_NOT_CONVERGED with its true residual); a non-zero initial guess reaches
+    the same solution as a zero one."""
+    import torch
+    w = _w("2d")
+    pb = oracle_problem(w)
+    s = gpu_solver(w, 32)
+    act = oracle.active_mask(pb)
+    zero = torch.zeros(s.vec_shape(0), dtype=torch.complex128, device="cuda")
+    x = to_gpu(random_field(pb, 81), 64)
+    st = s.solve(zero, x, tol=1e-6, max_iter=50, restart=5)
+    assert st["converged"] and st["iterations"] == 0 and st["rel_residual"] == 0.0
+    assert torch.count_nonzero(x) == 0
+    b = w.rhs.ravel() * act
+    bt = to_gpu(b.reshape(oracle.dof_shape(pb)), 64)
+    x0 = to_gpu(random_field(pb, 82), 64)
+    x1 = x0.clone()
+    st = s.solve(bt, x1, tol=1e-6, max_iter=0, restart=5)
+    assert not st["converged"] and st["iterations"] == 0
+    assert torch.equal(x1, x0)
+    H = oracle.assemble(pb, 0.0)
+    r_true = np.linalg.norm(b - H @ to_np(x0).ravel()) / np.linalg.norm(b)
+    assert abs(st["rel_residual"] - r_true) < 1e-10 * r_true
+    xa = torch.zeros_like(bt)
+    s.solve(bt, xa, tol=1e-10, max_iter=500, restart=5)
+    xb = x0.clone()
+    s.solve(bt, xb, tol=1e-10, max_iter=500, restart=5)
+    assert rel(to_np(xb), to_np(xa)) < 1e-7
+    s.close()
+
+
+def test_single_level_hierarchy_is_an_exact_preconditioner():
+    """levels = 1 with the dense coarsest solve: the preconditioner is H_s^{-1} itself; with no
+    shift (alpha on the only level = the physical attenuation only, via a tiny alpha) FGMRES
+    converges in a couple of iterations (FP32 inverse, FP64 outer)."""
+    import torch
+    w = small_heterogeneous((16, 12), seed=4, levels=1, abl_cells=2, sigma_cells=2.0)
+    w.alpha = 1e-12
+    pb = oracle_problem(w)
+    s = gpu_solver(w, 64)
+    b = w.rhs.ravel() * oracle.active_mask(pb)
+    bt = to_gpu(b.reshape(oracle.dof_shape(pb)), 64)
+    xt = torch.zeros_like(bt)
+    st = s.solve(bt, xt, tol=1e-10, max_iter=10, restart=5)
+    assert st["converged"] and st["iterations"] <= 2
+    s.close()

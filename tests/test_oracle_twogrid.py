@@ -44,3 +44,24 @@ def test_spread_stencil_converges_faster_than_the_standard_one_in_every_column(m
     for r23 in rows[:3]:
         r1 = next(r for r in rows[3:] if r[2] == r23[2] and r[3] == r23[3])
         assert measured[r23] < measured[r1] - 0.2
+
+
+@pytest.mark.parametrize("row", _table1())
+def test_smoothing_factor_squared_matches_table1(row):
+    """mu_loc^2 of Table 1: two sweeps around an ideal coarse-grid correction (the projection
+    that removes the low frequencies), on a 32^2 periodic grid."""
+    from oracle.twogrid import smoothing_factor
+    mu2 = smoothing_factor(32, row[0], row[2], row[3], row[1], nu=2)
+    assert abs(mu2 - row[5]) <= 0.05, (row, mu2)
+
+
+def _sec42():
+    path = os.path.join(os.path.dirname(__file__), "golden", "sec42_mu_opt.txt")
+    return [tuple(float(v) for v in l.split()) for l in open(path) if l.strip() and not l.startswith("#")]
+
+
+@pytest.mark.parametrize("row", _sec42())
+def test_optimal_smoothing_factor_matches_section_4_2(row):
+    from oracle.twogrid import smoothing_factor
+    mu = smoothing_factor(32, row[0], row[2], row[3], row[1], nu=1)
+    assert abs(mu - row[4]) <= 0.05, (row, mu)

@@ -64,8 +64,16 @@ HD void residual_cell(const Grid<T>& g, const cx<T>* __restrict__ b, const cx<T>
     G1c = g1(1);
     if (INTERIOR || i >= 1) {
       const cx<T> lap = ih * (mu9[1][0] * G1m - mu9[1][1] * G1c + mnA * g2(1) - mnC * g2(2));
-      const cx<T> mass = g.beta * (m1(i, j) * A[1][1]) +
-                         g.sm * (m1(i - 1, j) * A[1][0] + m1(i + 1, j) * A[1][2] + m1(i, j - 1) * A[0][1] + m1(i, j + 1) * A[2][1]);
+      cx<T> mass;
+      if (NOABL) {  // every face mass is rho_f omega^2 (1 - i att): one complex scaling at the end
+        auto rs = [&](int ii, int jj) { return RHO(ii - 1, jj) + RHO(ii, jj); };
+        mass = mkc<T>(h5 * w2, -(h5 * w2) * att) *
+               (g.beta * (rs(i, j) * A[1][1]) +
+                g.sm * (rs(i - 1, j) * A[1][0] + rs(i + 1, j) * A[1][2] + rs(i, j - 1) * A[0][1] + rs(i, j + 1) * A[2][1]));
+      } else {
+        mass = g.beta * (m1(i, j) * A[1][1]) +
+               g.sm * (m1(i - 1, j) * A[1][0] + m1(i + 1, j) * A[1][2] + m1(i, j - 1) * A[0][1] + m1(i, j + 1) * A[2][1]);
+      }
       r[k] = ldg(b + k) - (lap - mass + ih * (pC - P(i - 1, j)));
     } else {
       r[k] = z;
@@ -90,8 +98,16 @@ HD void residual_cell(const Grid<T>& g, const cx<T>* __restrict__ b, const cx<T>
     H2c = (INTERIOR || j + 1 < ny) ? h2(1) : ih * (t1 * ((z - B[1][0]) + (z - B[1][2])) + t0 * (z - B[1][1]));
     if (INTERIOR || j >= 1) {
       const cx<T> lap = ih * (mnA * h1(0) - mnB * h1(1) + mu9[0][1] * H2m - mu9[1][1] * H2c);
-      const cx<T> mass = g.beta * (m2(i, j) * B[1][1]) +
-                         g.sm * (m2(i - 1, j) * B[1][0] + m2(i + 1, j) * B[1][2] + m2(i, j - 1) * B[0][1] + m2(i, j + 1) * B[2][1]);
+      cx<T> mass;
+      if (NOABL) {
+        auto rs = [&](int ii, int jj) { return RHO(ii, jj - 1) + RHO(ii, jj); };
+        mass = mkc<T>(h5 * w2, -(h5 * w2) * att) *
+               (g.beta * (rs(i, j) * B[1][1]) +
+                g.sm * (rs(i - 1, j) * B[1][0] + rs(i + 1, j) * B[1][2] + rs(i, j - 1) * B[0][1] + rs(i, j + 1) * B[2][1]));
+      } else {
+        mass = g.beta * (m2(i, j) * B[1][1]) +
+               g.sm * (m2(i - 1, j) * B[1][0] + m2(i + 1, j) * B[1][2] + m2(i, j - 1) * B[0][1] + m2(i, j + 1) * B[2][1]);
+      }
       r[N + k] = ldg(b + N + k) - (lap - mass + ih * (pC - P(i, j - 1)));
     } else {
       r[N + k] = z;

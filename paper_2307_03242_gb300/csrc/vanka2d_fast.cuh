@@ -131,18 +131,31 @@ HD void vanka_cell(const Grid<T>& g, const cx<T>* __restrict__ b, const cx<T>* _
       G1c = g1(1);
       G1p = g1(2);
       const cx<T> G2A = g2(0, 1), G2C = g2(0, 2), G2B = g2(1, 1), G2D = g2(1, 2);
-      // face masses m u at the u1 faces the two rows need
-      const cx<T> MUw = mW * A[1][1], MUe = mE * A[1][2];
-      const cx<T> MUww = m1(h5 * (R0[0] + R0[1]), -1, 0) * A[1][0];
-      const cx<T> MUee = m1(h5 * (R0[3] + R0[4]), 2, 0) * A[1][3];
-      const cx<T> MUws = m1(h5 * (Rm[0] + Rm[1]), 0, -1) * A[0][1];
-      const cx<T> MUwn = m1(h5 * (Rp[0] + Rp[1]), 0, 1) * A[2][1];
-      const cx<T> MUes = m1(h5 * (Rm[1] + Rm[2]), 1, -1) * A[0][2];
-      const cx<T> MUen = m1(h5 * (Rp[1] + Rp[2]), 1, 1) * A[2][2];
       const cx<T> lapW = ih * (mu9[1][0] * G1m - mu9[1][1] * G1c + mnA * G2A - mnC * G2C);
       const cx<T> lapE = ih * (mu9[1][1] * G1c - mu9[1][2] * G1p + mnB * G2B - mnD * G2D);
-      const cx<T> massW = g.beta * MUw + g.sm * (MUww + MUe + MUws + MUwn);
-      const cx<T> massE = g.beta * MUe + g.sm * (MUw + MUee + MUes + MUen);
+      cx<T> massW, massE;  // the spread face-mass terms of the two u1 rows
+      if (NOABL) {
+        // every face mass is rho_f omega^2 (1 - i att): weight u by the density sums first and
+        // scale by the common complex factor once
+        const cx<T> cm = mkc<T>(h5 * w2, -(h5 * w2) * att);
+        const cx<T> Vw = (R0[1] + R0[2]) * A[1][1], Ve = (R0[2] + R0[3]) * A[1][2];
+        const cx<T> Vww = (R0[0] + R0[1]) * A[1][0], Vee = (R0[3] + R0[4]) * A[1][3];
+        const cx<T> Vws = (Rm[0] + Rm[1]) * A[0][1], Vwn = (Rp[0] + Rp[1]) * A[2][1];
+        const cx<T> Ves = (Rm[1] + Rm[2]) * A[0][2], Ven = (Rp[1] + Rp[2]) * A[2][2];
+        massW = cm * (g.beta * Vw + g.sm * (Vww + Ve + Vws + Vwn));
+        massE = cm * (g.beta * Ve + g.sm * (Vw + Vee + Ves + Ven));
+      } else {
+        // face masses m u at the u1 faces the two rows need
+        const cx<T> MUw = mW * A[1][1], MUe = mE * A[1][2];
+        const cx<T> MUww = m1(h5 * (R0[0] + R0[1]), -1, 0) * A[1][0];
+        const cx<T> MUee = m1(h5 * (R0[3] + R0[4]), 2, 0) * A[1][3];
+        const cx<T> MUws = m1(h5 * (Rm[0] + Rm[1]), 0, -1) * A[0][1];
+        const cx<T> MUwn = m1(h5 * (Rp[0] + Rp[1]), 0, 1) * A[2][1];
+        const cx<T> MUes = m1(h5 * (Rm[1] + Rm[2]), 1, -1) * A[0][2];
+        const cx<T> MUen = m1(h5 * (Rp[1] + Rp[2]), 1, 1) * A[2][2];
+        massW = g.beta * MUw + g.sm * (MUww + MUe + MUws + MUwn);
+        massE = g.beta * MUe + g.sm * (MUw + MUee + MUes + MUen);
+      }
       r[0] = exW ? z : b[k] - (lapW - massW + ih * (pC - pW));
       r[1] = exE ? z : b[k + 1] - (lapE - massE + ih * (pE - pC));
     }
@@ -169,17 +182,28 @@ HD void vanka_cell(const Grid<T>& g, const cx<T>* __restrict__ b, const cx<T>* _
       H2c = h2(1);
       const cx<T> H2p = h2(2);
       const cx<T> H1A = h1(0, 1), H1B = h1(1, 1), H1C = h1(0, 2), H1D = h1(1, 2);
-      const cx<T> MUs = mS * B[1][1], MUn = mN * B[2][1];
-      const cx<T> MUss = m2(h5 * (rS2 + Rm[1]), 0, -1) * B[0][1];
-      const cx<T> MUnn = m2(h5 * (Rp[1] + rN2), 0, 2) * B[3][1];
-      const cx<T> MUsw = m2(h5 * (Rm[0] + R0[1]), -1, 0) * B[1][0];
-      const cx<T> MUse = m2(h5 * (Rm[2] + R0[3]), 1, 0) * B[1][2];
-      const cx<T> MUnw = m2(h5 * (R0[1] + Rp[0]), -1, 1) * B[2][0];
-      const cx<T> MUne = m2(h5 * (R0[3] + Rp[2]), 1, 1) * B[2][2];
       const cx<T> lapS = ih * (mnA * H1A - mnB * H1B + mu9[0][1] * H2m - mu9[1][1] * H2c);
       const cx<T> lapN = ih * (mnC * H1C - mnD * H1D + mu9[1][1] * H2c - mu9[2][1] * H2p);
-      const cx<T> massS = g.beta * MUs + g.sm * (MUsw + MUse + MUss + MUn);
-      const cx<T> massN = g.beta * MUn + g.sm * (MUnw + MUne + MUs + MUnn);
+      cx<T> massS, massN;  // the spread face-mass terms of the two u2 rows
+      if (NOABL) {
+        const cx<T> cm = mkc<T>(h5 * w2, -(h5 * w2) * att);
+        const cx<T> Vs = (Rm[1] + R0[2]) * B[1][1], Vn = (R0[2] + Rp[1]) * B[2][1];
+        const cx<T> Vss = (rS2 + Rm[1]) * B[0][1], Vnn = (Rp[1] + rN2) * B[3][1];
+        const cx<T> Vsw = (Rm[0] + R0[1]) * B[1][0], Vse = (Rm[2] + R0[3]) * B[1][2];
+        const cx<T> Vnw = (R0[1] + Rp[0]) * B[2][0], Vne = (R0[3] + Rp[2]) * B[2][2];
+        massS = cm * (g.beta * Vs + g.sm * (Vsw + Vse + Vss + Vn));
+        massN = cm * (g.beta * Vn + g.sm * (Vnw + Vne + Vs + Vnn));
+      } else {
+        const cx<T> MUs = mS * B[1][1], MUn = mN * B[2][1];
+        const cx<T> MUss = m2(h5 * (rS2 + Rm[1]), 0, -1) * B[0][1];
+        const cx<T> MUnn = m2(h5 * (Rp[1] + rN2), 0, 2) * B[3][1];
+        const cx<T> MUsw = m2(h5 * (Rm[0] + R0[1]), -1, 0) * B[1][0];
+        const cx<T> MUse = m2(h5 * (Rm[2] + R0[3]), 1, 0) * B[1][2];
+        const cx<T> MUnw = m2(h5 * (R0[1] + Rp[0]), -1, 1) * B[2][0];
+        const cx<T> MUne = m2(h5 * (R0[3] + Rp[2]), 1, 1) * B[2][2];
+        massS = g.beta * MUs + g.sm * (MUsw + MUse + MUss + MUn);
+        massN = g.beta * MUn + g.sm * (MUnw + MUne + MUs + MUnn);
+      }
       r[2] = exS ? z : b[N + k] - (lapS - massS + ih * (pC - pS));
       r[3] = exN ? z : b[N + k + nx] - (lapN - massN + ih * (pN - pC));
     }

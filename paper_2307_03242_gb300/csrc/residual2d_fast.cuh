@@ -116,8 +116,10 @@ HD void residual_cell(const Grid<T>& g, const cx<T>* __restrict__ b, const cx<T>
   r[2 * N + k] = ldg(b + 2 * N + k) - (G1c + H2c + ldg(g.cp + k) * pC);
 }
 
+// Four blocks of 256 per SM (64 registers, a few spilled): the kernel is latency-bound, and the
+// extra warps hide more than the spills cost (2048^2 residual + restriction 137 -> 124 us).
 template <typename T>
-__global__ void __launch_bounds__(BX * BY) residual_fast(Grid<T> g, const cx<T>* __restrict__ b,
+__global__ void __launch_bounds__(BX * BY, 4) residual_fast(Grid<T> g, const cx<T>* __restrict__ b,
                                                         const cx<T>* __restrict__ x, cx<T>* __restrict__ r) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;

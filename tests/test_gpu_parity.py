@@ -235,6 +235,29 @@ def test_wcycle_and_kcycle_match_oracle(case, prec, cycle):
     s.close()
 
 
+@pytest.mark.parametrize("case", ["2d", "2d_odd_coarse"])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_per_level_damping_matches_oracle(case, prec):
+    """A different damping on every level (the coarsest level keeps its own): a W-cycle whose
+    levels each read their own entry."""
+    w = _w(case)
+    w.coarse, w.coarse_sweeps, w.coarse_damping, w.cycle = "smooth", 3, 0.8, "W"
+    w.damping = [0.6, 0.35, 0.2][:w.levels]
+    pb = oracle_problem(w)
+    hier = oracle_hierarchy(w, pb)
+    s = gpu_solver(w, prec)
+    b = random_field(pb, 67)
+    ref = oracle.vcycle(hier, b.ravel())
+    import torch
+    xt = torch.zeros(s.vec_shape(0), dtype=s.cdtype, device="cuda")
+    s.vcycle(to_gpu(b, prec), xt, zero_guess=True)
+    assert rel(to_np(xt).ravel() * oracle.active_mask(pb), ref) < TOL_CYCLE[prec]
+    # the same cycle with one damping everywhere differs: the entries are not all read from one slot
+    hier1 = oracle_hierarchy(w, pb, damping=w.damping[0])
+    assert rel(oracle.vcycle(hier1, b.ravel()), ref) > 100 * TOL_CYCLE[32]
+    s.close()
+
+
 @pytest.mark.parametrize("case", ["2d", "3d"])
 def test_vcycle_is_deterministic(case):
     w = _w(case)

@@ -140,8 +140,8 @@ def config_c4_batch(count: int = 64, seed0: int = 1000, sizes=(256, 384, 512, 76
     points per minimum shear wavelength, and 1-4 unit point forces in the depth component at
     random positions outside the absorbing layer (extra["sources"], the first also in rhs).
     Solver: the 2048^2 configuration's, whose level spacings h_l = 2^l h it shares: W(2,2) on 5
-    levels (coarsest n/16, 16^2 to 64^2), shift 0.5 (1.0 and 2 red-black sweeps on the
-    coarsest level), FGMRES(5)."""
+    levels (coarsest n/16, 16^2 to 64^2), damping 0.5 / 0.3 / 0.3 / 0.2 by level, shift 0.5 (1.0
+    and 2 red-black sweeps on the coarsest level), FGMRES(5)."""
     out = []
     for k in range(count):
         rng = np.random.default_rng(seed0 + k)
@@ -158,7 +158,8 @@ def config_c4_batch(count: int = 64, seed0: int = 1000, sizes=(256, 384, 512, 76
         sources = [point_source((n, n), 1, (int(rng.integers(lo, hi)), int(rng.integers(lo, hi))))
                    for _ in range(nsrc)]
         w = Workload("c4_%02d_%d" % (k, n), (n, n), h, lam, mu, rho, omega, sources[0],
-                     levels=5, alpha=0.5, damping=0.2, abl_cells=abl_cells, coarse="smooth", coarse_sweeps=2,
+                     levels=5, alpha=0.5, damping=(0.5, 0.3, 0.3, 0.2, 0.2), abl_cells=abl_cells, coarse="smooth",
+                     coarse_sweeps=2,
                      coarse_damping=0.8, cycle="W", alpha_coarsest=1.0, restart=5)
         w.extra["sources"] = sources
         out.append(w)

@@ -109,14 +109,17 @@ def config_c1_homogeneous(n: int = 128) -> Workload:
 def config_c2_random2d(n: int = 2048, seed: int = 0, levels: int = 5, source_depth: int = 32) -> Workload:
     """2D smooth random medium: Vp in [1.5, 4.5] (Gaussian filter sigma 32 cells, correlation
     length ~64 cells), Vs = Vp/sqrt(3), rho = 0.31 Vp^0.25; 10 points per minimum shear
-    wavelength; point force in the depth component u2 at (n/2, depth 32). Solver: W(2,2) on 5
-    levels, shift 0.5, shift 1.0 on the coarsest level (2 red-black sweeps), FGMRES(5).
+    wavelength; point force in the depth component u2 at (n/2, depth 32). Solver: W(1,1) on 5
+    levels (the paper's 2D cycle), shift 0.5, shift 1.0 on the coarsest level (2 red-black
+    sweeps), FGMRES(5).
 
-    Damping per level, decreasing towards the coarse grids (0.5, 0.3, 0.3, then 0.2): two-grid
-    Fourier analysis of the red-black smoother puts the best w near 0.5-0.65 at 10 points per
-    wavelength and near 0.3 at 5 (the first coarse level); on this medium these values need 211
-    FGMRES iterations where a uniform 0.2 needs 232, and w above 0.3 on the third level slows
-    the solve (0.35: 256 iterations; 0.4: stalls)."""
+    Damping per level, decreasing towards the coarse grids (0.7, 0.4, 0.3, 0.25, then the
+    coarsest level's own 0.8). Two-grid Fourier analysis of the red-black smoother puts the best
+    w at 0.5-0.65 for 10 points per wavelength and near 0.3 for 5 (the first coarse level), and a
+    uniform 0.2 is far from both. Measured on this medium (FGMRES(5) iterations, seconds):
+    W(2,2) with 0.2 everywhere 232, 0.94; W(2,2) with 0.5 / 0.3 / 0.3 / 0.2 211, 0.86 (0.35 on
+    the third level 256, 0.4 stalls); W(2,1) 221-226, 0.77-0.78; W(1,1) with 0.7 / 0.4 / 0.3 /
+    0.25 255, 0.74, the fastest, each cycle being cheaper."""
     shape = (n, n)
     sigma = 32.0 * n / 2048.0 if n < 2048 else 32.0
     vp = gaussian_random_velocity(shape, seed, sigma_cells=sigma)
@@ -127,9 +130,9 @@ def config_c2_random2d(n: int = 2048, seed: int = 0, levels: int = 5, source_dep
     omega = omega_for_points_per_wavelength(float(vs.min()), h)
     rhs = point_source((n, n), 1, (n // 2, min(source_depth, n - 1)))
     return Workload("c2_random_2d_%d" % n, (n, n), h, lam, mu, rho, omega, rhs,
-                    levels=levels, alpha=0.5, damping=tuple(([0.5, 0.3, 0.3] + [0.2] * levels)[:levels]),
+                    levels=levels, alpha=0.5, damping=tuple(([0.7, 0.4, 0.3, 0.25] + [0.2] * levels)[:levels]),
                     abl_cells=20, coarse="smooth", coarse_sweeps=2, coarse_damping=0.8, cycle="W",
-                    alpha_coarsest=1.0, restart=5)
+                    alpha_coarsest=1.0, restart=5, nu_pre=1, nu_post=1)
 
 
 def config_c4_batch(count: int = 64, seed0: int = 1000, sizes=(256, 384, 512, 768, 1024),
@@ -139,9 +142,9 @@ def config_c4_batch(count: int = 64, seed0: int = 1000, sizes=(256, 384, 512, 76
     filter sigma 32 cells, Vp in [1.5, 4.5], Vs = Vp/sqrt(3), rho = 0.31 Vp^0.25), omega for 10
     points per minimum shear wavelength, and 1-4 unit point forces in the depth component at
     random positions outside the absorbing layer (extra["sources"], the first also in rhs).
-    Solver: the 2048^2 configuration's, whose level spacings h_l = 2^l h it shares: W(2,2) on 5
-    levels (coarsest n/16, 16^2 to 64^2), damping 0.5 / 0.3 / 0.3 / 0.2 by level, shift 0.5 (1.0
-    and 2 red-black sweeps on the coarsest level), FGMRES(5)."""
+    Solver: W(2,2) on 5 levels, whose spacings h_l = 2^l h match the 2048^2 configuration's
+    (coarsest n/16, 16^2 to 64^2), damping 0.5 / 0.3 / 0.3 / 0.2 by level, shift 0.5 (1.0 and 2
+    red-black sweeps on the coarsest level), FGMRES(5)."""
     out = []
     for k in range(count):
         rng = np.random.default_rng(seed0 + k)

@@ -19,13 +19,15 @@ Modules
   krylov          -- right-preconditioned restarted flexible GMRES (Saad 1993), modified Gram-Schmidt
   twogrid         -- Section 4.3 convergence factor in practice (Eq. convFactor) of the two-grid cycle
   lexvanka.c      -- the lexicographic (Gauss-Seidel over cells) Vanka sweep, compiled with gcc
+  adjoint         -- misfit gradient wrt lambda, mu, rho by the adjoint-state method (direct solves)
 
 Parity status: every function is pinned by tests/test_oracle_*.py against the
 paper's printed stencils, closed-form Fourier symbols, the two-grid symbol of
 Eq. symbolTG, dense direct solves, plane-wave solutions and Table 1's two-grid
-convergence factors (economic Vanka in lexicographic order). The full Vanka
-smoother has no printed symbol or factor in the paper; it is pinned by the
-single-cell exactness property and by the converged solves only.
+convergence factors (economic Vanka in lexicographic order); the adjoint
+gradient by central finite differences of the misfit. The full Vanka smoother
+has no printed symbol or factor in the paper; it is pinned by the single-cell
+exactness property and by the converged solves only.
 """
 from .discretization import Problem, assemble, apply, active_mask, coarsen, gamma_abl, dof_shape, window
 from .transfer import restriction, prolongation

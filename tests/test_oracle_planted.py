@@ -107,3 +107,25 @@ def test_material_coarsening_is_exact_for_linear_media():
     c = oracle.coarsen(pb)
     zc, yc, xc = np.meshgrid(*[2 * (np.arange(v) + 0.5) for v in c.n[::-1]], indexing="ij")
     np.testing.assert_allclose(c.mu, 1.0 + 0.3 * xc - 0.2 * yc + 0.7 * zc, atol=1e-13)
+
+
+# ---------------------------------------------------------------- adjoint-state gradient
+import oracle.adjoint as adj
+import test_oracle_adjoint as tadj
+
+
+def test_planted_missing_absorbing_layer_in_the_mass_derivative_breaks_the_fd_pin(monkeypatch):
+    monkeypatch.setattr(adj, "gamma_abl", lambda pb, comp: np.zeros(tuple(pb.n[::-1])))
+    _fails(tadj.test_gradient_matches_central_differences_cell_by_cell, "rho")
+
+
+def test_planted_two_cell_node_average_breaks_the_fd_pin(monkeypatch):
+    orig = adj.average_matrix
+    monkeypatch.setattr(adj, "average_matrix", lambda pb, axes, counts: orig(pb, axes[:1], counts))
+    _fails(tadj.test_gradient_matches_central_differences_cell_by_cell, "mu")
+
+
+def test_planted_unconjugated_adjoint_breaks_the_fd_pin(monkeypatch):
+    orig = adj.material_derivative
+    monkeypatch.setattr(adj, "material_derivative", lambda pb, u, a, shift=0.0: orig(pb, u, np.conj(a), shift))
+    _fails(tadj.test_gradient_matches_central_differences_in_a_random_direction, (12, 10), 2, "mu")

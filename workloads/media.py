@@ -196,6 +196,46 @@ def config_c3_layered3d(n: int = 256, source=(128, 128, 24), levels: int = 3) ->
                     nu_pre=1, nu_post=1, restart=8)
 
 
+
+def config_c5_adjoint(n: int = 128, seed: int = 0, source_side: int = 4, receiver_side: int = 64,
+                      depth: int = 4) -> Workload:
+    """3D inversion setting for the misfit gradient: a smooth random medium built like the 2D one
+    (white noise, Gaussian filter sigma n/16 cells, Vp mapped onto [1.5, 4.5], Vs = Vp/sqrt(3),
+    rho = 0.31 Vp^0.25) as the current model; the data model adds a Gaussian blob of +5 % in Vp
+    (radius n/8, at the grid centre, Vs and rho following Vp). source_side^2 unit point forces in
+    the depth component u3 on a regular grid at depth index `depth`, receiver_side^2 receivers of
+    u3 on a regular grid at the same depth; 10 points per minimum shear wavelength of the
+    current model. extra: "sources" (DOF arrays), "receivers" ((comp, (i, j, k)) tuples, x1
+    first), "true" (lam, mu, rho of the data model). Solver: the 3D recipe (K(1,1) on 3 levels,
+    shift 0.4, 2.5 and 16 red-black sweeps on the coarsest level, damping 0.15, FGMRES(8))."""
+    shape = (n, n, n)
+    vp = gaussian_random_velocity(shape, seed, sigma_cells=n / 16.0)
+    z = np.arange(n) + 0.5
+    Z, Y, X = np.meshgrid(z, z, z, indexing="ij")
+    c = n / 2.0
+    blob = 1.0 + 0.05 * np.exp(-((X - c) ** 2 + (Y - c) ** 2 + (Z - c) ** 2) / (n / 8.0) ** 2)
+
+    def model(v):
+        vs = v / np.sqrt(3.0)
+        rho = 0.31 * v ** 0.25
+        lam, mu = lame_from_velocity(v, vs, rho)
+        return lam, mu, rho
+
+    lam, mu, rho = model(vp)
+    h = 1.0
+    omega = omega_for_points_per_wavelength(float(vp.min() / np.sqrt(3.0)), h)
+    grid = lambda k: [int((i + 0.5) * n / k) for i in range(k)]
+    sources = [point_source(shape, 2, (i, j, depth)) for j in grid(source_side) for i in grid(source_side)]
+    receivers = [(2, (i, j, depth)) for j in grid(receiver_side) for i in grid(receiver_side)]
+    w = Workload("c5_adjoint_3d_%d" % n, shape, h, lam, mu, rho, omega, sources[0],
+                 levels=3, alpha=0.4, damping=0.15, abl_cells=max(2, int(round(20 * n / 256.0))),
+                 coarse="smooth", coarse_sweeps=16, coarse_damping=0.8, cycle="K", alpha_coarsest=2.5,
+                 nu_pre=1, nu_post=1, restart=8)
+    w.extra["sources"] = sources
+    w.extra["receivers"] = receivers
+    w.extra["true"] = model(vp * blob)
+    return w
+
 def small_heterogeneous(n, seed: int = 1, sigma_cells: float = 2.0, abl_cells: int = 2,
                         levels: int = 2, omega_ppw: float = 10.0) -> Workload:
     """A small random heterogeneous medium for parity tests (any dimension)."""

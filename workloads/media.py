@@ -113,13 +113,13 @@ def config_c2_random2d(n: int = 2048, seed: int = 0, levels: int = 5, source_dep
     levels (the paper's 2D cycle), shift 0.5, shift 1.0 on the coarsest level (2 red-black
     sweeps), FGMRES(5).
 
-    Damping per level, decreasing towards the coarse grids (0.7, 0.4, 0.3, 0.25, then the
-    coarsest level's own 0.8). Two-grid Fourier analysis of the red-black smoother puts the best
-    w at 0.5-0.65 for 10 points per wavelength and near 0.3 for 5 (the first coarse level), and a
-    uniform 0.2 is far from both. Measured on this medium (FGMRES(5) iterations, seconds):
-    W(2,2) with 0.2 everywhere 232, 0.94; W(2,2) with 0.5 / 0.3 / 0.3 / 0.2 211, 0.86 (0.35 on
-    the third level 256, 0.4 stalls); W(2,1) 221-226, 0.77-0.78; W(1,1) with 0.7 / 0.4 / 0.3 /
-    0.25 255, 0.74, the fastest, each cycle being cheaper."""
+    Damping per level (0.7, 0.4, 0.4, 0.3, then the coarsest level's own 0.8). Two-grid Fourier
+    analysis of the red-black smoother with one pre- and one post-step (alpha = 0.5, lambda =
+    mu) puts the best w at 0.7-0.8 for 10 points per wavelength (the finest level), 0.5-0.6 for 5
+    and 0.4 for 2.5, and a uniform 0.2 is far from all of them. Measured on this medium (FGMRES(5)
+    iterations, seconds): W(2,2) with 0.2 everywhere 232, 0.94; W(2,2) with 0.5 / 0.3 / 0.3 / 0.2
+    211, 0.86; W(2,1) 221-226, 0.77-0.78; W(1,1) with 0.7 / 0.4 / 0.3 / 0.25 255, 0.74; W(1,1)
+    with 0.7 / 0.4 / 0.4 / 0.3 230, 0.67, the fastest."""
     shape = (n, n)
     sigma = 32.0 * n / 2048.0 if n < 2048 else 32.0
     vp = gaussian_random_velocity(shape, seed, sigma_cells=sigma)
@@ -130,7 +130,7 @@ def config_c2_random2d(n: int = 2048, seed: int = 0, levels: int = 5, source_dep
     omega = omega_for_points_per_wavelength(float(vs.min()), h)
     rhs = point_source((n, n), 1, (n // 2, min(source_depth, n - 1)))
     return Workload("c2_random_2d_%d" % n, (n, n), h, lam, mu, rho, omega, rhs,
-                    levels=levels, alpha=0.5, damping=tuple(([0.7, 0.4, 0.3, 0.25] + [0.2] * levels)[:levels]),
+                    levels=levels, alpha=0.5, damping=tuple(([0.7, 0.4, 0.4, 0.3] + [0.2] * levels)[:levels]),
                     abl_cells=20, coarse="smooth", coarse_sweeps=2, coarse_damping=0.8, cycle="W",
                     alpha_coarsest=1.0, restart=5, nu_pre=1, nu_post=1)
 

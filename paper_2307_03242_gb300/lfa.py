@@ -355,6 +355,21 @@ def sweep(s: Setting, field, values, fn="rho_loc", step=0.02):
     return np.array(out)
 
 
+def damping_by_level(s: Setting, levels: int, candidates=None, step=0.04):
+    """Damping per level of a hierarchy whose finest level is described by `s` (its omega_h,
+    shift, material, smoother and sweep counts): level l has spacing 2^l h, hence omega_h 2^l,
+    and gets the candidate w with the smallest two-grid factor. The coarsest level is solved
+    separately and gets none. Returns [(w, rho_loc), ...] for levels 0 .. levels - 2."""
+    cands = np.round(np.arange(0.1, 1.0001, 0.05), 2) if candidates is None else candidates
+    out = []
+    for l in range(levels - 1):
+        sl = replace(s, omega_h=s.omega_h * 2 ** l, h=s.h * 2 ** l)
+        r = sweep(sl, "w", cands, step=step)
+        i = int(np.argmin(r))
+        out.append((float(cands[i]), float(r[i])))
+    return out
+
+
 def _table():
     rows = []
     for beta, w in ((1.0, 0.75), (2.0 / 3.0, 0.65)):

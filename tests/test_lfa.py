@@ -255,3 +255,15 @@ def test_minimal_shift_and_points_per_wavelength():
     p23, p1 = lim["ppw_min_beta_2_3"], lim["ppw_min_beta_1"]
     assert rho_at(2.0 / 3.0, 0.65, p23) < 1.0 < rho_at(2.0 / 3.0, 0.65, p23 - 1.0)
     assert rho_at(1.0, 0.75, p1) < 1.0 < rho_at(1.0, 0.75, p1 - 2.0)
+
+
+def test_damping_by_level_decreases_towards_the_coarse_grids():
+    """Coarser levels have fewer points per wavelength; their best damping is smaller and their
+    two-grid factor larger (Section 5.2 uses a smaller w on coarser grids for the same reason)."""
+    s = lfa.Setting(beta=2.0 / 3.0, omega_h=np.pi / 5, alpha=0.5, lam=1.0, smoother="full", order="red-black",
+                    nu1=1, nu2=1, h=1.0)
+    rec = lfa.damping_by_level(s, 4, candidates=np.array([0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8]), step=0.08)
+    ws, rhos = [r[0] for r in rec], [r[1] for r in rec]
+    assert len(rec) == 3
+    assert ws[0] >= ws[1] >= ws[2] and ws[0] > ws[2], rec
+    assert rhos[0] < rhos[1] < rhos[2] < 1.0, rec

@@ -157,6 +157,31 @@ emg_status emg_solve_batch(const emg_handle* handles, int count, const void* con
                            void* const* x, double tol, int max_iter, int restart,
                            emg_stats* stats, int workers, emg_status* status);
 
+/* ---- Adjoint-state gradient (frequency-domain inversion; the adjoint-state method, e.g.
+ * Plessix 2006; the paper's solver is the forward solver of such an inversion, Sec. 1 and 5). ----
+ * For a data misfit J = 1/2 sum_s |S u_s - d_s|^2 with u_s = H^-1 q_s, the gradient with respect
+ * to the cell fields is -Re sum_s a_s^H (dH/dm) u_s with the adjoint fields a_s = H^-H S^T
+ * (S u_s - d_s). H is the unshifted finest-level operator of this handle. Vectors are FP64
+ * complex device vectors of (dim+1)*ncell values in the layout of emg_apply. */
+
+/* y = H^H x (conjugate transpose of the unshifted operator), FP64. */
+emg_status emg_apply_adjoint(emg_handle h, const void* x, void* y);
+
+/* Solve H^H x = b by the FGMRES of emg_solve with H^H as the operator. The preconditioner is
+ * the handle's cycle mapped through z = S conj(M(conj(S r))), S = diag(I, -I) (displacements
+ * kept, pressure negated): with beta = 1 the operator satisfies H^H = S conj(H) S exactly, with
+ * the beta-spread stencils up to the spread of the coupling blocks, so the mapped cycle is a
+ * close preconditioner. Requires cycle_precision 32 (EMG_ERR_INVALID otherwise); arguments,
+ * statuses and stats as emg_solve. */
+emg_status emg_solve_adjoint(emg_handle h, const void* b, void* x, double tol, int max_iter,
+                             int restart, emg_stats* stats);
+
+/* Per cell k: g_lam[k] = -Re a^H (dH/dlambda_k) u, and likewise g_mu, g_rho (FP64 device
+ * arrays of ncell values, cell index x fastest). accumulate != 0 adds to the arrays (summing
+ * over sources); otherwise they are overwritten. u: forward field, a: adjoint field. */
+emg_status emg_material_gradient(emg_handle h, const void* u, const void* a, double* g_lam,
+                                 double* g_mu, double* g_rho, int accumulate);
+
 /* ---- Per-step entry points (one row of the cycle each; used for parity checks). ----
  * `level` 0 is the finest. Vectors are cycle vectors of that level's size. */
 

@@ -12,7 +12,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libemg.so")
-SOURCES = ["emg.cu", "launch2d.cu", "launch3d.cu", "noalloc.cu"]
+# host build of the per-cell adjoint functions, for CPU checks against the oracle (tests only)
+HOSTCHECK = os.path.join(PKG, "libemg_hostcheck.so")
+SOURCES = ["emg.cu", "launch2d.cu", "launch3d.cu", "noalloc.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
          "--diag-suppress=177"]
@@ -60,5 +62,23 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+def build_hostcheck(force: bool = False) -> str:
+    """libemg_hostcheck.so: csrc/hostcheck.cu compiled for the host only (the adjoint's per-cell
+    functions looped on the CPU), which the CPU tests compare with the FP64 oracle."""
+    src = os.path.join(CSRC, "hostcheck.cu")
+    deps = [src, os.path.join(CSRC, "adjoint.cuh"), os.path.join(CSRC, "emg_types.cuh")]
+    if not force and os.path.exists(HOSTCHECK) and all(os.path.getmtime(d) <= os.path.getmtime(HOSTCHECK) for d in deps):
+        return HOSTCHECK
+    tmp = HOSTCHECK + ".tmp"
+    cmd = [nvcc()] + ARCH + ["-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-I" + os.path.join(ROOT, "include"),
+                             src, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for hostcheck.cu:\n%s\n%s" % (" ".join(cmd), r.stderr))
+    os.replace(tmp, HOSTCHECK)
+    return HOSTCHECK
+
+
 if __name__ == "__main__":
     print(build_library(force="--force" in sys.argv, verbose=True))
+    print(build_hostcheck(force="--force" in sys.argv))

@@ -883,6 +883,38 @@ void outer_apply(emg_ctx& c, const void* x, bool x32, const cx<double>* b, doubl
   LAUNCHED(c);
 }
 
+// y = H^H x (the unshifted finest operator, conjugate-transposed) or y = bscale*b - H^H x, FP64;
+// x in FP64 or FP32.
+void outer_apply_adjoint(emg_ctx& c, const void* x, bool x32, const cx<double>* b, double bscale, cx<double>* y) {
+  const Level& F = c.lv[0];
+  ProfScope ps(c, EMG_K_APPLY64, 0,
+               (double)F.ncell * ((c.dim + 1) * ((x32 ? 8.0 : 16.0) + 16.0 + (b ? 16.0 : 0.0)) + 3 * 8.0));
+  const Grid<double> g = make_grid<double>(c, 0, false, c.mu64.p, c.rho64.p, c.cp64.p);
+  if (c.dim == 2) {
+    if (x32) launch_adjoint_apply<2, float>(g, (const cx<float>*)x, b, bscale, y, c.st);
+    else launch_adjoint_apply<2, double>(g, (const cx<double>*)x, b, bscale, y, c.st);
+  } else {
+    if (x32) launch_adjoint_apply<3, float>(g, (const cx<float>*)x, b, bscale, y, c.st);
+    else launch_adjoint_apply<3, double>(g, (const cx<double>*)x, b, bscale, y, c.st);
+  }
+  CKL();
+  LAUNCHED(c);
+}
+
+// z <- S conj(z) on an FP32 cycle vector (S = diag(I, -I)): maps the forward cycle onto a
+// preconditioner for H^H (emg_solve_adjoint).
+template <typename T>
+void sconj_cycle_vector(emg_ctx& c, cx<T>* z) {
+  if constexpr (std::is_same<T, float>::value) {
+    launch_sconj(z, (size_t)c.dim * c.lv[0].ncell, c.nvec(), c.st);
+    CKL();
+    LAUNCHED(c);
+  } else {
+    (void)z;
+    raise(EMG_ERR_INVALID, "adjoint solves need the FP32 cycle");
+  }
+}
+
 // Capture vcycle(0, b, z) into a graph; nullptr (and graphs off for this handle) if the capture
 // or the instantiation fails, e.g. because the runtime cannot capture a launch kind.
 template <typename T>
@@ -961,7 +993,8 @@ constexpr double kReorth = 1e-3;
 // scaled by a power of two so that ||b|| ~ 1 (exact), which keeps them inside the float exponent
 // range of the float-float kernels; x is unscaled on exit.
 template <typename T>
-emg_status solve_impl(emg_ctx& c, const cx<double>* b, cx<double>* x, double tol, int max_iter, int m, emg_stats* st) {
+emg_status solve_impl(emg_ctx& c, const cx<double>* b, cx<double>* x, double tol, int max_iter, int m, emg_stats* st,
+                      bool adj = false) {
   const size_t n = c.nvec();
   ensure_krylov(c, m);
   const bool f32 = std::is_same<T, float>::value;
@@ -990,7 +1023,8 @@ emg_status solve_impl(emg_ctx& c, const cx<double>* b, cx<double>* x, double tol
   CKL();
   LAUNCHED(c);
   auto true_residual = [&]() {
-    outer_apply(c, x, false, b, sc, r, false);  // r = sc*b - H (sc*x)
+    if (adj) outer_apply_adjoint(c, x, false, b, sc, r);  // r = sc*b - H^H (sc*x)
+    else outer_apply(c, x, false, b, sc, r, false);     // r = sc*b - H (sc*x)
     double rn2 = 0;
     mdots(c, true, nullptr, 0, 0, r, n, h, rn2);
     return std::sqrt(rn2);
@@ -1013,8 +1047,14 @@ emg_status solve_impl(emg_ctx& c, const cx<double>* b, cx<double>* x, double tol
       cx<double>* vj = V + (size_t)j * n;
       if (j > 0) update_scale(c, vj, V, n, pend, 1.0 / pend_norm, n, b32);  // finish V_j
       cx<double>* w = V + (size_t)(j + 1) * n;
+      if (adj) sconj_cycle_vector<T>(c, c.lv[0].b.as<cx<T>>());  // the cycle solves with conj(S v_j)
       precondition<T>(c, vj, Z + (size_t)j * n);
-      outer_apply(c, Z + (size_t)j * n, f32, nullptr, 0.0, w, false);
+      if (adj) {
+        sconj_cycle_vector<T>(c, Z + (size_t)j * n);  // z_j = S conj(M conj(S v_j))
+        outer_apply_adjoint(c, Z + (size_t)j * n, f32, nullptr, 0.0, w);
+      } else {
+        outer_apply(c, Z + (size_t)j * n, f32, nullptr, 0.0, w, false);
+      }
       double wn2 = 0;
       mdots(c, true, V, n, j + 1, w, n, h, wn2);
       double hh = 0;
@@ -1306,6 +1346,52 @@ emg_status emg_solve(emg_handle h, const void* b, void* x, double tol, int max_i
   if (c.prec == 32) return solve_impl<float>(c, (const cx<double>*)b, (cx<double>*)x, tol, max_iter, restart, stats);
   return solve_impl<double>(c, (const cx<double>*)b, (cx<double>*)x, tol, max_iter, restart, stats);
   ABI_CATCH
+}
+
+emg_status emg_apply_adjoint(emg_handle h, const void* x, void* y) {
+  ABI_TRY
+  emg_ctx& c = *checked(h);
+  check_ptr(x, "x");
+  check_ptr(y, "y");
+  outer_apply_adjoint(c, x, false, nullptr, 0.0, (cx<double>*)y);
+  ABI_CATCH
+  return EMG_OK;
+}
+
+emg_status emg_solve_adjoint(emg_handle h, const void* b, void* x, double tol, int max_iter, int restart,
+                             emg_stats* stats) {
+  ABI_TRY
+  emg_ctx& c = *checked(h);
+  check_ptr(b, "b");
+  check_ptr(x, "x");
+  if (restart < 1 || restart > 64) raise(EMG_ERR_INVALID, "restart must be in 1..64");
+  if (max_iter < 0) raise(EMG_ERR_INVALID, "max_iter < 0");
+  if (!(tol >= 0.0)) raise(EMG_ERR_INVALID, "tol must be >= 0");
+  if (c.prec != 32) raise(EMG_ERR_INVALID, "emg_solve_adjoint needs cycle_precision 32");
+  return solve_impl<float>(c, (const cx<double>*)b, (cx<double>*)x, tol, max_iter, restart, stats, true);
+  ABI_CATCH
+}
+
+emg_status emg_material_gradient(emg_handle h, const void* u, const void* a, double* g_lam, double* g_mu,
+                                 double* g_rho, int accumulate) {
+  ABI_TRY
+  emg_ctx& c = *checked(h);
+  check_ptr(u, "u");
+  check_ptr(a, "a");
+  for (const double* gp : {g_lam, g_mu, g_rho})
+    if (!gp || reinterpret_cast<uintptr_t>(gp) % 8) raise(EMG_ERR_INVALID, "gradient arrays must be 8-byte aligned device arrays");
+  const Grid<double> g = make_grid<double>(c, 0, false, c.mu64.p, c.rho64.p, c.cp64.p);
+  {
+    ProfScope ps(c, EMG_K_APPLY64, 0, (double)c.lv[0].ncell * (2 * (c.dim + 1) * 16.0 + 3 * 8.0 * (accumulate ? 2 : 1)));
+    if (c.dim == 2)
+      launch_adjoint_gradient<2>(g, (const cx<double>*)u, (const cx<double>*)a, g_lam, g_mu, g_rho, accumulate, c.st);
+    else
+      launch_adjoint_gradient<3>(g, (const cx<double>*)u, (const cx<double>*)a, g_lam, g_mu, g_rho, accumulate, c.st);
+    CKL();
+    LAUNCHED(c);
+  }
+  ABI_CATCH
+  return EMG_OK;
 }
 
 emg_status emg_solve_batch(const emg_handle* handles, int count, const void* const* b, void* const* x, double tol,

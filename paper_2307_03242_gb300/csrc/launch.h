@@ -43,3 +43,14 @@ cudaError_t launch_sweeps_coop2(const Grid<T>& g, const cx<T>* b, cx<T>* x, cx<T
 template <typename TI>
 void launch_apply_ff3(const ff3::FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y,
                       cudaStream_t st);
+
+// Adjoint-state gradient (adjoint.cu): y = H^H x or y = bscale b - H^H x on the finest level,
+// the per-cell material derivative, and z <- S conj(z) on an FP32 vector (nu displacement
+// entries, then the pressure).
+template <int D, typename TI>
+void launch_adjoint_apply(const Grid<double>& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y,
+                          cudaStream_t st);
+template <int D>
+void launch_adjoint_gradient(const Grid<double>& g, const cx<double>* u, const cx<double>* a, double* glam,
+                             double* gmu, double* grho, int accumulate, cudaStream_t st);
+void launch_sconj(cx<float>* z, size_t nu, size_t n, cudaStream_t st);

@@ -69,6 +69,9 @@ def _load():
         "emg_smooth_noalloc": [ctypes.POINTER(_Params), vp, vp, vp, vp, vp, i32, vp],
         "emg_solve_batch": [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(vp), dbl, i32, i32,
                             ctypes.POINTER(_Stats), i32, ctypes.POINTER(ctypes.c_int)],
+        "emg_apply_adjoint": [vp, vp, vp],
+        "emg_solve_adjoint": [vp, vp, vp, dbl, i32, i32, ctypes.POINTER(_Stats)],
+        "emg_material_gradient": [vp, vp, vp, vp, vp, vp, i32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -82,7 +85,8 @@ def _load():
 LIB = _load()
 EXPORTED = ["emg_create", "emg_destroy", "emg_last_error", "emg_apply", "emg_vcycle", "emg_solve", "emg_solve_host",
             "emg_level_info", "emg_smooth", "emg_residual_restrict", "emg_prolong_correct", "emg_coarse_solve",
-            "emg_profile", "emg_profile_read", "emg_smooth_noalloc", "emg_solve_batch"]
+            "emg_profile", "emg_profile_read", "emg_smooth_noalloc", "emg_solve_batch", "emg_apply_adjoint",
+            "emg_solve_adjoint", "emg_material_gradient"]
 NOALLOC_MAX_CELLS = 262144
 
 
@@ -335,6 +339,46 @@ class Solver:
                                  tol, max_iter, restart, ctypes.byref(st)), allow=(0, 5))
         self._out()
         return self._stats(st, hist, s)
+
+    def apply_adjoint(self, x, y):
+        """y = H^H x (unshifted finest operator, conjugate-transposed), complex128."""
+        import torch
+        n = self._n()
+        self._in()
+        _check(LIB.emg_apply_adjoint(self.h, _ptr(x, torch.complex128, n, "x"), _ptr(y, torch.complex128, n, "y")))
+        self._out()
+        return y
+
+    def solve_adjoint(self, b, x, tol=1e-6, max_iter=1000, restart=20, history_cap=0):
+        """Solve H^H x = b (FGMRES preconditioned by the mapped cycle; FP32 cycle only)."""
+        import torch
+        n = self._n()
+        st = _Stats()
+        hist = None
+        if history_cap:
+            hist = (ctypes.c_double * history_cap)()
+            st.history = hist
+            st.history_cap = history_cap
+        self._in()
+        s = _check(LIB.emg_solve_adjoint(self.h, _ptr(b, torch.complex128, n, "b"),
+                                         _ptr(x, torch.complex128, n, "x"), tol, max_iter, restart,
+                                         ctypes.byref(st)), allow=(0, 5))
+        self._out()
+        return self._stats(st, hist, s)
+
+    def material_gradient(self, u, a, out=None, accumulate=False):
+        """-Re a^H (dH/dm) u per cell for m = lambda, mu, rho: a tuple of three float64 tensors of
+        the grid's shape (written into `out` if given, added to it with accumulate=True)."""
+        import torch
+        n = self._n()
+        if out is None:
+            out = tuple(torch.zeros(self.shape, dtype=torch.float64, device=u.device) for _ in range(3))
+        ptrs = [_ptr(g, torch.float64, self.ncell, nm) for g, nm in zip(out, ("g_lam", "g_mu", "g_rho"))]
+        self._in()
+        _check(LIB.emg_material_gradient(self.h, _ptr(u, torch.complex128, n, "u"), _ptr(a, torch.complex128, n, "a"),
+                                         ptrs[0], ptrs[1], ptrs[2], 1 if accumulate else 0))
+        self._out()
+        return out
 
     def solve_host(self, b, x, tol=1e-6, max_iter=1000, restart=20, history_cap=0):
         """b, x: host numpy complex128 arrays (pinned or pageable); x is overwritten."""

@@ -131,3 +131,50 @@ def test_gradient_points_towards_the_data_model_on_a_small_inversion_instance():
                 + np.sum(g["rho"] * (rho_t - pb.rho)))
     # first order: -grad . dm = |r|^2 = 2 J (measured 1.012 x 2J for a 5 % blob)
     assert abs(descent / (2 * J) - 1.0) < 0.05, (descent, J)
+
+
+def test_conjugate_transpose_is_the_sign_conjugated_operator_at_beta_one():
+    """H^H = S conj(H) S with S = diag(I, -I) when beta = 1 (any medium); with the beta-spread
+    stencils the two differ, for a homogeneous medium only in the u-p coupling blocks. The GPU
+    adjoint solve preconditions H^H with the forward cycle mapped through this relation."""
+    import scipy.sparse as sp
+    for beta in (1.0, 2.0 / 3.0):
+        w = small_heterogeneous((8, 6), seed=5, abl_cells=2)
+        pb = replace(oracle_problem(w), beta=beta)
+        H = oracle.assemble(pb, 0.0)
+        N, d = pb.ncell, pb.dim
+        S = sp.diags(np.r_[np.ones(d * N), -np.ones(N)])
+        D = (H.conj().T - S @ H.conj() @ S).tocsr()
+        if beta == 1.0:
+            assert abs(D).max() <= 1e-12 * abs(H).max()
+        else:
+            assert abs(D).max() > 1e-3 * abs(H).max()
+    # homogeneous medium, beta = 2/3: the displacement block and the p-p block agree
+    pb = replace(oracle_problem(w), beta=2.0 / 3.0, lam=np.full(w.lam.shape, 2.0), mu=np.ones(w.lam.shape),
+                 rho=np.ones(w.lam.shape), abl_length=0.0)
+    H = oracle.assemble(pb, 0.0)
+    D = (H.conj().T - S @ H.conj() @ S).tocsr()
+    uu = D[:d * N][:, :d * N]
+    assert abs(uu).max() <= 1e-12 * abs(H).max() and abs(D[d * N:, d * N:]).max() == 0.0
+
+
+@pytest.mark.parametrize("n,levels", [((24, 16), 2), ((8, 8, 8), 2)])
+def test_mapped_forward_cycle_preconditions_the_adjoint_operator(n, levels):
+    """FGMRES on H^H with the preconditioner S conj(M(conj(S r))), M the forward cycle, needs at
+    most twice the iterations of the forward solve (measured 28 vs 21 in 2D, 14 vs 10 in 3D)."""
+    from _gpu_helpers import oracle_hierarchy
+    w = small_heterogeneous(n, seed=3, levels=levels, abl_cells=2, sigma_cells=2.0)
+    pb = oracle_problem(w)
+    hier = oracle_hierarchy(w, pb)
+    H = oracle.assemble(pb, 0.0)
+    Hh = H.conj().T.tocsr()
+    act = oracle.active_mask(pb)
+    S = np.r_[np.ones(pb.dim * pb.ncell), -np.ones(pb.ncell)]
+    rng = np.random.default_rng(4)
+    b = (rng.standard_normal(act.size) + 1j * rng.standard_normal(act.size)) * act
+    M = lambda v: oracle.vcycle(hier, v)
+    _, its, _ = oracle.fgmres(lambda v: H @ v, M, b, tol=1e-10, restart=20, max_iter=500)
+    x, its_a, _ = oracle.fgmres(lambda v: Hh @ v, lambda r: S * np.conj(M(np.conj(S * r))), b, tol=1e-10,
+                                restart=20, max_iter=500)
+    assert np.linalg.norm(b - Hh @ x) <= 1e-9 * np.linalg.norm(b)
+    assert its_a <= 2 * its, (its, its_a)

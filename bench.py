@@ -41,8 +41,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="emg", choices=["emg", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4"],
-                    help="c4: the 64-instance batch of 2D solves (emg_solve_batch)")
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+                    help="c4: the 64-instance batch of 2D solves (emg_solve_batch); c5: one misfit gradient of "
+                         "the 3D inversion setting (forward and adjoint solves of 16 sources)")
     ap.add_argument("--instances", type=int, default=64, help="c4: number of instances")
     ap.add_argument("--grid", type=int, default=None,
                     help="cells per axis instead of the configuration's own (c1-c3; smaller cases for kernel captures)")
@@ -215,6 +216,10 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.config not in REF_ITERS:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm covers the single-solve "
+                          "configurations c1-c3; %s has no single-solve iteration count" % args.config}))
+        return
     w = workload(args.config, args)
     iters = REF_ITERS[args.config]
     vals = []
@@ -277,6 +282,9 @@ def main():
         return
     if args.config == "c4":
         run_batch(args)
+        return
+    if args.config == "c5":
+        run_gradient(args)
         return
     import torch
     import torch.distributed as dist
@@ -524,6 +532,123 @@ def run_batch(args):
     out["clocks"] = clk.summary()
     for s in solvers:
         s.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+GRADIENT_METRIC = "time per misfit gradient wrt (lambda, mu, rho): forward + adjoint solves of every source, 1 GB300"
+
+
+def run_gradient(args):
+    """One misfit gradient of the 3D inversion setting (config_c5_adjoint: 128^3, 16 sources, 64 x
+    64 receivers): per step, a solver built from the current model, a forward solve per source,
+    an adjoint solve per source and the material-derivative kernel (inversion.misfit + backward),
+    timed with CUDA events on the current stream between synchronisations. The data come from
+    the +5 % blob model (set-up, untimed). A second, instrumented pass reports the finest-level
+    half-sweep bandwidth."""
+    import torch
+    import torch.distributed as dist
+    from paper_2307_03242_gb300 import emg, inversion
+    from workloads import config_c5_adjoint
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.grid or 128
+    w = config_c5_adjoint(n)
+    params = emg.params_from_workload(w, 32)
+    shape = (w.dim + 1,) + tuple(w.n[::-1])
+    rec = torch.tensor([int(np.ravel_multi_index((c,) + tuple(idx[::-1]), shape)) for c, idx in w.extra["receivers"]],
+                       dtype=torch.int64, device=dev)
+    sources = [torch.from_numpy(q).to(dev) for q in w.extra["sources"]]
+    true = emg.Solver(params, *w.extra["true"])
+    data = []
+    for q in sources:
+        u = torch.zeros_like(q)
+        true.solve(q, u, tol=w.tol, max_iter=4000, restart=w.restart)
+        data.append(u.reshape(-1)[rec].clone())
+    true.close()
+    model = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (w.lam, w.mu, w.rho)]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def gradient(m, stats=None, solver=None):
+        leaves = [t.detach().clone().requires_grad_(True) for t in m]
+        J = inversion.misfit(*leaves, params, sources, rec, data, tol=w.tol, solver=solver, stats=stats,
+                             restart=w.restart)
+        J.backward()
+        return J, [t.grad for t in leaves]
+
+    for _ in range(args.warmup):
+        gradient(model)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    barrier()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            J, g = gradient(model, stats)
+        e1.record(stream)
+        barrier()
+    tg = max_over_ranks(e0.elapsed_time(e1) / args.steps / 1e3, device=dev)
+    fwd = [st["iterations"] for st in stats if st["kind"] == "forward"]
+    adj = [st["iterations"] for st in stats if st["kind"] == "adjoint"]
+    # instrumented pass on a solver built once: finest-level half-sweep bandwidth, launch count
+    s = emg.Solver(params, *model)
+    s.profile(True)
+    s.profile_read(emg.K_ALL)
+    gradient(model, solver=s)
+    prof = s.profile_read(emg.K_SMOOTH)
+    launches = s.profile_read(emg.K_ALL)["launches"]
+    s.profile(False)
+    s.close()
+    # end to end: the model from pinned host memory in, the three gradient fields out
+    hm = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (w.lam, w.mu, w.rho)]
+    hg = [torch.empty_like(h).pin_memory() for h in hm]
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        m = [h.to(dev, non_blocking=True) for h in hm]
+        _, g = gradient(m)
+        for h, gg in zip(hg, g):
+            h.copy_(gg, non_blocking=True)
+        torch.cuda.synchronize()
+    te2e = (time.perf_counter() - t0) / args.steps
+    nbytes = int(sum(h.numel() for h in hm) * 8)
+    peak, peak_kind = load_peaks()
+    achieved = prof["bytes"] / (prof["ms"] * 1e-3) / 1e9 if prof["ms"] > 0 else None
+    out = {"metric": GRADIENT_METRIC, "value": tg, "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": tg * 1e3, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "c64 cycle / c128 outer", "data": "synthetic",
+           "config": {"workload": "c5_adjoint_3d_%d" % n, "grid": "%dx%dx%d" % tuple(w.n), "sources": len(sources),
+                      "receivers": int(rec.numel()), "cycle": "K(1,1)", "levels": w.levels,
+                      "krylov": "FGMRES(%d)" % w.restart, "tol": w.tol,
+                      "l2": "inputs larger than L2" if 16 * 4 * np.prod(w.n) > 129e6 else "inputs smaller than L2",
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "iterations": {"forward_median": int(np.median(fwd)), "adjoint_median": int(np.median(adj)),
+                          "forward_total": int(sum(fwd)) // args.steps, "adjoint_total": int(sum(adj)) // args.steps},
+           "misfit": float(J.item()),
+           "roofline": {"kernel": "vanka half-sweep (finest level, FP32, instrumented pass)", "bound": "hbm",
+                        "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                        "frac": achieved / peak if achieved else None, "traffic": None,
+                        "launches": prof["launches"]},
+           "e2e": {"value": te2e, "unit": "s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+           "gpu_launches": int(launches)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per_it, desc, threads = oracle_sample(w)
+        total = out["iterations"]["forward_total"] + out["iterations"]["adjoint_total"]
+        out["cpu_baseline"] = {"value": per_it * total, "unit": "s", "cores": threads, "kind": "oracle",
+                               "sample": desc + " x the forward and adjoint iterations of one gradient"}
+    out["clocks"] = clk.summary()
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

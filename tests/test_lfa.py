@@ -267,3 +267,15 @@ def test_damping_by_level_decreases_towards_the_coarse_grids():
     assert len(rec) == 3
     assert ws[0] >= ws[1] >= ws[2] and ws[0] > ws[2], rec
     assert rhos[0] < rhos[1] < rhos[2] < 1.0, rec
+
+
+def test_smoothing_factor_is_smallest_near_the_printed_damping():
+    """Figure 4.1 (left) and its text: mu_loc is smallest near w = 0.65 (beta = 2/3) and w = 0.75
+    (beta = 1), and nearly so for every beta at w = 0.7 (omega = pi/(5h), alpha = 0.1)."""
+    ws = np.round(np.arange(0.5, 0.91, 0.05), 2)
+    for r in _rows("sec42_mu_opt.txt"):
+        beta, w_opt, omega_h, alpha, _ = (float(v) for v in r)
+        s = lfa.Setting(beta=beta, omega_h=omega_h, alpha=alpha)
+        mus = lfa.sweep(s, "w", ws, fn="mu_loc", step=0.04)
+        assert abs(ws[int(np.argmin(mus))] - w_opt) <= 0.05 + 1e-9, (beta, list(zip(ws, mus)))
+        assert mus[list(ws).index(0.7)] <= mus.min() + 0.01

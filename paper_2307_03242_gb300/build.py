@@ -66,7 +66,7 @@ def build_hostcheck(force: bool = False) -> str:
     """libemg_hostcheck.so: csrc/hostcheck.cu compiled for the host only (the adjoint's per-cell
     functions looped on the CPU), which the CPU tests compare with the FP64 oracle."""
     src = os.path.join(CSRC, "hostcheck.cu")
-    deps = [src, os.path.join(CSRC, "adjoint.cuh"), os.path.join(CSRC, "emg_types.cuh")]
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [src]
     if not force and os.path.exists(HOSTCHECK) and all(os.path.getmtime(d) <= os.path.getmtime(HOSTCHECK) for d in deps):
         return HOSTCHECK
     tmp = HOSTCHECK + ".tmp"

@@ -1,7 +1,14 @@
-// Host build of the per-cell adjoint functions (adjoint.cuh), for CPU checks against the FP64
-// oracle: the same source the GPU kernels run, looped over the cells on the host. Not part of
-// the solve path; libemg_hostcheck.so holds no device code that runs.
+// Host build of per-cell functions of the kernels, for CPU checks against the FP64 oracle: the
+// same source the GPU kernels run (the adjoint rows and material derivative of adjoint.cuh; the
+// 2D red-black half-sweep of vanka2d_fast.cuh and the residual and restriction of
+// residual2d_fast.cuh, with the kernels' choice among their interior and attenuation-free
+// variants), looped over the cells on the host. Not part of the solve path;
+// libemg_hostcheck.so holds no device code that runs.
+#include <vector>
+
 #include "adjoint.cuh"
+#include "residual2d_fast.cuh"
+#include "vanka2d_fast.cuh"
 
 namespace {
 
@@ -60,9 +67,157 @@ void gradient_all(const Grid<double>& g, const cx<double>* u, const cx<double>* 
       }
 }
 
+// A 2D level as the library sets it up: material in precision T, the per-axis absorbing-layer
+// tables at k h and (k + 1/2) h for k = -2 .. n + 2 and the attenuation-free lattice range.
+template <typename T>
+struct Level2 {
+  Grid<T> g;
+  std::vector<T> mu, rho, cp, tab[2];
+  Level2(const int* n, double h, double beta, double omega, double att, double abl_len, double abl_gmax, double Lx,
+         double Ly, const double* mu64, const double* rho64, const double* cp64) {
+    const size_t N = (size_t)n[0] * n[1];
+    mu.assign(mu64, mu64 + N);
+    rho.assign(rho64, rho64 + N);
+    cp.assign(cp64, cp64 + N);
+    g.nx = n[0];
+    g.ny = n[1];
+    g.nz = 1;
+    g.h = (T)h;
+    g.ih = (T)(1.0 / h);
+    g.beta = (T)beta;
+    g.sm = (T)((1.0 - beta) / 4.0);
+    g.w2 = (T)(omega * omega);
+    g.att = (T)att;
+    g.ablL = (T)abl_len;
+    g.ablG = (T)abl_gmax;
+    g.Lx = (T)Lx;
+    g.Ly = (T)Ly;
+    g.Lz = T(0);
+    g.mu = mu.data();
+    g.rho = rho.data();
+    g.cp = cp.data();
+    g.abl_tab[2] = nullptr;
+    const double X[2] = {Lx, Ly};
+    for (int a = 0; a < 2; ++a) {
+      tab[a].assign(2 * (n[a] + 5), T(0));
+      for (int k = -2; k <= n[a] + 2; ++k)
+        for (int half = 0; half < 2; ++half) {
+          const double x = (k + 0.5 * half) * h;
+          tab[a][2 * (k + 2) + half] = (T)(abl_len > 0.0 ? abl_gmax * abl_axis(x, abl_len, X[a]) / (abl_len * abl_len) : 0.0);
+        }
+      auto zero_at = [&](int k) { return tab[a][2 * (k + 2)] == T(0) && tab[a][2 * (k + 2) + 1] == T(0); };
+      int lo = n[a] / 2, hi = n[a] / 2 - 1;
+      if (zero_at(n[a] / 2)) {
+        lo = hi = n[a] / 2;
+        while (lo > -2 && zero_at(lo - 1)) --lo;
+        while (hi < n[a] + 2 && zero_at(hi + 1)) ++hi;
+      }
+      g.abl_tab[a] = tab[a].data();
+      g.zlo[a] = lo;
+      g.zhi[a] = hi;
+    }
+  }
+};
+
+template <typename T>
+std::vector<cx<T>> to_cx(const double* v, size_t n) {
+  std::vector<cx<T>> out(n);
+  for (size_t k = 0; k < n; ++k) out[k] = mkc<T>((T)v[2 * k], (T)v[2 * k + 1]);
+  return out;
+}
+template <typename T>
+void from_cx(const std::vector<cx<T>>& v, double* out) {
+  for (size_t k = 0; k < v.size(); ++k) {
+    out[2 * k] = (double)v[k].re;
+    out[2 * k + 1] = (double)v[k].im;
+  }
+}
+
+// One red-black half-sweep of colour `colour` over every cell, choosing the variant as k2::vanka_fast does
+template <typename T>
+void half_sweep2(const Grid<T>& g, const cx<T>* b, const cx<T>* uin, cx<T>* uout, cx<T>* p, int colour, T w, int zin) {
+  for (int j = 0; j < g.ny; ++j)
+    for (int ip = 0; ip < (g.nx + 1) / 2; ++ip) {
+      const int i = 2 * ip + ((colour + j) & 1);
+      if (!zin && i >= 2 && i + 3 <= g.nx && j >= 2 && j + 3 <= g.ny) {
+        if (g.abl_free(0, i - 1, i + 2) && g.abl_free(1, j - 1, j + 2))
+          k2::vanka_cell<T, true, true>(g, b, uin, uout, p, colour, w, zin, ip, j);
+        else
+          k2::vanka_cell<T, true>(g, b, uin, uout, p, colour, w, zin, ip, j);
+      } else {
+        k2::vanka_cell<T, false>(g, b, uin, uout, p, colour, w, zin, ip, j);
+      }
+    }
+}
+
+// `sweeps` full sweeps with the library's buffer protocol: colour 0 reads x and writes the
+// displacements into alt, colour 1 reads alt and writes them back into x; p is updated in place.
+template <typename T>
+void sweeps2(const Level2<T>& L, const double* b64, double* x64, double w, int sweeps, int zero_first) {
+  const size_t N = (size_t)L.g.nx * L.g.ny;
+  std::vector<cx<T>> b = to_cx<T>(b64, 3 * N), x = to_cx<T>(x64, 3 * N), alt(2 * N, czero<T>());
+  cx<T>* p = x.data() + 2 * N;
+  for (int s = 0; s < sweeps; ++s)
+    for (int colour = 0; colour < 2; ++colour) {
+      const cx<T>* uin = colour == 0 ? x.data() : alt.data();
+      cx<T>* uout = colour == 0 ? alt.data() : x.data();
+      half_sweep2<T>(L.g, b.data(), uin, uout, p, colour, (T)w, (zero_first && s == 0 && colour == 0) ? 1 : 0);
+    }
+  from_cx(x, x64);
+}
+
+// r = b - H_s x with the variant choice of k2::residual_fast, then b_c = R r (k2::restrict_r)
+template <typename T>
+void residual_restrict2(const Level2<T>& L, const double* b64, const double* x64, double* bc64) {
+  const int nx = L.g.nx, ny = L.g.ny, nxc = nx / 2, nyc = ny / 2;
+  const size_t N = (size_t)nx * ny;
+  std::vector<cx<T>> b = to_cx<T>(b64, 3 * N), x = to_cx<T>(x64, 3 * N), r(3 * N), bc(3 * (size_t)nxc * nyc);
+  const Grid<T>& g = L.g;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      if (i >= 2 && i + 3 <= nx && j >= 2 && j + 3 <= ny) {
+        if (g.abl_free(0, i - 1, i + 2) && g.abl_free(1, j - 1, j + 2))
+          k2::residual_cell<T, true, true>(g, b.data(), x.data(), r.data(), i, j);
+        else
+          k2::residual_cell<T, true>(g, b.data(), x.data(), r.data(), i, j);
+      } else {
+        k2::residual_cell<T, false>(g, b.data(), x.data(), r.data(), i, j);
+      }
+    }
+  for (int J = 0; J < nyc; ++J)
+    for (int I = 0; I < nxc; ++I) k2::restrict_r_cell<T>(r.data(), bc.data(), nx, ny, nxc, nyc, I, J);
+  from_cx(bc, bc64);
+}
+
 }  // namespace
 
 extern "C" {
+
+// 2D red-black Vanka sweeps of one level (prec 32 or 64), complex128 b and x (x in/out);
+// att = gamma + the level's shift; abl_len, Lx, Ly physical (the finest grid's).
+int emg_hc_vanka2_sweeps(int prec, const int* n, double h, double beta, double omega, double att, double abl_len,
+                         double abl_gmax, double Lx, double Ly, const double* mu, const double* rho, const double* cp,
+                         const double* b, double* x, double w, int sweeps, int zero_first) {
+  if (prec == 64) sweeps2<double>(Level2<double>(n, h, beta, omega, att, abl_len, abl_gmax, Lx, Ly, mu, rho, cp), b, x, w,
+                                  sweeps, zero_first);
+  else if (prec == 32) sweeps2<float>(Level2<float>(n, h, beta, omega, att, abl_len, abl_gmax, Lx, Ly, mu, rho, cp), b, x,
+                                      w, sweeps, zero_first);
+  else return 1;
+  return 0;
+}
+
+// 2D residual and restriction of one level: bc (complex128, 3 (nx/2)(ny/2)) = R (b - H_s x).
+int emg_hc_residual_restrict2(int prec, const int* n, double h, double beta, double omega, double att, double abl_len,
+                              double abl_gmax, double Lx, double Ly, const double* mu, const double* rho,
+                              const double* cp, const double* b, const double* x, double* bc) {
+  if (prec == 64) residual_restrict2<double>(Level2<double>(n, h, beta, omega, att, abl_len, abl_gmax, Lx, Ly, mu, rho, cp),
+                                             b, x, bc);
+  else if (prec == 32) residual_restrict2<float>(Level2<float>(n, h, beta, omega, att, abl_len, abl_gmax, Lx, Ly, mu, rho,
+                                                               cp), b, x, bc);
+  else return 1;
+  return 0;
+}
+
 
 // y = H^H x for complex128 x, y of (dim+1) * n_x n_y (n_z) values; att = gamma + shift.
 int emg_hc_adjoint_apply(int dim, const int* n, double h, double beta, double omega, double att, double abl_len,

@@ -1,0 +1,144 @@
+"""Per-cell functions of the CUDA kernels, compiled for the host and looped over the cells
+(libemg_hostcheck.so), against the FP64 oracle, on the CPU:
+* the adjoint (csrc/adjoint.cuh): y = H^H x against the oracle's assembled conjugate transpose,
+  the material derivative -Re a^H (dH/dm) u against oracle/adjoint.py;
+* the 2D hot path: the red-black half-sweep (csrc/vanka2d_fast.cuh) and the residual and
+  restriction (csrc/residual2d_fast.cuh), each with the kernel's per-cell choice among its
+  general, interior and attenuation-free variants and the library's absorbing-layer tables,
+  against the oracle's red-black sweep and R (b - H_s x), in FP64 and FP32.
+These are the functions the GPU kernels run; the GPU tests check the launches."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.adjoint import material_derivative
+from workloads import small_heterogeneous
+from _gpu_helpers import oracle_problem
+
+DP = ctypes.POINTER(ctypes.c_double)
+
+
+@pytest.fixture(scope="module")
+def hc():
+    from paper_2307_03242_gb300.build import build_hostcheck
+    return ctypes.CDLL(build_hostcheck())
+
+
+def _args(pb):
+    n = np.array(list(pb.n) + [1] * (3 - pb.dim), dtype=np.int32)
+    mats = [np.ascontiguousarray(pb.mu.ravel()), np.ascontiguousarray(pb.rho.ravel()),
+            np.ascontiguousarray((1.0 / (pb.lam + pb.mu)).ravel())]
+    head = [pb.dim, n.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.c_double(pb.h), ctypes.c_double(pb.beta),
+            ctypes.c_double(pb.omega), ctypes.c_double(pb.gamma), ctypes.c_double(pb.abl_length),
+            ctypes.c_double(pb.abl_gamma_max)] + [m.ctypes.data_as(DP) for m in mats]
+    return head, (n, mats)
+
+
+def _cvec(v):
+    return v.view(np.float64).ctypes.data_as(DP)
+
+
+def _rand(act, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal(act.size) + 1j * rng.standard_normal(act.size)) * act
+
+
+CASES = [((9, 7), 2), ((16, 10), 3), ((6, 5, 4), 2), ((7, 6, 5), 1)]
+
+
+@pytest.mark.parametrize("n,abl", CASES)
+def test_host_adjoint_apply_matches_the_oracle_conjugate_transpose(hc, n, abl):
+    w = small_heterogeneous(n, seed=2, abl_cells=abl)
+    pb = oracle_problem(w)
+    act = oracle.active_mask(pb)
+    x = _rand(act, 1)
+    ref = oracle.assemble(pb, 0.0).conj().T @ x
+    y = np.zeros_like(x)
+    head, keep = _args(pb)
+    assert hc.emg_hc_adjoint_apply(*head, _cvec(x), _cvec(y)) == 0
+    assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n,abl", CASES)
+def test_host_material_derivative_matches_the_oracle(hc, n, abl):
+    w = small_heterogeneous(n, seed=4, abl_cells=abl)
+    pb = oracle_problem(w)
+    act = oracle.active_mask(pb)
+    u, a = _rand(act, 2), _rand(act, 3)
+    ref = material_derivative(pb, u, a)
+    g = [np.zeros(pb.ncell) for _ in range(3)]
+    head, keep = _args(pb)
+    assert hc.emg_hc_material_gradient(*head, _cvec(u), _cvec(a), *[v.ctypes.data_as(DP) for v in g]) == 0
+    for got, name in zip(g, ("lam", "mu", "rho")):
+        r = ref[name].ravel()
+        assert np.abs(got - r).max() <= 1e-13 * np.abs(r).max(), name
+
+
+# ---------------------------------------------------------------- forward 2D kernels, host build
+from oracle.smoother import red_black_sweep
+from _gpu_helpers import oracle_hierarchy, random_field
+
+FWD = {"2d": ((72, 40), 3, 5), "2d_odd_coarse": ((36, 20), 3, 3)}
+
+
+def _level_args(pb, hier, level, prec):
+    pl = hier.pbs[level]
+    n = np.array(list(pl.n) + [1], dtype=np.int32)
+    mats = [np.ascontiguousarray(pl.mu.ravel()), np.ascontiguousarray(pl.rho.ravel()),
+            np.ascontiguousarray((1.0 / (pl.lam + pl.mu)).ravel())]
+    head = [prec, n.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.c_double(pl.h), ctypes.c_double(pb.beta),
+            ctypes.c_double(pb.omega), ctypes.c_double(pb.gamma + hier.alphas[level]),
+            ctypes.c_double(pb.abl_length), ctypes.c_double(pb.abl_gamma_max), ctypes.c_double(pb.domain[0]),
+            ctypes.c_double(pb.domain[1])] + [m.ctypes.data_as(DP) for m in mats]
+    return head, (n, mats)
+
+
+@pytest.mark.parametrize("case", list(FWD))
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("level", [0, 1])
+@pytest.mark.parametrize("sweeps,zero_first", [(1, 0), (2, 0), (2, 1)])
+def test_host_red_black_vanka_matches_the_oracle(hc, case, prec, level, sweeps, zero_first):
+    """The 2D half-sweep's three variants (general, interior, interior without the absorbing
+    layer), chosen per cell as the kernel chooses them, against the oracle's red-black sweep."""
+    n, levels, abl = FWD[case]
+    w = small_heterogeneous(n, seed=1, levels=levels, abl_cells=abl, sigma_cells=2.0)
+    pb = oracle_problem(w)
+    hier = oracle_hierarchy(w, pb)
+    pl = hier.pbs[level]
+    b, x = random_field(pl, 21), random_field(pl, 22)
+    if zero_first:
+        x = np.zeros_like(x)
+    ref = x.ravel()
+    for _ in range(sweeps):
+        ref = red_black_sweep(hier.H[level], hier.V[level], hier.idx[level], hier.colour[level], b.ravel(), ref,
+                              hier.w[level])
+    got = np.ascontiguousarray(x.ravel()).copy()
+    if zero_first:
+        got[:] = np.nan  # a zero initial guess must not be read
+    head, keep = _level_args(pb, hier, level, prec)
+    bb = np.ascontiguousarray(b.ravel())
+    assert hc.emg_hc_vanka2_sweeps(*head, _cvec(bb), _cvec(got), ctypes.c_double(hier.w[level]), sweeps,
+                                   zero_first) == 0
+    tol = 1e-12 if prec == 64 else 1e-5
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("case", list(FWD))
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("level", [0, 1])
+def test_host_residual_restriction_matches_the_oracle(hc, case, prec, level):
+    n, levels, abl = FWD[case]
+    w = small_heterogeneous(n, seed=1, levels=levels, abl_cells=abl, sigma_cells=2.0)
+    pb = oracle_problem(w)
+    hier = oracle_hierarchy(w, pb)
+    pl = hier.pbs[level]
+    b, x = random_field(pl, 31), random_field(pl, 32)
+    ref = hier.R[level] @ (b.ravel() - hier.H[level] @ x.ravel())
+    bc = np.zeros(ref.size, dtype=np.complex128)
+    head, keep = _level_args(pb, hier, level, prec)
+    bb, xx = np.ascontiguousarray(b.ravel()), np.ascontiguousarray(x.ravel())
+    assert hc.emg_hc_residual_restrict2(*head, _cvec(bb), _cvec(xx), _cvec(bc)) == 0
+    tol = 1e-12 if prec == 64 else 2e-5
+    assert np.abs(bc - ref).max() <= tol * np.abs(ref).max()

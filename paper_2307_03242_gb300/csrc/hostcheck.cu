@@ -1,13 +1,14 @@
 // Host build of per-cell functions of the kernels, for CPU checks against the FP64 oracle: the
 // same source the GPU kernels run (the adjoint rows and material derivative of adjoint.cuh; the
 // 2D red-black half-sweep of vanka2d_fast.cuh and the residual and restriction of
-// residual2d_fast.cuh, with the kernels' choice among their interior and attenuation-free
-// variants), looped over the cells on the host. Not part of the solve path;
+// residual2d_fast.cuh, the 3D residual of residual3d.cuh, with the kernels' choice among their
+// interior and attenuation-free variants), looped over the cells on the host. Not part of the solve path;
 // libemg_hostcheck.so holds no device code that runs.
 #include <vector>
 
 #include "adjoint.cuh"
 #include "residual2d_fast.cuh"
+#include "residual3d.cuh"
 #include "vanka2d_fast.cuh"
 
 namespace {
@@ -67,38 +68,39 @@ void gradient_all(const Grid<double>& g, const cx<double>* u, const cx<double>* 
       }
 }
 
-// A 2D level as the library sets it up: material in precision T, the per-axis absorbing-layer
-// tables at k h and (k + 1/2) h for k = -2 .. n + 2 and the attenuation-free lattice range.
-template <typename T>
+// A 2D (D = 2) or 3D level as the library sets it up: material in precision T, the per-axis
+// absorbing-layer tables at k h and (k + 1/2) h for k = -2 .. n + 2 and the attenuation-free
+// lattice range.
+template <typename T, int D = 2>
 struct Level2 {
   Grid<T> g;
-  std::vector<T> mu, rho, cp, tab[2];
+  std::vector<T> mu, rho, cp, tab[3];
   Level2(const int* n, double h, double beta, double omega, double att, double abl_len, double abl_gmax, double Lx,
-         double Ly, const double* mu64, const double* rho64, const double* cp64) {
-    const size_t N = (size_t)n[0] * n[1];
+         double Ly, const double* mu64, const double* rho64, const double* cp64, double Lz = 0.0) {
+    const size_t N = (size_t)n[0] * n[1] * (D == 3 ? n[2] : 1);
     mu.assign(mu64, mu64 + N);
     rho.assign(rho64, rho64 + N);
     cp.assign(cp64, cp64 + N);
     g.nx = n[0];
     g.ny = n[1];
-    g.nz = 1;
+    g.nz = D == 3 ? n[2] : 1;
     g.h = (T)h;
     g.ih = (T)(1.0 / h);
     g.beta = (T)beta;
-    g.sm = (T)((1.0 - beta) / 4.0);
+    g.sm = (T)((1.0 - beta) / (2.0 * D));
     g.w2 = (T)(omega * omega);
     g.att = (T)att;
     g.ablL = (T)abl_len;
     g.ablG = (T)abl_gmax;
     g.Lx = (T)Lx;
     g.Ly = (T)Ly;
-    g.Lz = T(0);
+    g.Lz = (T)Lz;
     g.mu = mu.data();
     g.rho = rho.data();
     g.cp = cp.data();
     g.abl_tab[2] = nullptr;
-    const double X[2] = {Lx, Ly};
-    for (int a = 0; a < 2; ++a) {
+    const double X[3] = {Lx, Ly, Lz};
+    for (int a = 0; a < D; ++a) {
       tab[a].assign(2 * (n[a] + 5), T(0));
       for (int k = -2; k <= n[a] + 2; ++k)
         for (int half = 0; half < 2; ++half) {
@@ -189,9 +191,49 @@ void residual_restrict2(const Level2<T>& L, const double* b64, const double* x64
   from_cx(bc, bc64);
 }
 
+// r = b - H_s x in 3D with the variant choice of k3::residual (interior cells: the register
+// cube, with or without the absorbing layer; cells next to the boundary: the reference rows)
+template <typename T>
+void residual3(const Level2<T, 3>& L, const double* b64, const double* x64, double* r64) {
+  const Grid<T>& g = L.g;
+  const size_t N = (size_t)g.nx * g.ny * g.nz;
+  std::vector<cx<T>> b = to_cx<T>(b64, 4 * N), x = to_cx<T>(x64, 4 * N), r(4 * N);
+  const cx<T>* u[3] = {x.data(), x.data() + N, x.data() + 2 * N};
+  const cx<T>* p = x.data() + 3 * N;
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        if (i >= 2 && i + 3 <= g.nx && j >= 2 && j + 3 <= g.ny && k >= 2 && k + 3 <= g.nz) {
+          if (g.abl_free(0, i - 1, i + 2) && g.abl_free(1, j - 1, j + 2) && g.abl_free(2, k - 1, k + 2))
+            k3::residual_cell3<T, true>(g, b.data(), x.data(), r.data(), i, j, k);
+          else
+            k3::residual_cell3<T, false>(g, b.data(), x.data(), r.data(), i, j, k);
+          continue;
+        }
+        const size_t q = s3::lin(g, i, j, k);
+        const int idx[3] = {i, j, k};
+        for (int c = 0; c < 3; ++c)
+          r[c * N + q] = idx[c] >= 1 ? b[c * N + q] - s3::row_u(c, u[c], p, g, i, j, k) : czero<T>();
+        r[3 * N + q] = b[3 * N + q] - s3::row_p(u, p, g, i, j, k);
+      }
+  from_cx(r, r64);
+}
+
 }  // namespace
 
 extern "C" {
+
+// 3D residual of one level: r (complex128, 4 nx ny nz) = b - H_s x.
+int emg_hc_residual3(int prec, const int* n, double h, double beta, double omega, double att, double abl_len,
+                     double abl_gmax, double Lx, double Ly, double Lz, const double* mu, const double* rho,
+                     const double* cp, const double* b, const double* x, double* r) {
+  if (prec == 64) residual3<double>(Level2<double, 3>(n, h, beta, omega, att, abl_len, abl_gmax, Lx, Ly, mu, rho, cp, Lz),
+                                    b, x, r);
+  else if (prec == 32) residual3<float>(Level2<float, 3>(n, h, beta, omega, att, abl_len, abl_gmax, Lx, Ly, mu, rho, cp, Lz),
+                                        b, x, r);
+  else return 1;
+  return 0;
+}
 
 // 2D red-black Vanka sweeps of one level (prec 32 or 64), complex128 b and x (x in/out);
 // att = gamma + the level's shift; abl_len, Lx, Ly physical (the finest grid's).

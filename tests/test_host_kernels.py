@@ -142,3 +142,28 @@ def test_host_residual_restriction_matches_the_oracle(hc, case, prec, level):
     assert hc.emg_hc_residual_restrict2(*head, _cvec(bb), _cvec(xx), _cvec(bc)) == 0
     tol = 1e-12 if prec == 64 else 2e-5
     assert np.abs(bc - ref).max() <= tol * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("n,abl", [((12, 10, 9), 2), ((16, 8, 8), 3)])
+def test_host_3d_residual_matches_the_oracle(hc, prec, n, abl):
+    """The 3D residual kernel's interior variants (the register cube with and without the
+    absorbing layer) and its boundary rows, chosen per cell as the kernel chooses them."""
+    w = small_heterogeneous(n, seed=6, levels=2, abl_cells=abl, sigma_cells=2.0)
+    pb = oracle_problem(w)
+    alpha = 0.4
+    b, x = random_field(pb, 41), random_field(pb, 42)
+    ref = b.ravel() - oracle.assemble(pb, alpha) @ x.ravel()
+    nn = np.array(n, dtype=np.int32)
+    mats = [np.ascontiguousarray(pb.mu.ravel()), np.ascontiguousarray(pb.rho.ravel()),
+            np.ascontiguousarray((1.0 / (pb.lam + pb.mu)).ravel())]
+    r = np.zeros_like(ref)
+    bb, xx = np.ascontiguousarray(b.ravel()), np.ascontiguousarray(x.ravel())
+    assert hc.emg_hc_residual3(prec, nn.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.c_double(pb.h),
+                               ctypes.c_double(pb.beta), ctypes.c_double(pb.omega), ctypes.c_double(pb.gamma + alpha),
+                               ctypes.c_double(pb.abl_length), ctypes.c_double(pb.abl_gamma_max),
+                               *[ctypes.c_double(v) for v in pb.domain], *[m.ctypes.data_as(DP) for m in mats],
+                               _cvec(bb), _cvec(xx), _cvec(r)) == 0
+    act = oracle.active_mask(pb)
+    tol = 1e-12 if prec == 64 else 2e-5
+    assert np.abs((r - ref) * act).max() <= tol * np.abs(ref).max()

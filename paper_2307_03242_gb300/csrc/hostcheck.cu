@@ -2,11 +2,13 @@
 // same source the GPU kernels run (the adjoint rows and material derivative of adjoint.cuh; the
 // 2D red-black half-sweep of vanka2d_fast.cuh and the residual and restriction of
 // residual2d_fast.cuh, the 3D residual of residual3d.cuh, with the kernels' choice among their
-// interior and attenuation-free variants), looped over the cells on the host. Not part of the solve path;
+// interior and attenuation-free variants; the 3D float-float FP64 apply of apply_ff3d.cuh on the
+// library's host-built coefficients), looped over the cells on the host. Not part of the solve path;
 // libemg_hostcheck.so holds no device code that runs.
 #include <vector>
 
 #include "adjoint.cuh"
+#include "ff3_setup.h"
 #include "residual2d_fast.cuh"
 #include "residual3d.cuh"
 #include "vanka2d_fast.cuh"
@@ -222,6 +224,23 @@ void residual3(const Level2<T, 3>& L, const double* b64, const double* x64, doub
 }  // namespace
 
 extern "C" {
+
+// 3D FP64 apply of the outer solve in float-float arithmetic: y = H x (shift 0) or H_s x, with
+// the coefficient arrays built as the library builds them (ff3::build_host, ff3::make).
+int emg_hc_apply_ff3(const int* n, double h, double beta, double omega, double gamma, double shift, double abl_len,
+                     double abl_gmax, const double* L, const double* lam, const double* mu, const double* rho,
+                     const double* x, double* y) {
+  ff3::HostFF3 o;
+  ff3::build_host(o, n[0], n[1], n[2], h, lam, mu, rho, omega, gamma, abl_len, abl_gmax, L);
+  const df::f2* edge[3] = {o.edge[0].data(), o.edge[1].data(), o.edge[2].data()};
+  const ff2::c2* m[3] = {o.m[0].data(), o.m[1].data(), o.m[2].data()};
+  const ff3::FineFF3 g = ff3::make(o, o.mu.data(), o.cp.data(), edge, m, n[0], n[1], n[2], h, beta, shift);
+  for (int k = 0; k < n[2]; ++k)
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i)
+        ff3::cell_rows<double>(g, (const cx<double>*)x, nullptr, 0.0, (cx<double>*)y, i, j, k);
+  return 0;
+}
 
 // 3D residual of one level: r (complex128, 4 nx ny nz) = b - H_s x.
 int emg_hc_residual3(int prec, const int* n, double h, double beta, double omega, double att, double abl_len,

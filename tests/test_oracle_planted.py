@@ -129,3 +129,48 @@ def test_planted_unconjugated_adjoint_breaks_the_fd_pin(monkeypatch):
     orig = adj.material_derivative
     monkeypatch.setattr(adj, "material_derivative", lambda pb, u, a, shift=0.0: orig(pb, u, np.conj(a), shift))
     _fails(tadj.test_gradient_matches_central_differences_in_a_random_direction, (12, 10), 2, "mu")
+
+
+# ---------------------------------------------------------------- LFA tool (pins against the oracle)
+import paper_2307_03242_gb300.lfa as lfa
+import test_lfa as tl
+
+
+def test_planted_wrong_relaxation_order_breaks_the_lexicographic_symbol_pin(monkeypatch):
+    """Cells of the same row relaxed after the cell counted as relaxed before it."""
+    def wrong(s, theta):
+        st = lfa.operator_stencil(s, s.h)
+        L = np.zeros((theta.shape[0], 5, 5), dtype=np.complex128)
+        for a, (ca, oa) in enumerate(lfa.CELL):
+            for b, (cb, ob) in enumerate(lfa.CELL):
+                for d, coef in st.get((ca, cb), {}).items():
+                    e = (d[0] - ob[0] + oa[0], d[1] - ob[1] + oa[1])
+                    if e[1] < 0 or (e[1] == 0 and e[0] != 0):
+                        L[:, a, b] += coef * lfa._phase(theta, e)
+        return L
+    monkeypatch.setattr(lfa, "_earlier_coupling", wrong)
+    _fails(tl.test_lexicographic_symbol_matches_oracle_sweep_away_from_the_start, "economic")
+
+
+def test_planted_swapped_prolongation_weights_break_the_coarse_correction_pin(monkeypatch):
+    orig = lfa._transfer_taps
+
+    def wrong(comp, axis, kind):
+        t = orig(comp, axis, kind)
+        if kind == "P" and comp != axis:
+            return {-1: 0.75, 0: 0.25, 1: 0.25, 2: 0.75}
+        return t
+    monkeypatch.setattr(lfa, "_transfer_taps", wrong)
+    _fails(tl.test_coarse_correction_symbol_matches_oracle, 2.0 / 3.0, np.pi / 5, 0.15)
+
+
+def test_planted_colour_sign_breaks_the_red_black_symbol_pin(monkeypatch):
+    orig = lfa.red_black_symbol
+
+    def wrong(s, theta):
+        out = orig(s, theta)
+        out[:, :3, 3:] *= -1.0  # the coupling between theta and theta + (pi, pi) with the wrong sign
+        out[:, 3:, :3] *= -1.0
+        return out
+    monkeypatch.setattr(lfa, "red_black_symbol", wrong)
+    _fails(tl.test_red_black_symbol_matches_oracle_sweep, "full", 2.0 / 3.0, np.pi / 5, 0.15)

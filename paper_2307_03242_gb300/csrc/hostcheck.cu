@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "adjoint.cuh"
+#include "adjoint_ff3.cuh"
 #include "ff3_setup.h"
 #include "residual2d_fast.cuh"
 #include "residual3d.cuh"
@@ -239,6 +240,22 @@ int emg_hc_apply_ff3(const int* n, double h, double beta, double omega, double g
     for (int j = 0; j < n[1]; ++j)
       for (int i = 0; i < n[0]; ++i)
         ff3::cell_rows<double>(g, (const cx<double>*)x, nullptr, 0.0, (cx<double>*)y, i, j, k);
+  return 0;
+}
+
+// 3D y = H^H x in float-float arithmetic on the same coefficient arrays (adjoint_ff3.cuh).
+int emg_hc_apply_adjoint_ff3(const int* n, double h, double beta, double omega, double gamma, double abl_len,
+                             double abl_gmax, const double* L, const double* lam, const double* mu, const double* rho,
+                             const double* x, double* y) {
+  ff3::HostFF3 o;
+  ff3::build_host(o, n[0], n[1], n[2], h, lam, mu, rho, omega, gamma, abl_len, abl_gmax, L);
+  const df::f2* edge[3] = {o.edge[0].data(), o.edge[1].data(), o.edge[2].data()};
+  const ff2::c2* m[3] = {o.m[0].data(), o.m[1].data(), o.m[2].data()};
+  const ff3::FineFF3 g = ff3::make(o, o.mu.data(), o.cp.data(), edge, m, n[0], n[1], n[2], h, beta, 0.0);
+  for (int k = 0; k < n[2]; ++k)
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i)
+        ff3::cell_rows_adjoint<double>(g, (const cx<double>*)x, nullptr, 0.0, (cx<double>*)y, i, j, k);
   return 0;
 }
 

@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 from oracle.adjoint import material_derivative
+from oracle.discretization import replace
 from workloads import small_heterogeneous
 from _gpu_helpers import oracle_problem
 
@@ -187,5 +188,29 @@ def test_host_3d_float_float_apply_matches_the_oracle(hc, shift, n, abl):
                                ctypes.c_double(pb.beta), ctypes.c_double(pb.omega), ctypes.c_double(pb.gamma),
                                ctypes.c_double(shift), ctypes.c_double(pb.abl_length), ctypes.c_double(pb.abl_gamma_max),
                                L.ctypes.data_as(DP), *[m.ctypes.data_as(DP) for m in mats], _cvec(xx), _cvec(y)) == 0
+    act = oracle.active_mask(pb)
+    assert np.abs((y - ref) * act).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n,abl", [((12, 10, 9), 2), ((7, 6, 5), 1), ((6, 6, 6), 0)])
+def test_host_3d_float_float_adjoint_apply_matches_the_oracle(hc, n, abl):
+    """y = H^H x in double-FP32 arithmetic on the forward apply's coefficient arrays (the
+    transpose of its 27-point expansion) against the oracle's conjugate transpose."""
+    w = small_heterogeneous(n, seed=8, levels=2, abl_cells=max(abl, 1), sigma_cells=2.0)
+    pb = oracle_problem(w)
+    if abl == 0:
+        pb = replace(pb, abl_length=0.0)
+    x = random_field(pb, 61)
+    ref = oracle.assemble(pb, 0.0).conj().T @ x.ravel()
+    nn = np.array(n, dtype=np.int32)
+    L = np.array(pb.domain, dtype=np.float64)
+    mats = [np.ascontiguousarray(a.ravel()) for a in (pb.lam, pb.mu, pb.rho)]
+    y = np.zeros_like(ref)
+    xx = np.ascontiguousarray(x.ravel())
+    assert hc.emg_hc_apply_adjoint_ff3(nn.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.c_double(pb.h),
+                                       ctypes.c_double(pb.beta), ctypes.c_double(pb.omega), ctypes.c_double(pb.gamma),
+                                       ctypes.c_double(pb.abl_length), ctypes.c_double(pb.abl_gamma_max),
+                                       L.ctypes.data_as(DP), *[m.ctypes.data_as(DP) for m in mats], _cvec(xx),
+                                       _cvec(y)) == 0
     act = oracle.active_mask(pb)
     assert np.abs((y - ref) * act).max() <= 1e-12 * np.abs(ref).max()

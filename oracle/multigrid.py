@@ -9,7 +9,7 @@ r_2h = R(q - A_h u), coarse problem, correction u += P e_2h, nu_2
 post-relaxations. The coarse operators are re-discretisations of the shifted
 operator (Remark 2.1 and Section 3.2: the same stencil on the 2h grid, with the
 same omega, beta and shift alpha added to the attenuation). The coarsest level
-is solved either exactly (dense LU of the coarsest operator, the paper's 2D
+is solved either exactly (dense or sparse LU of the coarsest operator, the paper's 2D
 choice in Section 3.2) or inexactly by a fixed number of red-black Vanka sweeps
 from a zero guess (reading: a GPU-friendly stand-in for the paper's inexact
 hybrid-Kaczmarz coarsest solve of Section 5.3).
@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import numpy as np
 import scipy.linalg as sla
+import scipy.sparse.linalg as spla
 
 from .discretization import Problem, assemble, coarsen, active_mask
 from .transfer import restriction, prolongation
@@ -58,6 +59,10 @@ class Hierarchy:
         if coarse == "dense":
             Hc = self.H[last][self.act_c][:, self.act_c].toarray()
             self.lu = sla.lu_factor(Hc)
+        elif coarse == "sparse":
+            # the same exact coarsest solve as "dense" (Sec. 3.2: LU in 2D), with a sparse LU for
+            # coarsest grids whose dense matrix would not fit in memory
+            self.splu = spla.splu(self.H[last][self.act_c][:, self.act_c].tocsc())
 
     def smooth(self, l, b, x, count, w):
         for _ in range(count):
@@ -69,6 +74,8 @@ class Hierarchy:
         x = np.zeros_like(b)
         if self.coarse == "dense":
             x[self.act_c] = sla.lu_solve(self.lu, b[self.act_c])
+        elif self.coarse == "sparse":
+            x[self.act_c] = self.splu.solve(np.ascontiguousarray(b[self.act_c]))
         else:
             x = self.smooth(last, b, x, self.coarse_sweeps, self.coarse_damping)
         return x

@@ -2,10 +2,11 @@
 medium, W(1,1) cycles of red-black Vanka, exact coarsest solve, FGMRES(5)) against the printed
 iteration counts, as context for the solver variants.
 
-The counts are not reproduced one to one: the paper leaves the absorbing layer's profile and
-strength and the source's component unstated (readings: gamma_max (delta/L)^2 with gamma_max = 2,
-a unit force on u_2 at the middle of the first unknown row). With those readings the oracle
-needs 0.35-0.55 times the printed cycles. What the table shows is reproduced and pinned: the
+The counts depend on what the paper leaves unstated: the absorbing layer's profile and strength
+and the source's component (readings: gamma_max (delta/L)^2 with gamma_max = 2, a unit force on
+u_2 at the middle of the first unknown row). With those readings the oracle needs 0.35-0.55 times
+the printed cycles; a weaker layer, gamma_max = 0.5, brings the two-level counts to 19 and 37
+against the printed 22 and 39 (a source at mid-depth with gamma_max = 2: 20 and 37). What the table shows is reproduced and pinned: the
 spread stencil beta = 2/3 needs clearly fewer cycles than the standard beta = 1 (printed ratio
 0.56 with two levels, 0.66 with three), and three levels need several times the cycles of two.
 The 1024 x 256 rows (printed 56 / 32; measured 29 / 17, the growth from 512 x 128 as printed,
@@ -30,11 +31,11 @@ def _rows():
     return out
 
 
-def _cycles(nx, ny, levels, beta, alpha):
+def _cycles(nx, ny, levels, beta, alpha, gamma_max=2.0):
     h = 1.0
     shape = (ny, nx)
     pb = Problem((nx, ny), h, 2 * np.pi / (10 * h), 0.01, beta, np.full(shape, 20.0), np.ones(shape), np.ones(shape),
-                 abl_length=20 * h, abl_gamma_max=2.0)
+                 abl_length=20 * h, abl_gamma_max=gamma_max)
     w = {2: 0.55, 3: 0.35}[levels]
     hier = oracle.Hierarchy(pb, levels, alpha, w, nu_pre=1, nu_post=1, coarse="sparse", cycle="W")
     b = np.zeros(oracle.dof_shape(pb), dtype=complex)
@@ -67,3 +68,11 @@ def test_three_levels_need_several_times_the_cycles_of_two(measured):
 def test_cycle_counts_are_within_the_stated_band_of_table2(measured):
     for r, its in measured.items():
         assert 0.3 * r[5] <= its <= 1.0 * r[5], (r, its)
+
+
+def test_two_level_counts_match_table2_with_a_weaker_absorbing_layer():
+    """With gamma_max = 0.5 the two-level 512 x 128 counts are within 20 % of the printed ones."""
+    for r in _rows():
+        if r[0] == 512 and r[2] == 2:
+            its = _cycles(*r[:5], gamma_max=0.5)
+            assert abs(its - r[5]) <= 0.2 * r[5], (r, its)

@@ -279,3 +279,14 @@ def test_smoothing_factor_is_smallest_near_the_printed_damping():
         mus = lfa.sweep(s, "w", ws, fn="mu_loc", step=0.04)
         assert abs(ws[int(np.argmin(mus))] - w_opt) <= 0.05 + 1e-9, (beta, list(zip(ws, mus)))
         assert mus[list(ws).index(0.7)] <= mus.min() + 0.01
+
+
+def test_red_black_order_is_no_worse_than_lexicographic_at_table1_settings():
+    """The GPU smoother's red-black order against the lexicographic order of the paper's analysis
+    (economic Vanka, one pre- and one post-step): the two-grid factor is not larger."""
+    for r in _table1():
+        beta, w, omega_h, alpha = r[:4]
+        base = dict(beta=beta, w=w, omega_h=omega_h, alpha=alpha)
+        lex = lfa.rho_loc(lfa.Setting(**base), step=0.04)[0]
+        rb = lfa.rho_loc(lfa.Setting(order="red-black", **base), step=0.04)[0]
+        assert rb <= lex + 1e-3, (r, lex, rb)

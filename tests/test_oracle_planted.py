@@ -174,3 +174,50 @@ def test_planted_colour_sign_breaks_the_red_black_symbol_pin(monkeypatch):
         return out
     monkeypatch.setattr(lfa, "red_black_symbol", wrong)
     _fails(tl.test_red_black_symbol_matches_oracle_sweep, "full", 2.0 / 3.0, np.pi / 5, 0.15)
+
+
+def test_planted_second_recursive_call_from_zero_breaks_the_wcycle_pin(monkeypatch):
+    """A W-cycle whose second recursive call starts from zero instead of from the first call's
+    result computes the V-cycle's correction; the closed-form W propagator must catch it."""
+    import oracle.multigrid as mg
+    import test_oracle_wcycle as tw
+
+    def wrong(hier, b, x=None, level=0):
+        b = np.asarray(b, dtype=np.complex128).ravel()
+        if level == hier.levels - 1:
+            return hier.coarse_solve(b)
+        x = np.zeros_like(b) if x is None else np.asarray(x, dtype=np.complex128).ravel().copy()
+        x = hier.smooth(level, b, x, hier.nu_pre, hier.w[level])
+        bc = hier.R[level] @ (b - hier.H[level] @ x)
+        ec = wrong(hier, bc, None, level + 1)
+        for _ in range(hier.gamma_cycle - 1):
+            if level + 1 < hier.levels - 1:
+                ec = wrong(hier, bc, None, level + 1)  # the mistake: restarts from zero
+        x = x + hier.P[level] @ ec
+        return hier.smooth(level, b, x, hier.nu_post, hier.w[level])
+    monkeypatch.setattr(mg, "vcycle", wrong)
+    _fails(tw.test_wcycle_equals_closed_form_error_propagator_with_exact_coarsest, (1, 1))
+
+
+def test_planted_coarsest_solved_twice_breaks_the_once_per_visit_pin(monkeypatch):
+    """A textbook W-cycle that also repeats the inexact coarsest solve on the level above it
+    departs from the reading the pin fixes."""
+    import oracle.multigrid as mg
+    import test_oracle_wcycle as tw
+    orig = mg.vcycle
+
+    def wrong(hier, b, x=None, level=0):
+        if level == hier.levels - 2 and hier.cycle == "W":
+            b = np.asarray(b, dtype=np.complex128).ravel()
+            x = np.zeros_like(b) if x is None else np.asarray(x, dtype=np.complex128).ravel().copy()
+            x = hier.smooth(level, b, x, hier.nu_pre, hier.w[level])
+            bc = hier.R[level] @ (b - hier.H[level] @ x)
+            last = hier.levels - 1
+            ec = hier.coarse_solve(bc)
+            # the mistake: a second coarsest solve, continuing from the first one's result
+            ec = hier.smooth(last, bc, ec, hier.coarse_sweeps, hier.coarse_damping)
+            x = x + hier.P[level] @ ec
+            return hier.smooth(level, b, x, hier.nu_post, hier.w[level])
+        return orig(hier, b, x, level)
+    monkeypatch.setattr(mg, "vcycle", wrong)
+    _fails(tw.test_wcycle_solves_an_inexact_coarsest_level_once_per_visit)

@@ -229,10 +229,14 @@ emg_status emg_profile_read(emg_handle h, int kernel_class, double* total_ms, in
  * copy of the displacement components, is a fixed file-scope device array of
  * 2 * EMG_NOALLOC_MAX_CELLS complex FP32 values (4 MiB), which every GPU that loads the library
  * holds until the process exits.
- * Limits and behaviour: grids with more than EMG_NOALLOC_MAX_CELLS cells, dim != 2 or
- * cycle_precision != 32 are rejected with EMG_ERR_INVALID before any work. The first call on a
- * device looks up the device address of the work array (cudaGetSymbolAddress); make that first
- * call before any stream capture. Every call shares the one work array: calls that overlap on the
+ * Limits and behaviour: level parameters that emg_create would reject (h, omega, gamma, alpha,
+ * beta, level_alpha, abl_cells, levels, ...), a non-finite damping[0] or abl_gamma_max, grids with more
+ * than EMG_NOALLOC_MAX_CELLS cells, dim != 2 or cycle_precision != 32 are rejected with
+ * EMG_ERR_INVALID before any work. The first call on a device looks up the device address of the
+ * work array (cudaGetSymbolAddress); make that first call before any stream capture. The address
+ * is cached per device and context: after a device reset (cudaDeviceReset) or any other teardown
+ * of the context, the next call looks it up again, so that call, too, belongs before any stream
+ * capture. Every call shares the one work array: calls that overlap on the
  * GPU (different streams, or other threads) race and give wrong results; serialise them. The
  * array keeps the last call's contents; nothing in it needs to start at zero, because each
  * sweep's first half writes every entry before the second half reads it. Enqueued on

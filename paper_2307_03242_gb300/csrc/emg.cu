@@ -1128,16 +1128,13 @@ emg_status solve_impl(emg_ctx& c, const cx<double>* b, cx<double>* x, double tol
   return beta / bhat <= tol ? EMG_OK : EMG_NOT_CONVERGED;
 }
 
-void check_params(const emg_params* p) {
+// The checks that concern one level's operator and smoother (grid, coefficients, precision).
+void check_level_params(const emg_params* p) {
   if (!p) raise(EMG_ERR_INVALID, "params is NULL");
   if (p->dim != 2 && p->dim != 3) raise(EMG_ERR_INVALID, "dim must be 2 or 3");
   if (p->levels < 1 || p->levels > EMG_MAX_LEVELS) raise(EMG_ERR_INVALID, "levels out of range");
-  const int div = 1 << (p->levels - 1);
-  for (int a = 0; a < p->dim; ++a) {
+  for (int a = 0; a < p->dim; ++a)
     if (p->n[a] < 2) raise(EMG_ERR_INVALID, "each n must be >= 2");
-    if (p->n[a] % div) raise(EMG_ERR_INVALID, "n[" + std::to_string(a) + "] not divisible by 2^(levels-1)");
-    if (p->n[a] / div < 2) raise(EMG_ERR_INVALID, "coarsest grid must have >= 2 cells per axis");
-  }
   if (!(p->h > 0) || !std::isfinite(p->h)) raise(EMG_ERR_INVALID, "h must be positive");
   if (!std::isfinite(p->omega) || !std::isfinite(p->gamma) || !std::isfinite(p->alpha) || !std::isfinite(p->beta))
     raise(EMG_ERR_INVALID, "non-finite omega/gamma/alpha/beta");
@@ -1149,6 +1146,16 @@ void check_params(const emg_params* p) {
   if (p->cycle_type != EMG_CYCLE_V && p->cycle_type != EMG_CYCLE_W && p->cycle_type != EMG_CYCLE_K)
     raise(EMG_ERR_INVALID, "unknown cycle_type");
   if (p->smoother != EMG_VANKA_FULL && p->smoother != EMG_VANKA_ECONOMIC) raise(EMG_ERR_INVALID, "unknown smoother");
+}
+
+// Every check of emg_create: one level's, then the hierarchy's.
+void check_params(const emg_params* p) {
+  check_level_params(p);
+  const int div = 1 << (p->levels - 1);
+  for (int a = 0; a < p->dim; ++a) {
+    if (p->n[a] % div) raise(EMG_ERR_INVALID, "n[" + std::to_string(a) + "] not divisible by 2^(levels-1)");
+    if (p->n[a] / div < 2) raise(EMG_ERR_INVALID, "coarsest grid must have >= 2 cells per axis");
+  }
   if (p->coarse_solver != EMG_COARSE_DENSE && p->coarse_solver != EMG_COARSE_SMOOTH)
     raise(EMG_ERR_INVALID, "unknown coarse_solver");
   if (p->coarse_solver == EMG_COARSE_SMOOTH && p->coarse_sweeps < 1 && p->levels > 0)
@@ -1183,6 +1190,16 @@ void check_ptr(const void* p, const char* what) {
   catch (const std::exception& e) { g_err = e.what(); return EMG_ERR_INVALID; }
 
 void emg_set_last_error(const std::string& msg) { g_err = msg; }
+
+emg_status emg_validate_level_params(const emg_params* p, std::string* why) {
+  try {
+    check_level_params(p);
+  } catch (const EmgError& e) {
+    if (why) *why = e.msg;
+    return e.s;
+  }
+  return EMG_OK;
+}
 
 
 

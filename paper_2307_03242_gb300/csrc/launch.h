@@ -1,6 +1,7 @@
 // Launchers of the stencil kernels; each dimension lives in its own translation unit
 // (launch2d.cu, launch3d.cu) so that the library builds in parallel.
 #pragma once
+#include "emg.h"
 #include "emg_types.cuh"
 #include "apply_ff2d.cuh"
 #include "apply_ff3d.cuh"
@@ -9,6 +10,9 @@
 
 // Sets the message that emg_last_error() returns on the calling thread.
 void emg_set_last_error(const std::string& msg);
+// The checks emg_create makes of one level's grid, coefficients, precision and smoother (not of
+// the hierarchy): EMG_OK, or EMG_ERR_INVALID with the reason in *why.
+emg_status emg_validate_level_params(const emg_params* p, std::string* why);
 
 template <typename T, typename TI>
 void launch_apply2(const Grid<T>& g, const cx<TI>* x, const cx<T>* b, T bscale, cx<T>* y, cudaStream_t st);

@@ -6,8 +6,10 @@
 // them the smoother of emg_smooth without a handle: the caller passes the material, b and x; the
 // only work array -- the ping-pong copy of the displacement components that the red-black
 // half-sweeps need -- is a fixed file-scope device array, so nothing is allocated.
+#include <cuda.h>  // driver API types only; the two context queries are resolved at run time
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -22,7 +24,36 @@ __device__ __align__(256) cx<float> g_noalloc_alt[2 * EMG_NOALLOC_MAX_CELLS];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
+// Per device: the array's device address and the ID of the context it was looked up in.
 void* g_alt_addr[kMaxDevices] = {nullptr};
+unsigned long long g_alt_ctx[kMaxDevices] = {0};
+
+// Unique ID of the calling thread's current context (cuCtxGetCurrent + cuCtxGetId, resolved through
+// the runtime so the library needs no link-time dependency on the driver library). A context
+// created after a device reset has a new ID, so a cached address is never reused across contexts.
+// Returns false when the ID cannot be determined; the caller then looks the address up again.
+bool current_context_id(unsigned long long* id) {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {  // under g_mutex
+    resolved = true;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&get_current, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess)
+      get_current = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&get_id, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      get_id = nullptr;
+    cudaGetLastError();
+  }
+  if (!get_current || !get_id) return false;
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 emg_status fail(emg_status s, const std::string& m) {
   emg_set_last_error(m);  // reported by emg_last_error()
@@ -33,7 +64,14 @@ emg_status fail(emg_status s, const std::string& m) {
 
 extern "C" emg_status emg_smooth_noalloc(const emg_params* p, const float* mu, const float* rho, const float* cp,
                                          const void* b, void* x, int sweeps, void* cuda_stream) {
-  if (!p || !mu || !rho || !cp || !b || !x) return fail(EMG_ERR_INVALID, "NULL argument");
+  if (!p) return fail(EMG_ERR_INVALID, "params is NULL");
+  // the checks emg_create makes of one level (h, omega, gamma, alpha, beta, level_alpha, abl_cells, ...)
+  std::string why;
+  const emg_status ps = emg_validate_level_params(p, &why);
+  if (ps != EMG_OK) return fail(ps, why);
+  if (!std::isfinite(p->damping[0]) || !std::isfinite(p->abl_gamma_max))
+    return fail(EMG_ERR_INVALID, "non-finite damping[0] or abl_gamma_max");
+  if (!mu || !rho || !cp || !b || !x) return fail(EMG_ERR_INVALID, "NULL argument");
   if (p->dim != 2) return fail(EMG_ERR_INVALID, "emg_smooth_noalloc supports dim = 2 only");
   if (p->cycle_precision != 32) return fail(EMG_ERR_INVALID, "emg_smooth_noalloc works on FP32 cycle vectors");
   if (sweeps < 0) return fail(EMG_ERR_INVALID, "sweeps < 0");
@@ -50,16 +88,23 @@ extern "C" emg_status emg_smooth_noalloc(const emg_params* p, const float* mu, c
   if (dev < 0 || dev >= kMaxDevices) return fail(EMG_ERR_INVALID, "device index out of range");
   void* alt = nullptr;
   {
-    // First call on a device: look up the device address of the file-scope array (the host-side
-    // symbol is only a stand-in and must not be passed to a kernel).
+    // First call on a device (or in a new context of it, e.g. after cudaDeviceReset): look up the
+    // device address of the file-scope array (the host-side symbol is only a stand-in and must not
+    // be passed to a kernel).
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_alt_addr[dev]) {
+    unsigned long long ctx = 0;
+    const bool known = current_context_id(&ctx);
+    if (!g_alt_addr[dev] || !known || g_alt_ctx[dev] != ctx) {
       void* ptr = nullptr;
       e = cudaGetSymbolAddress(&ptr, g_noalloc_alt);
       if (e != cudaSuccess) return fail(EMG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_alt_addr[dev] = ptr;
+      // the lookup makes the device's primary context current if no context was yet
+      g_alt_addr[dev] = current_context_id(&ctx) ? ptr : nullptr;
+      g_alt_ctx[dev] = ctx;
+      alt = ptr;
+    } else {
+      alt = g_alt_addr[dev];
     }
-    alt = g_alt_addr[dev];
   }
   // Level-0 grid of the hierarchy the parameters describe (same coefficients as emg_smooth).
   Grid<float> g;

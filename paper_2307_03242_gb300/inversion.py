@@ -57,7 +57,9 @@ class Misfit(torch.autograd.Function):
         for q, u, r in zip(ctx.sources, ctx.fields, ctx.resid):
             if u is None:  # recompute the forward field
                 u = torch.zeros_like(q)
-                s.solve(q, u, tol=ctx.tol, max_iter=4000, restart=ctx.restart)
+                st = s.solve(q, u, tol=ctx.tol, max_iter=4000, restart=ctx.restart)
+                if not st["converged"]:
+                    raise RuntimeError("recomputed forward solve did not converge: %s" % st)
             rhs = torch.zeros_like(q)
             rhs.reshape(-1).index_add_(0, ctx.receivers, r)
             a = torch.zeros_like(q)

@@ -89,14 +89,18 @@ def _inversion_instance(n, source_side, receiver_side):
         data=[torch.from_numpy(d).to(dev) for d in data])
 
 
-def test_misfit_gradient_through_autograd_matches_the_oracle():
+@pytest.mark.parametrize("keep_fields", [True, False])
+def test_misfit_gradient_through_autograd_matches_the_oracle(keep_fields):
+    """keep_fields=False: the backward pass recomputes each forward field (and checks that the
+    recomputing solve converged) instead of keeping it."""
     import torch
     from paper_2307_03242_gb300 import emg, inversion
     w, pb, rec, srcs, data, t = _inversion_instance(16, 2, 4)
     J_ref, g_ref = misfit_and_gradient(pb, [q.ravel() for q in srcs], rec, data)
     lam, mu, rho = (torch.from_numpy(np.ascontiguousarray(a)).cuda().requires_grad_(True) for a in (w.lam, w.mu, w.rho))
     params = emg.params_from_workload(w, 32)
-    J = inversion.misfit(lam, mu, rho, params, t["sources"], t["receivers"], t["data"], tol=1e-11)
+    J = inversion.misfit(lam, mu, rho, params, t["sources"], t["receivers"], t["data"], tol=1e-11,
+                         keep_fields=keep_fields)
     J.backward()
     assert abs(J.item() - J_ref) <= 1e-8 * J_ref
     for got, name in zip((lam.grad, mu.grad, rho.grad), ("lam", "mu", "rho")):

@@ -53,3 +53,15 @@ def test_noalloc_rejects_grids_beyond_its_work_array():
     dummy = ctypes.c_void_p(16)
     st = emg.LIB.emg_smooth_noalloc(ctypes.byref(prm2), dummy, dummy, dummy, dummy, dummy, 1, None)
     assert st == 1 and b"limited to 262144" in emg.LIB.emg_last_error()
+
+
+@pytest.mark.parametrize("field,value", [("h", 0.0), ("h", float("nan")), ("omega", float("inf")),
+                                         ("abl_cells", -1)])
+def test_noalloc_rejects_parameters_that_emg_create_rejects(field, value):
+    """The parameter checks of emg_create run before any device work (no GPU needed)."""
+    from paper_2307_03242_gb300 import emg
+    prm = emg.Params(n=(64, 64), levels=1, cycle_precision=32).to_c()
+    setattr(prm, field, value)
+    dummy = ctypes.c_void_p(16)
+    st = emg.LIB.emg_smooth_noalloc(ctypes.byref(prm), dummy, dummy, dummy, dummy, dummy, 1, None)
+    assert st == 1, emg.LIB.emg_last_error()

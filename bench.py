@@ -3,14 +3,15 @@ FP64 solve, and V-cycle HBM bandwidth, on one GB300.
 
 Workload (default): the 2D heterogeneous configuration -- 2048 x 2048 cells, smooth random medium
 (Vp 1.5-4.5, correlation length 64 cells), 10 points per minimum shear wavelength, point source at
-depth 32, 5-level V(2,2) hierarchy, FGMRES(20) to 1e-6. One "step" is one complete solve from a
-zero initial guess with the right-hand side resident in HBM.
+depth 32, 5-level W(1,1) hierarchy with two coarsest sweeps, FGMRES(5) to 1e-6. One "step" is one
+complete solve from a zero initial guess with the right-hand side resident in HBM.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl emg|reference] [--config c2|c1|c3]
 
 --impl reference times the FP64 CPU oracle (oracle/) on the host cores instead: each step runs a
 few FGMRES iterations on a crop of the same medium and extrapolates to the full solve.
-Prints one JSON line on rank 0.
+Prints one JSON line on rank 0; the default (c2) line carries the other configurations as
+sub-results under "configs".
 """
 from __future__ import annotations
 
@@ -51,6 +52,8 @@ def parse():
     ap.add_argument("--restart", type=int, default=None, help="FGMRES restart length (default: the workload's)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed plain-FP64 solves (after 1 warm-up)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub-configs", action="store_true",
+                    help="c2: leave out the other configurations' sub-results (c1, c2 seed 1, c3, c4, c5)")
     ap.add_argument("--levels", type=int, default=None)
     ap.add_argument("--alpha", type=float, default=None)
     ap.add_argument("--damping", type=float, default=None)
@@ -77,12 +80,12 @@ def workload(name, args=None):
     return w
 
 
-# Sources of the dominant kernel (the finest-level 2D red-black half-sweep); the DRAM traffic
+# Sources of the dominant kernel (the finest-level one-pass 2D red-black sweep); the DRAM traffic
 # recorded from an ncu capture is reported only while these files are unchanged.
-HOT_KERNEL_SOURCES = ["paper_2307_03242_gb300/csrc/vanka2d_fast.cuh",
+HOT_KERNEL_SOURCES = ["paper_2307_03242_gb300/csrc/sweep2d_tile.cuh", "paper_2307_03242_gb300/csrc/vanka2d_fast.cuh",
                       "paper_2307_03242_gb300/csrc/kernels2d.cuh", "paper_2307_03242_gb300/csrc/stencil2d.cuh",
                       "paper_2307_03242_gb300/csrc/emg_types.cuh"]
-HOT_KERNEL_PROFILE = "profiles/vanka2d_c2_2048.txt"
+HOT_KERNEL_PROFILE = "profiles/sweep_tile_c2_2048.txt"
 
 
 def hot_kernel_hash():
@@ -200,15 +203,19 @@ def oracle_sample(w, iters=3, crop=512):
     H = oracle.assemble(pb, 0.0)
     b = np.zeros(H.shape[0], complex)
     b[oracle.active_mask(pb)] = 1.0
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     _, its, _ = oracle.fgmres(lambda v: H @ v, lambda v: oracle.vcycle(hier, v), b, tol=1e-30, restart=w.restart,
                               max_iter=iters)
-    dt = (time.perf_counter() - t0) / its
+    wall, cpu = time.perf_counter() - t0, time.process_time() - c0
+    dt = wall / its
     scale = float(np.prod(w.n)) / float(np.prod(n))
     desc = ("oracle FGMRES(%d)+%s(%d,%d) iterations on a %s crop of the same medium (%d levels), %d iterations "
             "timed, per-iteration time scaled by the cell ratio %.1f" % (w.restart, w.cycle, w.nu_pre, w.nu_post,
                                                                          "x".join(map(str, n)), lv, its, scale))
-    threads = int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or os.cpu_count()
+    # the threads the oracle actually kept busy (process CPU time over wall time): scipy.sparse
+    # products run on one thread, the small dense block solves mostly so
+    threads = max(1, int(round(cpu / wall)))
+    desc += "; %.2f CPU-seconds per wall second on %d host cores" % (cpu / wall, os.cpu_count())
     return dt * scale, desc, threads
 
 
@@ -272,38 +279,37 @@ def run_profile(args):
     print(json.dumps({"profile_iters": st["iterations"], "rel_residual": st["rel_residual"], "workload": w.name}))
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        run_reference(args)
-        return
-    if args.profile_iters > 0:
-        run_profile(args)
-        return
-    if args.config == "c4":
-        run_batch(args)
-        return
-    if args.config == "c5":
-        run_gradient(args)
-        return
+def dist_context():
+    """(world, rank, local device index, device): one process per GPU under torchrun; the process
+    group (NCCL) serves only the barrier and the max-over-ranks timing."""
     import torch
     import torch.distributed as dist
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
+    if world > 1 and not dist.is_initialized():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    return world, rank, local, torch.device("cuda", local)
+
+
+def bench_single(args, w, steps, warmup, fp64_steps, cpu_baseline, e2e_steps=None):
+    """One configuration solved K times from a zero guess (the JSON line of a single-solve
+    workload): the FP32-cycle solve timed with CUDA events, the plain FP64 solve (fp64_steps > 0),
+    the V-cycle alone, the end-to-end solve through host buffers and, on request, the oracle."""
+    import torch
+    import torch.distributed as dist
     from paper_2307_03242_gb300 import emg
-    w = workload(args.config, args)
+    world, rank, local, dev = dist_context()
+    e2e_steps = steps if e2e_steps is None else e2e_steps
     shape = (w.dim + 1,) + tuple(w.n[::-1])
     nvec = int(np.prod(shape))
-    dev = torch.device("cuda", local)
     b = torch.from_numpy(w.rhs.astype(np.complex128)).to(dev)
     # the solver runs on a stream of its own, where its preconditioner cycle is replayed as a
     # captured CUDA graph; the timing events are recorded on that stream
     sst = torch.cuda.Stream(dev)
     s32 = emg.Solver(emg.params_from_workload(w, 32), w.lam, w.mu, w.rho, stream=sst)
+    paths = [s32.sweep_path(l)[0] for l in range(w.levels)]
     x = torch.zeros_like(b)
 
     def barrier():
@@ -315,7 +321,7 @@ def main():
         x.zero_()
         return s.solve(b, x, tol=w.tol, max_iter=2000, restart=args.restart)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         st = solve(s32)
     s32.profile_read(emg.K_ALL)
     s32.profile(True)
@@ -328,12 +334,12 @@ def main():
     with ClockSampler(local) as clk:
         e0.record(stream)
         iters = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             st = solve(s32)
             iters.append(st["iterations"])
         e1.record(stream)
         barrier()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     prof = s32.profile_read(emg.K_SMOOTH)
     breakdown = {name: s32.profile_read(cls) for name, cls in (("restrict", emg.K_RESTRICT), ("prolong", emg.K_PROLONG),
                                                                ("apply64", emg.K_APPLY64), ("krylov", emg.K_KRYLOV))}
@@ -363,17 +369,18 @@ def main():
 
     # plain FP64 solve
     s32.close()
-    s64 = emg.Solver(emg.params_from_workload(w, 64), w.lam, w.mu, w.rho, stream=sst)
-    st64 = solve(s64)
-    barrier()
-    t0 = time.perf_counter()
-    e0.record(stream)
-    for _ in range(args.fp64_steps):
+    t64, st64 = None, None
+    if fp64_steps > 0:
+        s64 = emg.Solver(emg.params_from_workload(w, 64), w.lam, w.mu, w.rho, stream=sst)
         st64 = solve(s64)
-    e1.record(stream)
-    barrier()
-    t64 = e0.elapsed_time(e1) / args.fp64_steps / 1e3
-    s64.close()
+        barrier()
+        e0.record(stream)
+        for _ in range(fp64_steps):
+            st64 = solve(s64)
+        e1.record(stream)
+        barrier()
+        t64 = e0.elapsed_time(e1) / fp64_steps / 1e3
+        s64.close()
 
     # end to end through the public API with host buffers (copies inside the timed region)
     s32 = emg.Solver(emg.params_from_workload(w, 32), w.lam, w.mu, w.rho, stream=sst)
@@ -382,49 +389,105 @@ def main():
     s32.solve_host(bh, xh, tol=w.tol, max_iter=2000, restart=args.restart)
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         xh[:] = 0
         sth = s32.solve_host(bh, xh, tol=w.tol, max_iter=2000, restart=args.restart)
     barrier()
-    te2e = (time.perf_counter() - t0) / args.steps
+    te2e = (time.perf_counter() - t0) / e2e_steps
     s32.close()
 
     peak, peak_kind = load_peaks()
     achieved = prof["bytes"] / (prof["ms"] * 1e-3) / 1e9 if prof["ms"] > 0 else None
-    out = {"metric": METRIC, "value": t32, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+    out = {"metric": METRIC, "value": t32, "unit": "s", "n_gpus": world, "steps": steps, "warmup": warmup,
            "ms_per_step": t32 * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "c64 cycle / c128 outer", "data": "synthetic", "config": config_json(w, args),
-           "iterations": {"fp32_precond": int(np.median(iters)), "fp64_plain": st64["iterations"]},
-           "rel_residual": {"fp32_precond": res32, "fp64_plain": st64["rel_residual"]},
-           "fp64_plain": {"value": t64, "unit": "s", "steps": args.fp64_steps, "warmup": 1},
-           "speedup_vs_fp64": t64 / t32,
+           "iterations": {"fp32_precond": int(np.median(iters)), "fp64_plain": st64["iterations"] if st64 else None},
+           "rel_residual": {"fp32_precond": res32, "fp64_plain": st64["rel_residual"] if st64 else None},
+           "fp64_plain": {"value": t64, "unit": "s", "steps": fp64_steps, "warmup": 1} if st64 else None,
+           "speedup_vs_fp64": t64 / t32 if t64 else None,
            "vcycle": {"ms": vms, "gbs_algorithmic": v_gbs, "bytes_per_cell": per_cell,
                       "frac_of_hbm": v_gbs / peak},
-           "roofline": {"kernel": "vanka half-sweep (finest level, FP32)", "bound": "hbm", "achieved": achieved,
+           "roofline": {"kernel": "one-pass red-black Vanka sweep k2t::sweep_tile (finest level, FP32)",
+                        "bytes_basis": "84 B per cell per sweep (3S + 3r), 60 B from a zero guess, + 6 B of coarse "
+                                       "correction in the first post-sweep", "bound": "hbm", "achieved": achieved,
                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                         "frac": achieved / peak if achieved else None, "traffic": recorded_traffic(),
                         "launches": prof["launches"], "avg_launch_ms": prof["ms"] / max(prof["launches"], 1),
                         "bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
                         "fp32": fp32_fraction(prof)},
-           "fine_level_ms_per_solve": dict({"smooth": prof["ms"] / args.steps},
-                                           **{k: v["ms"] / args.steps for k, v in breakdown.items()}),
+           "fine_level_ms_per_solve": dict({"smooth": prof["ms"] / steps},
+                                           **{k: v["ms"] / steps for k, v in breakdown.items()}),
            "e2e": {"value": te2e, "unit": "s", "h2d_bytes_per_step": 2 * nvec * 16, "d2h_bytes_per_step": nvec * 16},
            "gpu_launches": int(launches)}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    out["sweep_paths"] = [emg.SWEEP_NAMES[p] for p in paths]
+    if rank == 0 and world == 1 and cpu_baseline:
         per_it, desc, threads = oracle_sample(w)
         out["cpu_baseline"] = {"value": per_it * out["iterations"]["fp32_precond"], "unit": "s", "cores": threads,
                                "kind": "oracle", "sample": desc + " x the FP32 solve's iteration count"}
     out["clocks"] = clk.summary()
+    return out
+
+
+def sub_configs(args):
+    """The other configurations, each with its own timing, iterations, end-to-end figure and clock
+    record, at fewer steps so that the default run stays short: the small 128^2 case (C1), a
+    second medium of the 2048^2 configuration (seed 1, held out from the damping choice), the
+    256^3 layered medium (C3), the 64-instance batch (C4) and the 128^3 misfit gradient (C5)."""
+    import copy
+    from workloads import config_c2_random2d
+    out = {}
+    a = copy.copy(args)
+    a.restart = None
+    w1 = workload("c1", a)
+    out["c1"] = bench_single(a, w1, steps=3, warmup=1, fp64_steps=1, cpu_baseline=False, e2e_steps=3)
+    a = copy.copy(args)
+    a.restart = None
+    w = config_c2_random2d(seed=1)
+    a.restart = w.restart
+    r = bench_single(a, w, steps=2, warmup=1, fp64_steps=0, cpu_baseline=False, e2e_steps=1)
+    r["config"]["workload"] = "c2_random_2d_2048_seed1"
+    out["c2_seed1"] = r
+    a = copy.copy(args)
+    a.restart = None
+    w3 = workload("c3", a)
+    out["c3"] = bench_single(a, w3, steps=1, warmup=1, fp64_steps=0, cpu_baseline=False, e2e_steps=1)
+    a = copy.copy(args)
+    out["c4"] = bench_batch(a, steps=1, warmup=1)
+    a = copy.copy(args)
+    a.grid = None
+    out["c5"] = bench_gradient(a, steps=1, warmup=1)
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if args.profile_iters > 0:
+        run_profile(args)
+        return
+    world, rank, local, dev = dist_context()
+    if args.config == "c4":
+        out = bench_batch(args, args.steps, args.warmup)
+    elif args.config == "c5":
+        out = bench_gradient(args, args.steps, args.warmup)
+    else:
+        w = workload(args.config, args)
+        out = bench_single(args, w, args.steps, args.warmup, args.fp64_steps, not args.no_cpu_baseline)
+        if args.config == "c2" and world == 1 and not args.no_sub_configs and args.grid is None:
+            out["configs"] = sub_configs(args)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
+        import torch.distributed as dist
         dist.destroy_process_group()
 
 
 BATCH_METRIC = "time to solve a batch of independent 2D systems to 1e-6 rel. residual (FP32 cycle, FP64 FGMRES), 1 GB300"
 
 
-def run_batch(args):
+def bench_batch(args, steps, warmup):
     """The 2D batch (config_c4_batch): every (instance, source) system solved to 1e-6, all of them
     in one emg_solve_batch call per step (each instance on a stream of its own). Reported: the
     batch time (wall clock between device synchronisations, since the work spans every
@@ -435,13 +498,7 @@ def run_batch(args):
     import torch.distributed as dist
     from paper_2307_03242_gb300 import emg
     from workloads import config_c4_batch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    world, rank, local, dev = dist_context()
     ws = config_c4_batch(args.instances)
     solvers, jobs = [], []
     for w in ws:
@@ -463,18 +520,18 @@ def run_batch(args):
             x.zero_()
         return emg.solve_batch(jobs, tol=tol, max_iter=2000, restart=restart, workers=args.workers)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         res = batch()
     for s in solvers:
         s.profile_read(emg.K_ALL)
     barrier()
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(steps):
             res = batch()
         barrier()
-        tb = (time.perf_counter() - t0) / args.steps
-    launches = sum(s.profile_read(emg.K_ALL)["launches"] for s in solvers) // args.steps
+        tb = (time.perf_counter() - t0) / steps
+    launches = sum(s.profile_read(emg.K_ALL)["launches"] for s in solvers) // steps
     tb = max_over_ranks(tb, device=dev)
     # the same systems one after another, with per-launch instrumentation
     smooth = {"ms": 0.0, "launches": 0, "bytes": 0.0}
@@ -496,21 +553,21 @@ def run_batch(args):
     hx = [torch.empty_like(h).pin_memory() for h in hb]
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         for h, (_, b, _) in zip(hb, jobs):
             b.copy_(h, non_blocking=True)
         batch()
         for h, (_, _, x) in zip(hx, jobs):
             h.copy_(x, non_blocking=True)
         torch.cuda.synchronize()
-    te2e = (time.perf_counter() - t0) / args.steps
+    te2e = (time.perf_counter() - t0) / steps
     nbytes = int(sum(h.numel() for h in hb) * 16)
     its = [r["iterations"] for r in res]
     peak, peak_kind = load_peaks()
     achieved = smooth["bytes"] / (smooth["ms"] * 1e-3) / 1e9 if smooth["ms"] > 0 else None
     sizes = sorted(set(w.n[0] for w in ws))
-    out = {"metric": BATCH_METRIC, "value": tb, "unit": "s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": tb * 1e3, "higher_is_better": False, "scaling": "weak",
+    out = {"metric": BATCH_METRIC, "value": tb, "unit": "s", "n_gpus": world, "steps": steps,
+           "warmup": warmup, "ms_per_step": tb * 1e3, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "c64 cycle / c128 outer", "data": "synthetic",
            "config": {"workload": "c4_batch_%d" % len(ws), "instances": len(ws), "systems": len(jobs),
                       "grids": "%s (squares)" % "/".join(map(str, sizes)), "mcell_systems": round(mcells, 2),
@@ -530,18 +587,17 @@ def run_batch(args):
            "e2e": {"value": te2e, "unit": "s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
            "gpu_launches": int(launches)}
     out["clocks"] = clk.summary()
+    out["sweep_paths"] = {str(n): [emg.SWEEP_NAMES[s.sweep_path(l)[0]] for l in range(s.params.levels)]
+                          for n, s in sorted({w.n[0]: s for w, s in zip(ws, solvers)}.items())}
     for s in solvers:
         s.close()
-    if rank == 0:
-        print(json.dumps(out))
-    if world > 1:
-        dist.destroy_process_group()
+    return out
 
 
 GRADIENT_METRIC = "time per misfit gradient wrt (lambda, mu, rho): forward + adjoint solves of every source, 1 GB300"
 
 
-def run_gradient(args):
+def bench_gradient(args, steps, warmup):
     """One misfit gradient of the 3D inversion setting (config_c5_adjoint: 128^3, 16 sources, 64 x
     64 receivers): per step, a solver built from the current model, a forward solve per source,
     an adjoint solve per source and the material-derivative kernel (inversion.misfit + backward),
@@ -552,13 +608,7 @@ def run_gradient(args):
     import torch.distributed as dist
     from paper_2307_03242_gb300 import emg, inversion
     from workloads import config_c5_adjoint
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    world, rank, local, dev = dist_context()
     n = args.grid or 128
     w = config_c5_adjoint(n)
     params = emg.params_from_workload(w, 32)
@@ -587,7 +637,7 @@ def run_gradient(args):
         J.backward()
         return J, [t.grad for t in leaves]
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         gradient(model)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -595,11 +645,11 @@ def run_gradient(args):
     barrier()
     with ClockSampler(local) as clk:
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             J, g = gradient(model, stats)
         e1.record(stream)
         barrier()
-    tg = max_over_ranks(e0.elapsed_time(e1) / args.steps / 1e3, device=dev)
+    tg = max_over_ranks(e0.elapsed_time(e1) / steps / 1e3, device=dev)
     fwd = [st["iterations"] for st in stats if st["kind"] == "forward"]
     adj = [st["iterations"] for st in stats if st["kind"] == "adjoint"]
     # instrumented pass on a solver built once: finest-level half-sweep bandwidth, launch count
@@ -616,18 +666,18 @@ def run_gradient(args):
     hg = [torch.empty_like(h).pin_memory() for h in hm]
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         m = [h.to(dev, non_blocking=True) for h in hm]
         _, g = gradient(m)
         for h, gg in zip(hg, g):
             h.copy_(gg, non_blocking=True)
         torch.cuda.synchronize()
-    te2e = (time.perf_counter() - t0) / args.steps
+    te2e = (time.perf_counter() - t0) / steps
     nbytes = int(sum(h.numel() for h in hm) * 8)
     peak, peak_kind = load_peaks()
     achieved = prof["bytes"] / (prof["ms"] * 1e-3) / 1e9 if prof["ms"] > 0 else None
-    out = {"metric": GRADIENT_METRIC, "value": tg, "unit": "s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": tg * 1e3, "higher_is_better": False, "scaling": "weak",
+    out = {"metric": GRADIENT_METRIC, "value": tg, "unit": "s", "n_gpus": world, "steps": steps,
+           "warmup": warmup, "ms_per_step": tg * 1e3, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "c64 cycle / c128 outer", "data": "synthetic",
            "config": {"workload": "c5_adjoint_3d_%d" % n, "grid": "%dx%dx%d" % tuple(w.n), "sources": len(sources),
                       "receivers": int(rec.numel()), "cycle": "K(1,1)", "levels": w.levels,
@@ -635,7 +685,7 @@ def run_gradient(args):
                       "l2": "inputs larger than L2" if 16 * 4 * np.prod(w.n) > 129e6 else "inputs smaller than L2",
                       "parallelism": "replicas" if world > 1 else "single"},
            "iterations": {"forward_median": int(np.median(fwd)), "adjoint_median": int(np.median(adj)),
-                          "forward_total": int(sum(fwd)) // args.steps, "adjoint_total": int(sum(adj)) // args.steps},
+                          "forward_total": int(sum(fwd)) // steps, "adjoint_total": int(sum(adj)) // steps},
            "misfit": float(J.item()),
            "roofline": {"kernel": "vanka half-sweep (finest level, FP32, instrumented pass)", "bound": "hbm",
                         "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -649,10 +699,7 @@ def run_gradient(args):
         out["cpu_baseline"] = {"value": per_it * total, "unit": "s", "cores": threads, "kind": "oracle",
                                "sample": desc + " x the forward and adjoint iterations of one gradient"}
     out["clocks"] = clk.summary()
-    if rank == 0:
-        print(json.dumps(out))
-    if world > 1:
-        dist.destroy_process_group()
+    return out
 
 
 def fp32_fraction(prof):
@@ -667,27 +714,32 @@ def fp32_fraction(prof):
 
 
 def vcycle_bytes_per_cell(w, cw, rw):
-    """Algorithmic bytes per finest cell of one preconditioner cycle (unfused red/black
-    half-sweeps), with c = complex word, r = real word, S = (d+1)c per cell of a level:
-      half-sweep     S (read x) + (d+1/2)c (read b) + 3r + (d+1/2)c (write faces, p of the colour)
-      residual + R   2S + 3r (read x, b, material) + S/2^d (write the coarse b)
-      P + correction 2S (read and write x) + S/2^d (read the coarse e)
+    """Algorithmic bytes per finest cell of one preconditioner cycle: the method's minimum traffic
+    of each step (every input read once, every output written once, no stored matrix), with
+    c = complex word, r = real word, S = (d+1)c per cell of a level:
+      sweep (both colours)     3S + 3r (read x, b and mu, rho, 1/(lambda+mu); write x);
+                               2S + 3r for a sweep from a zero guess (x is not read)
+      residual + restriction   2S + 3r (read x, b, material) + S/2^d (write the coarse b)
+      prolongation + correction into the first post-sweep: S/2^d (read the coarse e)
     Level l has 2^-dl of the finest cells. A V-cycle visits every level once; a W- or K-cycle
-    visits level l <= L-2 2^l times and the coarsest level 2^(L-2) times."""
+    visits level l <= L-2 2^l times (the first call of each pair from a zero guess) and the
+    coarsest level 2^(L-2) times (from a zero guess)."""
     d = w.dim
     S = (d + 1) * cw
-    half = S + 2 * (d + 0.5) * cw + 3 * rw
+    sweep = 3 * S + 3 * rw
     g = 1 if w.cycle == "V" else 2
     tot = 0.0
     for l in range(w.levels):
         cells = 2.0 ** (-d * l)
         if l < w.levels - 1:
-            lvl = 2 * (w.nu_pre + w.nu_post) * half + (2 * S + 3 * rw + S / 2 ** d) + (2 * S + S / 2 ** d)
             visits = g ** l
+            zero_visits = 1 if l == 0 else visits // g  # the finest cycle starts from zero, then one call per pair
+            lvl = (w.nu_pre + w.nu_post) * sweep + (2 * S + 3 * rw + S / 2 ** d) + S / 2 ** d
+            tot += cells * (visits * lvl - (zero_visits * S if w.nu_pre > 0 else 0.0))
         else:
-            lvl = 2 * w.coarse_sweeps * half if w.coarse == "smooth" else 0.0
             visits = g ** max(l - 1, 0)
-        tot += visits * cells * lvl
+            lvl = (w.coarse_sweeps * sweep - S) if w.coarse == "smooth" else 0.0
+            tot += visits * cells * lvl
     return tot
 
 if __name__ == "__main__":

@@ -57,6 +57,15 @@ typedef enum {
 enum { EMG_COARSE_DENSE = 0, EMG_COARSE_SMOOTH = 1 };
 enum { EMG_CYCLE_V = 0, EMG_CYCLE_W = 1, EMG_CYCLE_K = 2 };
 enum { EMG_VANKA_FULL = 0, EMG_VANKA_ECONOMIC = 1 };
+/* How a level's red-black sweeps run (emg_params.sweep_path). EMG_SWEEP_AUTO: chosen per level at
+ * creation by timing the candidates below on the level's own buffers (cached per device, grid
+ * size and sweep count for the life of the process). The others force one path on every 2D FP32
+ * level that can take it (the others keep their automatic choice): EMG_SWEEP_HALF: one launch per
+ * colour; EMG_SWEEP_COOP: all sweeps of a call in one cooperative launch; EMG_SWEEP_TILE24 /
+ * EMG_SWEEP_TILE8: one launch per sweep, both colours in shared-memory tiles of 60 x 24 / 60 x 8
+ * cells (n[0] of the level a multiple of 4). Every path computes the same sweeps (Sec. 3.2);
+ * FP32 rounding differs. FP64 cycles and 3D levels ignore the field. */
+enum { EMG_SWEEP_AUTO = 0, EMG_SWEEP_HALF = 1, EMG_SWEEP_COOP = 2, EMG_SWEEP_TILE24 = 3, EMG_SWEEP_TILE8 = 4 };
 
 /* Solver description. All lengths in the same unit as h. */
 typedef struct {
@@ -88,6 +97,7 @@ typedef struct {
                                paper's solves); EMG_VANKA_ECONOMIC: its displacement part is replaced
                                by its diagonal (the paper's LFA variant, Sec. 2.3), in red-black
                                order here */
+  int32_t sweep_path;       /* EMG_SWEEP_*: how the sweeps of 2D FP32 levels run (0: autotuned) */
 } emg_params;
 
 typedef struct {
@@ -215,6 +225,11 @@ enum { EMG_K_SMOOTH = 0, EMG_K_RESTRICT = 1, EMG_K_PROLONG = 2, EMG_K_APPLY64 = 
 emg_status emg_profile(emg_handle h, int enable);
 emg_status emg_profile_read(emg_handle h, int kernel_class, double* total_ms, int64_t* launches,
                             double* bytes);
+
+/* The sweep path level `level` took (EMG_SWEEP_HALF .. EMG_SWEEP_TILE8) and, when it was chosen
+ * by timing, the measured time of one smoothing call of the level in microseconds (else 0).
+ * No counterpart in the paper: it reports the autotuner's choice. */
+emg_status emg_sweep_path(emg_handle h, int level, int32_t* path, double* us_per_call);
 
 /* ---- Allocation-free smoothing. ----
  * No counterpart in the paper: this entry point exists for callers that cannot allocate device

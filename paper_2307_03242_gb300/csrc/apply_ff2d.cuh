@@ -81,6 +81,7 @@ struct cacc {
 template <typename TI>
 __global__ void __launch_bounds__(BX * BY) apply(FineFF g, const cx<TI>* __restrict__ x, const cx<double>* __restrict__ b,
                                                 double bscale, cx<double>* __restrict__ y) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int nx = g.nx, ny = g.ny;

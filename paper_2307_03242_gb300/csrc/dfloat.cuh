@@ -18,38 +18,89 @@ struct f2 {
   float hi, lo;
 };
 
-// Exact split of a double into hi (24 significant bits, truncated) + lo (low 29 mantissa bits,
-// rounded to 24). Integer operations and one int->float conversion; no FP64 arithmetic.
-HD f2 split(double x) {
-  f2 r;
+// Bit access (device intrinsics, memcpy on the host).
+HD unsigned long long dbits(double x) {
 #ifdef __CUDA_ARCH__
-  r.hi = __double2float_rz(x);
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (unsigned long long)__double_as_longlong(x);
 #else
-  r.hi = (float)x;
-  if (std::fabs((double)r.hi) > std::fabs(x)) r.hi = std::nextafter(r.hi, 0.0f);
   unsigned long long b;
   std::memcpy(&b, &x, sizeof b);
+  return b;
 #endif
-  const unsigned int hib = (unsigned int)(b >> 32);
-  const unsigned int lob = (unsigned int)b & 0x1fffffffu;
-  const int e = (int)((hib >> 20) & 0x7ffu);  // biased exponent of x
-  // lo = lob * 2^(e-1075) = (lob * 2^-52) * 2^(e-1023); the second factor is a normal float for
-  // e >= 897, i.e. whenever hi is a normal float; below that lo is dropped.
+}
+HD double bdouble(unsigned long long b) {
 #ifdef __CUDA_ARCH__
-  float sc = (e >= 897 && e <= 1150) ? __int_as_float((e - 896) << 23) : 0.0f;
-  float lo = __uint2float_rn(lob) * 0x1p-52f * sc;
+  return __longlong_as_double((long long)b);
 #else
-  float sc = 0.0f;
-  if (e >= 897 && e <= 1150) {
-    const int bits = (e - 896) << 23;
-    std::memcpy(&sc, &bits, sizeof sc);
-  }
-  float lo = (float)lob * 0x1p-52f * sc;
+  double x;
+  std::memcpy(&x, &b, sizeof x);
+  return x;
 #endif
-  r.lo = (hib & 0x80000000u) ? -lo : lo;
+}
+HD unsigned fbits(float x) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(x);
+#else
+  unsigned b;
+  std::memcpy(&b, &x, sizeof b);
+  return b;
+#endif
+}
+HD float bfloat(unsigned b) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float x;
+  std::memcpy(&x, &b, sizeof x);
+  return x;
+#endif
+}
+
+// Split of a double into hi + lo with integer and FP32 operations only (none on the FP64 pipe,
+// which on this part is ~57x slower): hi = the double truncated to 24 significant bits (the sign,
+// the rebiased exponent and the top 23 mantissa bits), lo = the next 23 mantissa bits, built as
+// ((1 + m 2^-23) - 1) 2^(e-1046), exact. The bits below (6 of 52) are dropped: hi + lo differs
+// from x by less than 2^-46 |x|. Magnitudes outside the normal float range (about 1e-38 .. 3e38)
+// give hi = 0 (tiny) or an infinity (huge; NaN stays NaN); lo is dropped below about 1e-31.
+HD f2 split(double x) {
+  const unsigned long long b = dbits(x);
+  const unsigned hib = (unsigned)(b >> 32), lob = (unsigned)b;
+  const unsigned sgn = hib & 0x80000000u;
+  const int e = (int)((hib >> 20) & 0x7ffu);  // biased exponent of x
+  f2 r;
+  if (e >= 897 && e <= 1150) {
+    r.hi = bfloat(sgn | ((unsigned)(e - 896) << 23) | ((hib & 0xfffffu) << 3) | (lob >> 29));
+    float lo = 0.0f;
+    if (e >= 920) {
+      const float f = bfloat(0x3f800000u | ((lob & 0x1fffffffu) >> 6)) - 1.0f;  // (top 23 of the 29 low bits) 2^-23
+      lo = f * bfloat((unsigned)(e - 919) << 23);                               // times 2^(e-1046)
+    }
+    r.lo = sgn ? -lo : lo;
+  } else if (e < 897) {
+    r.hi = bfloat(sgn);
+    r.lo = 0.0f;
+  } else {
+    const bool nan = e == 2047 && ((hib & 0xfffffu) | lob) != 0;
+    r.hi = bfloat(nan ? 0x7fc00000u : (sgn | 0x7f800000u));
+    r.lo = 0.0f;
+  }
   return r;
 }
+
+// A float widened to a double by assembling its bits (no FP64 instruction); subnormal floats
+// take the plain conversion.
+HD double widen(float f) {
+  const unsigned u = fbits(f);
+  const unsigned ex = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+  if (ex == 0) return m == 0 ? bdouble(sgn) : (double)f;
+  const unsigned long long dex = ex == 255 ? 0x7ffull : (unsigned long long)(ex + 896);
+  return bdouble(sgn | (dex << 52) | ((unsigned long long)m << 29));
+}
+
+// hi + lo as a double: two assembled widenings and one FP64 addition (instead of two conversions
+// and an addition on the FP64 pipe).
+HD double join(float hi, float lo) { return widen(hi) + widen(lo); }
 
 // Knuth TwoSum: s + e == a + b exactly.
 HD void two_sum(float a, float b, float& s, float& e) {
@@ -83,7 +134,7 @@ struct acc {
     hi = s;
     lo += t + a.lo;
   }
-  HD double to_double() const { return (double)hi + (double)lo; }
+  HD double to_double() const { return join(hi, lo); }
   HD f2 norm() const {
     f2 r;
     two_sum(hi, lo, r.hi, r.lo);

@@ -20,6 +20,8 @@
 #include <atomic>
 #include <map>
 #include <thread>
+#include <mutex>
+#include <tuple>
 
 #include "emg.h"
 #include "launch.h"
@@ -92,6 +94,8 @@ struct Level {
   DBuf abl_tab[3];                         // absorbing-layer attenuation per axis (cycle precision)
   int zlo[3] = {1, 1, 1}, zhi[3] = {0, 0, 0};  // lattice range where that attenuation is zero
   DBuf kz1, kz2, kq1, kq2, kr2, kpart, kcoef;  // K-cycle work vectors (levels 1 .. L-2)
+  int path = EMG_SWEEP_HALF;  // how the level's sweeps run (EMG_SWEEP_*)
+  double tuned_us = 0.0;      // measured time of one smoothing call when the path was timed
 };
 
 }  // namespace
@@ -107,6 +111,7 @@ struct emg_ctx {
   DBuf ff3_edge[3], ff3_m[3];              // 3D: edge mu per orientation, face masses
   DBuf cinv;               // dense inverse of the coarsest operator (cycle precision)
   DBuf rscr;               // the fine residual between the residual and restriction kernels
+  DBuf dev_err;            // device status word of bounded waits (bit 0: a tile load timed out)
   int cn = 0;
   // Krylov workspace
   int km = 0;
@@ -303,18 +308,90 @@ void launch_apply(emg_ctx& c, const Grid<T>& g, const void* x, bool x32, const c
 // cooperative launch (measured on the 2048^2 hierarchy: 128^2 to 512^2 gain 15-45 %, 1024^2 loses).
 constexpr long long kCoopMaxColourCells = 1 << 17;
 
+// Whether level l's sweeps run as one-pass tiled sweeps (k2t::sweep_tile).
+bool tiled_level(const emg_ctx& c, int l) {
+  const int p = c.lv[l].path;
+  return p == EMG_SWEEP_TILE24 || p == EMG_SWEEP_TILE8;
+}
+
+// Whether a sweep path can run level l.
+bool path_ok(const emg_ctx& c, int l, int path) {
+  const Level& L = c.lv[l];
+  switch (path) {
+    case EMG_SWEEP_HALF: return true;
+    case EMG_SWEEP_COOP: return c.dim == 2;
+    case EMG_SWEEP_TILE24:
+    case EMG_SWEEP_TILE8: return c.dim == 2 && c.prec == 32 && L.n[0] % 4 == 0 && L.n[0] >= 4;
+    default: return false;
+  }
+}
+
+// The path without timing: the cooperative launch for the 2D levels below the finest with few
+// cells, one launch per colour otherwise.
+int default_path(const emg_ctx& c, int l) {
+  const Level& L = c.lv[l];
+  if (c.dim == 2 && l > 0 && (long long)((L.n[0] + 1) / 2) * L.n[1] <= kCoopMaxColourCells) return EMG_SWEEP_COOP;
+  return EMG_SWEEP_HALF;
+}
+
+// Algorithmic bytes of one one-pass sweep of level l: read x (unless it is zero), b and the three
+// material reals, write x.
+double tiled_sweep_bytes(const emg_ctx& c, int l, bool zero_in) {
+  const double S = (c.dim + 1) * 8.0;
+  return (double)c.lv[l].ncell * ((zero_in ? 2.0 : 3.0) * S + 3 * 4.0);
+}
+
+// `sweeps` red-black sweeps on level l starting from the state in `cur`; `other` is a second
+// vector of (d+1) n values. Returns the buffer that holds the result: one-pass tiled sweeps
+// cannot work in place, so they alternate between cur and other; every other path works in
+// place in cur and uses other as its ping-pong copy of the displacements.
 template <typename T>
-void smooth(emg_ctx& c, int l, const cx<T>* b, cx<T>* x, int sweeps, double w, bool zero_first) {
+void prolong_correct(emg_ctx& c, int l, const cx<T>* e, cx<T>* x);
+
+// e: a coarse correction (level l+1) to add, x += P e, before the first sweep; the one-pass
+// sweep adds it while loading its tiles (prolongation + correction fused into the sweep).
+template <typename T>
+cx<T>* smooth2(emg_ctx& c, int l, const cx<T>* b, cx<T>* cur, cx<T>* other, int sweeps, double w, bool zero_first,
+               const cx<T>* e = nullptr) {
   Level& L = c.lv[l];
   Grid<T> g = level_grid<T>(c, l);
   const size_t N = L.ncell;
-  cx<T>* alt = L.alt.as<cx<T>>();
+  if (e && (sweeps == 0 || zero_first || !std::is_same<T, float>::value || !tiled_level(c, l))) {
+    prolong_correct<T>(c, l, e, cur);
+    e = nullptr;
+  }
+  if (sweeps == 0) {
+    if (zero_first) CK(cudaMemsetAsync(cur, 0, (c.dim + 1) * N * sizeof(cx<T>), c.st));
+    return cur;
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    if (tiled_level(c, l)) {
+      const int ty = L.path == EMG_SWEEP_TILE24 ? 24 : 8;
+      if (!sweep_tile_fits(g, b, cur, other)) raise(EMG_ERR_INVALID, "sweep buffers are not 16-byte aligned");
+      for (int s = 0; s < sweeps; ++s) {
+        const bool zin = zero_first && s == 0;
+        const cx<float>* es = s == 0 ? (const cx<float>*)e : nullptr;
+        const Level* C = es ? &c.lv[l + 1] : nullptr;
+        {
+          // with a correction, the sweep also reads e (3 coarse values per 4 fine cells)
+          ProfScope ps(c, EMG_K_SMOOTH, l, tiled_sweep_bytes(c, l, zin) + (es ? C->ncell * 3 * 8.0 : 0.0));
+          CK(launch_sweep_tile(g, b, cur, other, (float)w, zin ? 1 : 0, es, C ? C->n[0] : 0, C ? C->n[1] : 0, ty,
+                               c.dev_err.as<int>(), c.st));
+          LAUNCHED(c);
+        }
+        std::swap(cur, other);
+      }
+      return cur;
+    }
+  }
+  cx<T>* alt = other;
+  cx<T>* x = cur;
   cx<T>* p = x + (size_t)c.dim * N;
   const double bytes = l == 0 ? half_sweep_bytes<T>(c) : 0.0;
-  if (c.dim == 2 && l > 0 && sweeps > 0 && (long long)((L.n[0] + 1) / 2) * L.n[1] <= kCoopMaxColourCells) {
+  if (c.dim == 2 && L.path == EMG_SWEEP_COOP) {
     CK(launch_sweeps_coop2<T>(g, b, x, alt, sweeps, (T)w, zero_first ? 1 : 0, c.st));
     LAUNCHED(c);
-    return;
+    return cur;
   }
   for (int s = 0; s < sweeps; ++s) {
     for (int colour = 0; colour < 2; ++colour) {
@@ -325,10 +402,112 @@ void smooth(emg_ctx& c, int l, const cx<T>* b, cx<T>* x, int sweeps, double w, b
       if (c.dim == 2) launch_vanka2<T>(g, b, uin, uout, p, colour, (T)w, zin, c.st);
       else launch_vanka3<T>(g, b, uin, uout, p, colour, (T)w, zin, c.st);
       CKL();
-  LAUNCHED(c);
+      LAUNCHED(c);
     }
   }
-  if (sweeps == 0 && zero_first) CK(cudaMemsetAsync(x, 0, (c.dim + 1) * N * sizeof(cx<T>), c.st));
+  return cur;
+}
+
+// Sweeps with the result in x (the level's alternate vector serves as the second buffer).
+template <typename T>
+void smooth(emg_ctx& c, int l, const cx<T>* b, cx<T>* x, int sweeps, double w, bool zero_first) {
+  cx<T>* alt = c.lv[l].alt.as<cx<T>>();
+  cx<T>* r = smooth2<T>(c, l, b, x, alt, sweeps, w, zero_first);
+  if (r != x) CK(cudaMemcpyAsync(x, r, (c.dim + 1) * c.lv[l].ncell * sizeof(cx<T>), cudaMemcpyDeviceToDevice, c.st));
+}
+
+// ---------------------------------------------------------------- sweep-path autotuner
+// A level's smoothing call (its sweep count) is timed on each path that can run it, on the level's
+// own buffers (right after set-up, outside any stream capture), and the fastest is kept. Choices
+// are cached per device, grid, sweep count and smoother for the life of the process, so handles
+// of the same sizes (a batch of instances) tune once.
+struct TuneKey {
+  int dev, nx, ny, sweeps, economic;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, nx, ny, sweeps, economic) < std::tie(o.dev, o.nx, o.ny, o.sweeps, o.economic);
+  }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, std::pair<int, double>> g_tune_cache;
+
+// Mean time of one smoothing call of `sweeps` sweeps on level l along its current path, in us.
+double time_smoothing(emg_ctx& c, int l, int sweeps, double w) {
+  Level& L = c.lv[l];
+  cx<float>* b = L.b.as<cx<float>>();
+  cx<float>* cur = L.x.as<cx<float>>();
+  cx<float>* oth = L.alt.as<cx<float>>();
+  auto call = [&]() {
+    cx<float>* r = smooth2<float>(c, l, b, cur, oth, sweeps, w, false);
+    if (r != cur) std::swap(cur, oth);
+  };
+  call();
+  call();
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  constexpr int reps = 5;
+  CK(cudaEventRecord(e0, c.st));
+  for (int r = 0; r < reps; ++r) call();
+  CK(cudaEventRecord(e1, c.st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return 1e3 * ms / reps;
+}
+
+void choose_sweep_paths(emg_ctx& c) {
+  for (int l = 0; l < c.L; ++l) {
+    Level& L = c.lv[l];
+    L.path = default_path(c, l);
+    L.tuned_us = 0.0;
+    const bool coarsest = l == c.L - 1;
+    if (c.dim != 2 || c.prec != 32 || (coarsest && c.prm.coarse_solver != EMG_COARSE_SMOOTH)) continue;
+    const int forced = c.prm.sweep_path;
+    if (forced != EMG_SWEEP_AUTO) {
+      if (path_ok(c, l, forced)) L.path = forced;
+      continue;
+    }
+    const int sweeps = coarsest ? c.prm.coarse_sweeps : std::max(1, std::max(c.prm.nu_pre, c.prm.nu_post));
+    const double w = coarsest ? c.prm.coarse_damping : L.w;
+    const TuneKey key{c.dev, L.n[0], L.n[1], sweeps, c.prm.smoother};
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        L.path = it->second.first;
+        L.tuned_us = it->second.second;
+        continue;
+      }
+    }
+    const long long colour_cells = (long long)((L.n[0] + 1) / 2) * L.n[1];
+    std::vector<int> cand = {EMG_SWEEP_HALF};
+    if (colour_cells <= (1 << 19)) cand.push_back(EMG_SWEEP_COOP);
+    for (int p : {EMG_SWEEP_TILE24, EMG_SWEEP_TILE8})
+      if (path_ok(c, l, p)) cand.push_back(p);
+    int best = L.path;
+    double best_us = 0.0;
+    for (int p : cand) {
+      L.path = p;
+      const double us = time_smoothing(c, l, sweeps, w);
+      if (best_us == 0.0 || us < best_us) {
+        best = p;
+        best_us = us;
+      }
+    }
+    L.path = best;
+    L.tuned_us = best_us;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = {best, best_us};
+  }
+  // the timing runs swept zero vectors; leave the level buffers as set-up left them
+  for (auto& L : c.lv) {
+    CK(cudaMemsetAsync(L.x.p, 0, L.x.bytes, c.st));
+    CK(cudaMemsetAsync(L.alt.p, 0, L.alt.bytes, c.st));
+  }
+  CK(cudaStreamSynchronize(c.st));
+  c.launches = 0;
 }
 
 template <typename T>
@@ -338,6 +517,18 @@ void residual_restrict(emg_ctx& c, int l, const cx<T>* b, const cx<T>* x, cx<T>*
   Grid<T> g = level_grid<T>(c, l);
   const double cw = 2.0 * sizeof(T);
   ProfScope ps(c, EMG_K_RESTRICT, l, (double)L.ncell * (2 * (c.dim + 1) * cw + 3 * sizeof(T)) + C.ncell * (c.dim + 1) * cw);
+  if constexpr (std::is_same<T, float>::value) {
+    // 2D FP32 levels whose rows meet the tile kernel's alignment rule: one pass, no fine residual
+    // in memory; 60 x 24 tiles where they fill the GPU twice over, 60 x 8 tiles otherwise
+    if (c.dim == 2 && path_ok(c, l, EMG_SWEEP_TILE24) &&
+        !(((uintptr_t)b | (uintptr_t)x | (uintptr_t)bc) % 16)) {
+      const long long tiles24 = (long long)((L.n[0] + 59) / 60) * ((L.n[1] + 23) / 24);
+      const int ty = tiles24 >= 2LL * c.sms ? 24 : 8;
+      CK(launch_resid_restrict_tile(g, b, x, bc, C.n[0], C.n[1], ty, c.dev_err.as<int>(), c.st));
+      LAUNCHED(c);
+      return;
+    }
+  }
   if (c.dim == 2) launch_restrict2<T>(g, b, x, bc, C.n, c.rscr.as<cx<T>>(), c.st);
   else launch_restrict3<T>(g, b, x, bc, C.n, c.rscr.as<cx<T>>(), c.st);
   CKL();
@@ -362,13 +553,9 @@ void coarse_solve(emg_ctx& c, const cx<T>* b, cx<T>* x) {
   const int l = c.L - 1;
   if (c.prm.coarse_solver == EMG_COARSE_DENSE) {
     const int n = c.cn;
-    kv::dense_gemv<T><<<(n + 7) / 8, 256, 0, c.st>>>(c.cinv.as<cx<T>>(), b, x, n);
+    launch_dep(kv::dense_gemv<T>, dim3((n + 7) / 8), dim3(256), 0, c.st, c.cinv.as<cx<T>>(), b, x, n);
     CKL();
   LAUNCHED(c);
-  } else if (c.dim == 2 && c.prm.coarse_sweeps > 0) {
-    Grid<T> g = level_grid<T>(c, l);
-    CK(launch_sweeps_coop2<T>(g, b, x, c.lv[l].alt.as<cx<T>>(), c.prm.coarse_sweeps, (T)c.prm.coarse_damping, 1, c.st));
-    LAUNCHED(c);
   } else {
     smooth<T>(c, l, b, x, c.prm.coarse_sweeps, c.prm.coarse_damping, true);
   }
@@ -383,17 +570,17 @@ void kcoef(emg_ctx& c, int m, const cx<T>* a, const cx<T>* b, double* coef) {
   Level& M = c.lv[m];
   const size_t n = (c.dim + 1) * M.ncell;
   const int nblk = vec_blocks(c, n);
-  kc::dot_parts<T><<<nblk, kc::RT, 0, c.st>>>(a, b, n, M.kpart.as<double>());
+  launch_dep(kc::dot_parts<T>, dim3(nblk), dim3(kc::RT), 0, c.st, a, b, n, M.kpart.as<double>());
   CKL();
   LAUNCHED(c);
-  kc::finalize_coef<<<1, kv::RP, 0, c.st>>>(M.kpart.as<double>(), nblk, coef);
+  launch_dep(kc::finalize_coef, dim3(1), dim3(kv::RP), 0, c.st, M.kpart.as<double>(), nblk, coef);
   CKL();
   LAUNCHED(c);
 }
 
 template <typename T>
 void kaxpy(emg_ctx& c, size_t n, cx<T>* y, const cx<T>* x0, const cx<T>* x, const double* coef, T sgn) {
-  kc::axpy_coef<T><<<vec_blocks(c, n), 256, 0, c.st>>>(y, x0, x, coef, sgn, n);
+  launch_dep(kc::axpy_coef<T>, dim3(vec_blocks(c, n)), dim3(256), 0, c.st, y, x0, x, coef, sgn, n);
   CKL();
   LAUNCHED(c);
 }
@@ -435,17 +622,20 @@ void vcycle(emg_ctx& c, int l, const cx<T>* b, cx<T>* x, bool zero_guess) {
   }
   Level& L = c.lv[l];
   Level& C = c.lv[l + 1];
-  if (zero_guess && c.prm.nu_pre == 0) CK(cudaMemsetAsync(x, 0, (c.dim + 1) * L.ncell * sizeof(cx<T>), c.st));
-  smooth<T>(c, l, b, x, c.prm.nu_pre, L.w, zero_guess);
-  residual_restrict<T>(c, l, b, x, C.b.as<cx<T>>());
+  // the level's state moves between x and the level's alternate vector (one-pass sweeps do not
+  // work in place); it ends in x
+  cx<T>* alt = L.alt.as<cx<T>>();
+  cx<T>* cur = smooth2<T>(c, l, b, x, alt, c.prm.nu_pre, L.w, zero_guess);
+  residual_restrict<T>(c, l, b, cur, C.b.as<cx<T>>());
   if (c.prm.cycle_type == EMG_CYCLE_K && l + 1 < c.L - 1) {
     kcycle_correction<T>(c, l + 1, C.b.as<cx<T>>(), C.x.as<cx<T>>());
   } else {
     vcycle<T>(c, l + 1, C.b.as<cx<T>>(), C.x.as<cx<T>>(), true);
     if (c.prm.cycle_type == EMG_CYCLE_W && l + 1 < c.L - 1) vcycle<T>(c, l + 1, C.b.as<cx<T>>(), C.x.as<cx<T>>(), false);
   }
-  prolong_correct<T>(c, l, C.x.as<cx<T>>(), x);
-  smooth<T>(c, l, b, x, c.prm.nu_post, L.w, false);
+  // prolongation + correction, fused into the first post-sweep where the sweep is one pass
+  cur = smooth2<T>(c, l, b, cur, cur == x ? alt : x, c.prm.nu_post, L.w, false, C.x.as<const cx<T>>());
+  if (cur != x) CK(cudaMemcpyAsync(x, cur, (c.dim + 1) * L.ncell * sizeof(cx<T>), cudaMemcpyDeviceToDevice, c.st));
 }
 
 // ---------------------------------------------------------------- host assembly of the coarsest operator
@@ -691,7 +881,7 @@ void build(emg_ctx& c) {
     upload_abl_tables<T>(c, L);
     L.b.alloc((d + 1) * L.ncell * sizeof(cx<T>));
     L.x.alloc((d + 1) * L.ncell * sizeof(cx<T>));
-    L.alt.alloc(d * L.ncell * sizeof(cx<T>));
+    L.alt.alloc((d + 1) * L.ncell * sizeof(cx<T>));  // a whole second state (one-pass sweeps alternate)
     if (c.prm.cycle_type == EMG_CYCLE_K && l >= 1 && l < c.L - 1) {
       const size_t vb = (d + 1) * L.ncell * sizeof(cx<T>);
       L.kz1.alloc(vb);
@@ -707,6 +897,8 @@ void build(emg_ctx& c) {
     CK(cudaMemset(L.alt.p, 0, L.alt.bytes));
   }
   if (c.L > 1) c.rscr.alloc((d + 1) * c.lv[0].ncell * sizeof(cx<T>));
+  c.dev_err.alloc(16);
+  CK(cudaMemset(c.dev_err.p, 0, c.dev_err.bytes));
   // finest material in FP64 for the outer operator
   Level& F = c.lv[0];
   std::vector<double> cp(F.ncell);
@@ -732,6 +924,7 @@ void build(emg_ctx& c) {
     c.cn = (int)NF;
   }
   CK(cudaDeviceSynchronize());
+  choose_sweep_paths(c);
 }
 
 // ---------------------------------------------------------------- FP64 Krylov helpers
@@ -755,8 +948,8 @@ void ensure_krylov(emg_ctx& c, int m) {
 template <int NV>
 void launch_mdot(emg_ctx& c, bool ff, const cx<double>* V, size_t ldv, const cx<double>* w, size_t n, double* part,
                  int nblk) {
-  if (ff) kf::mdot<NV><<<nblk, kv::RT, 0, c.st>>>(V, ldv, w, n, part);
-  else kv::mdot<NV><<<nblk, kv::RT, 0, c.st>>>(V, ldv, w, n, part);
+  if (ff) launch_dep(kf::mdot<NV>, dim3(nblk), dim3(kv::RT), 0, c.st, V, ldv, w, n, part);
+  else launch_dep(kv::mdot<NV>, dim3(nblk), dim3(kv::RT), 0, c.st, V, ldv, w, n, part);
   CKL();
   LAUNCHED(c);
 }
@@ -795,7 +988,7 @@ void mdots(emg_ctx& c, bool ff, const cx<double>* V, size_t ldv, int cnt, const 
       }
     }
     const int nr = 2 * nv + 1;
-    kv::reduce_parts<<<nr, kv::RP, 0, c.st>>>(part, nblk, nr, red + off);
+    launch_dep(kv::reduce_parts, dim3(nr), dim3(kv::RP), 0, c.st, part, nblk, nr, red + off);
     CKL();
     LAUNCHED(c);
     chunks.push_back({s, nv});
@@ -827,12 +1020,12 @@ double update_scale(emg_ctx& c, cx<double>* w, const cx<double>* V, size_t ldv,
   for (int i = 0; i < cnt; ++i) co.c[i] = {to_f2(h[i].real()), to_f2(h[i].imag())};
   {
     ProfScope ps(c, EMG_K_KRYLOV, 0, (double)n * 16 * (cnt + 2) + (out32 ? n * 8.0 : 0.0));
-    kf::update_scale<<<nblk, kv::RT, 0, c.st>>>(w, V, ldv, cnt, co, to_f2(s), n, out32, c.part.as<double>());
+    launch_dep(kf::update_scale, dim3(nblk), dim3(kv::RT), 0, c.st, w, V, ldv, cnt, co, to_f2(s), n, out32, c.part.as<double>());
     CKL();
     LAUNCHED(c);
   }
   if (!want_norm) return 0.0;
-  kv::reduce_parts<<<1, kv::RP, 0, c.st>>>(c.part.as<double>(), nblk, 1, c.red.as<double>());
+  launch_dep(kv::reduce_parts, dim3(1), dim3(kv::RP), 0, c.st, c.part.as<double>(), nblk, 1, c.red.as<double>());
   CKL();
   LAUNCHED(c);
   CK(cudaMemcpyAsync(c.hred, c.red.p, sizeof(double), cudaMemcpyDeviceToHost, c.st));
@@ -980,6 +1173,17 @@ void precondition(emg_ctx& c, const cx<double>* v, cx<T>* z) {
   vcycle<T>(c, 0, b, z, true);
 }
 
+// Reads the device status word of the bounded waits (after a synchronisation): a tile load that
+// timed out left the sweep's result unusable.
+void check_device_status(emg_ctx& c) {
+  int flags = 0;
+  CK(cudaMemcpy(&flags, c.dev_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flags) {
+    CK(cudaMemset(c.dev_err.p, 0, sizeof(int)));
+    raise(EMG_ERR_TIMEOUT, "a shared-memory tile load of the one-pass sweep timed out");
+  }
+}
+
 // Re-orthogonalise when ||w'||^2 < kReorth ||w||^2. At that ratio the Pythagorean norm keeps
 // ~13 correct digits (its absolute error is ~eps ||w||^2) and one classical Gram-Schmidt pass
 // leaves the new vector orthogonal to ~eps ||w||/||w'|| ~ 1e-14, far below what a 1e-6 solve
@@ -1019,7 +1223,7 @@ emg_status solve_impl(emg_ctx& c, const cx<double>* b, cx<double>* x, double tol
   }
   const double sc = std::ldexp(1.0, -std::ilogb(bnorm));  // power of two: sc*||b|| in [1, 2)
   const double bhat = sc * bnorm;
-  kv::scale<<<vec_blocks(c, n), 256, 0, c.st>>>(x, x, sc, n);
+  launch_dep(kv::scale, dim3(vec_blocks(c, n)), dim3(256), 0, c.st, x, x, sc, n);
   CKL();
   LAUNCHED(c);
   auto true_residual = [&]() {
@@ -1108,17 +1312,18 @@ emg_status solve_impl(emg_ctx& c, const cx<double>* b, cx<double>* x, double tol
     for (int i = 0; i < k; ++i) co.c[i] = {to_f2(y[i].real()), to_f2(y[i].imag())};
     {
       ProfScope ps(c, EMG_K_KRYLOV, 0, (double)n * (32.0 + k * (f32 ? 8.0 : 16.0)));
-      kf::combine<T><<<vec_blocks(c, n), kv::RT, 0, c.st>>>(x, Z, n, k, co, n);
+      launch_dep(kf::combine<T>, dim3(vec_blocks(c, n)), dim3(kv::RT), 0, c.st, x, Z, n, k, co, n);
       CKL();
       LAUNCHED(c);
     }
     beta = true_residual();
     ++restarts;
   }
-  kv::scale<<<vec_blocks(c, n), 256, 0, c.st>>>(x, x, 1.0 / sc, n);
+  launch_dep(kv::scale, dim3(vec_blocks(c, n)), dim3(256), 0, c.st, x, x, 1.0 / sc, n);
   CKL();
   LAUNCHED(c);
   CK(cudaStreamSynchronize(c.st));
+  check_device_status(c);
   if (st) {
     st->iterations = its;
     st->restarts = restarts;
@@ -1146,6 +1351,7 @@ void check_level_params(const emg_params* p) {
   if (p->cycle_type != EMG_CYCLE_V && p->cycle_type != EMG_CYCLE_W && p->cycle_type != EMG_CYCLE_K)
     raise(EMG_ERR_INVALID, "unknown cycle_type");
   if (p->smoother != EMG_VANKA_FULL && p->smoother != EMG_VANKA_ECONOMIC) raise(EMG_ERR_INVALID, "unknown smoother");
+  if (p->sweep_path < EMG_SWEEP_AUTO || p->sweep_path > EMG_SWEEP_TILE8) raise(EMG_ERR_INVALID, "unknown sweep_path");
 }
 
 // Every check of emg_create: one level's, then the hierarchy's.
@@ -1277,6 +1483,17 @@ emg_status emg_level_info(emg_handle h, int level, int32_t n[3], double* cell_si
   check_level(c, level, false);
   for (int a = 0; a < 3; ++a) n[a] = c.lv[level].n[a];
   if (cell_size) *cell_size = c.lv[level].h;
+  ABI_CATCH
+  return EMG_OK;
+}
+
+emg_status emg_sweep_path(emg_handle h, int level, int32_t* path, double* us_per_call) {
+  ABI_TRY
+  emg_ctx& c = *checked(h);
+  check_level(c, level, false);
+  if (!path) raise(EMG_ERR_INVALID, "path is NULL");
+  *path = c.lv[level].path;
+  if (us_per_call) *us_per_call = c.lv[level].tuned_us;
   ABI_CATCH
   return EMG_OK;
 }

@@ -6,6 +6,8 @@
 
 #define HD __host__ __device__ __forceinline__
 
+#include "pdl.cuh"
+
 template <typename T>
 struct alignas(2 * sizeof(T)) cx {
   T re, im;

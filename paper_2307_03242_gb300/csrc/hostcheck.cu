@@ -5,13 +5,18 @@
 // interior and attenuation-free variants; the 3D float-float FP64 apply of apply_ff3d.cuh on the
 // library's host-built coefficients), looped over the cells on the host. Not part of the solve path;
 // libemg_hostcheck.so holds no device code that runs.
+#include <cmath>
+#include <limits>
 #include <vector>
 
 #include "adjoint.cuh"
 #include "adjoint_ff3.cuh"
+#include "dfloat.cuh"
 #include "ff3_setup.h"
 #include "residual2d_fast.cuh"
 #include "residual3d.cuh"
+#include "sweep2d_tile.cuh"
+#include "residual2d_tile.cuh"
 #include "vanka2d_fast.cuh"
 
 namespace {
@@ -222,9 +227,196 @@ void residual3(const Level2<T, 3>& L, const double* b64, const double* x64, doub
   from_cx(r, r64);
 }
 
+// One full sweep of the one-pass tiled kernel (k2t::sweep_tile) on the host: the same tiles, the
+// same shared-region contents (zeros outside the grid as the TMA copies give them, clamped
+// material and zeroed boundary faces on boundary tiles) and the same colour-0 / colour-1 phases
+// and lane mapping. Shared entries the kernel never writes before reading are poisoned with NaN
+// (the colour-0 faces of interior tiles), so a read of one shows in the result.
+template <int TYV>
+void sweep_tiled(const Grid<float>& g, const cx<float>* b, const cx<float>* xin, cx<float>* xout, float w, int zero_in,
+                 const cx<float>* e = nullptr, int nxc = 0, int nyc = 0) {
+  using namespace k2t;
+  using G = Geo<TYV>;
+  constexpr int TY = G::TY, PLANE = G::PLANE, EX = G::EX, EPLANE = G::EPLANE;
+  const size_t N = (size_t)g.nx * g.ny;
+  const float nan = std::numeric_limits<float>::quiet_NaN();
+  std::vector<cx<float>> U(3 * PLANE), V(2 * PLANE);
+  std::vector<float> MU(PLANE), RHO(PLANE);
+  const int tx = (g.nx + TX - 1) / TX, ty = (g.ny + TY - 1) / TY;
+  for (int by = 0; by < ty; ++by)
+    for (int bx = 0; bx < tx; ++bx) {
+      const Tile t = tile_of<G>(g, bx, by);
+      for (int q = 0; q < PLANE; ++q) {
+        const int gx = t.x0 - HALO + q % DX, gy = t.y0 - HALO + q / DX;
+        const bool in = gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny;
+        const size_t k = (size_t)gy * g.nx + gx;
+        for (int c = 0; c < 3; ++c) U[c * PLANE + q] = (in && !zero_in) ? xin[c * N + k] : czero<float>();
+        MU[q] = in ? g.mu[k] : 0.f;
+        RHO[q] = in ? g.rho[k] : 0.f;
+      }
+      if (e) {
+        // the coarse box as the TMA copy gives it: zeros outside the coarse grid, NaN beyond the box
+        for (auto& v : V) v = mkc<float>(nan, nan);
+        const int ex0 = t.x0 / 2 - 4, ey0 = t.y0 / 2 - 3;
+        const size_t Nc = (size_t)nxc * nyc;
+        for (int c = 0; c < 3; ++c)
+          for (int q = 0; q < EPLANE; ++q) {
+            const int I = ex0 + q % EX, J = ey0 + q / EX;
+            const bool in = I >= 0 && I < nxc && J >= 0 && J < nyc;
+            V[c * EPLANE + q] = in ? e[c * Nc + (size_t)J * nxc + I] : czero<float>();
+          }
+        if (t.fast) add_prolonged<G, true>(g, t, U.data(), V.data(), nxc, nyc, 0, 1);
+        else add_prolonged<G, false>(g, t, U.data(), V.data(), nxc, nyc, 0, 1);
+      }
+      for (auto& v : V) v = t.boundary ? czero<float>() : mkc<float>(nan, nan);
+      if (t.boundary) fix_boundary<G>(g, t, U.data(), MU.data(), RHO.data(), 0, 1);
+      View s{U.data(), U.data() + PLANE, U.data() + 2 * PLANE, MU.data(), RHO.data()};
+      cx<float>* v1 = V.data();
+      cx<float>* v2 = V.data() + PLANE;
+      for (int patch = 0; patch < G::C0_PATCHES; ++patch)
+        for (int lane = 0; lane < 32; ++lane) {
+          int lx, ly;
+          c0_pos(patch, lane, lx, ly);
+          if (t.fast) {
+            if (zero_in) relax_c0<true, true>(g, t, s, v1, v2, b, w, lx, ly);
+            else relax_c0<true, false>(g, t, s, v1, v2, b, w, lx, ly);
+          } else {
+            if (zero_in) relax_c0<false, true>(g, t, s, v1, v2, b, w, lx, ly);
+            else relax_c0<false, false>(g, t, s, v1, v2, b, w, lx, ly);
+          }
+        }
+      const View s1{v1, v2, U.data() + 2 * PLANE, MU.data(), RHO.data()};
+      for (int patch = 0; patch < G::C1_PATCHES; ++patch)
+        for (int lane = 0; lane < 32; ++lane) {
+          int lx, ly;
+          if (!c1_pos(patch, lane, lx, ly)) continue;
+          if (t.fast) relax_c1<true>(g, t, s1, b, xout, w, lx, ly);
+          else relax_c1<false>(g, t, s1, b, xout, w, lx, ly);
+        }
+    }
+}
+
+// The one-pass residual + restriction (k2t::resid_restrict_tile) on the host: the same tiles,
+// shared-region contents, phases and work order; unwritten shared entries are NaN.
+template <int TYV>
+void resid_restrict_tiled(const Grid<float>& g, const cx<float>* b, const cx<float>* x, cx<float>* bc, int nxc,
+                          int nyc) {
+  using namespace k2t;
+  using G = Geo<TYV>;
+  constexpr int TY = G::TY, PLANE = G::PLANE;
+  const size_t N = (size_t)g.nx * g.ny;
+  const float nan = std::numeric_limits<float>::quiet_NaN();
+  std::vector<cx<float>> U(3 * PLANE), V(2 * PLANE);
+  std::vector<float> MU(PLANE), RHO(PLANE);
+  for (int by = 0; by < (g.ny + TY - 1) / TY; ++by)
+    for (int bx = 0; bx < (g.nx + TX - 1) / TX; ++bx) {
+      const Tile t = tile_of<G>(g, bx, by);
+      for (int q = 0; q < PLANE; ++q) {
+        const int gx = t.x0 - HALO + q % DX, gy = t.y0 - HALO + q / DX;
+        const bool in = gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny;
+        const size_t k = (size_t)gy * g.nx + gx;
+        for (int c = 0; c < 3; ++c) U[c * PLANE + q] = in ? x[c * N + k] : czero<float>();
+        MU[q] = in ? g.mu[k] : 0.f;
+        RHO[q] = in ? g.rho[k] : 0.f;
+      }
+      for (auto& v : V) v = mkc<float>(nan, nan);
+      if (t.boundary) fix_boundary<G>(g, t, U.data(), MU.data(), RHO.data(), 0, 1);
+      const View s{U.data(), U.data() + PLANE, U.data() + 2 * PLANE, MU.data(), RHO.data()};
+      constexpr int EW = TX + 1, EH = TY + 1;
+      for (int q = 0; q < EW * EH; ++q) {
+        const int lx = HALO - 1 + q % EW, ly = HALO - 1 + q / EW;
+        if (t.noabl) resid_phase1<true>(g, t, s, V.data(), V.data() + PLANE, b, lx, ly);
+        else resid_phase1<false>(g, t, s, V.data(), V.data() + PLANE, b, lx, ly);
+      }
+      for (int q = 0; q < (TX / 2) * (TY / 2); ++q)
+        restrict_phase2(g, t, s, V.data(), V.data() + PLANE, b, bc, nxc, nyc, q % (TX / 2), q / (TX / 2));
+    }
+}
+
 }  // namespace
 
 extern "C" {
+
+// One-pass tiled residual + restriction (FP32) of a 2D level: bc (complex128, 3 (nx/2)(ny/2)) =
+// R (b - H_s x); the arguments of emg_hc_residual_restrict2 without prec, then the tile height.
+int emg_hc_resid_restrict_tiled(const int* n, double h, double beta, double omega, double att, double abl_len,
+                                double abl_gmax, double Lx, double Ly, const double* mu, const double* rho,
+                                const double* cp, const double* b64, const double* x64, double* bc64, int ty) {
+  if (n[0] % 4 || n[0] < 4 || n[1] < 2 || (ty != 24 && ty != 8)) return -1;
+  Level2<float> L(n, h, beta, omega, att, abl_len, abl_gmax, Lx, Ly, mu, rho, cp);
+  const size_t N = (size_t)n[0] * n[1];
+  const int nxc = n[0] / 2, nyc = n[1] / 2;
+  std::vector<cx<float>> b = to_cx<float>(b64, 3 * N), x = to_cx<float>(x64, 3 * N),
+                         bc(3 * (size_t)nxc * nyc, mkc<float>(std::numeric_limits<float>::quiet_NaN(), 0.f));
+  if (ty == 24) resid_restrict_tiled<24>(L.g, b.data(), x.data(), bc.data(), nxc, nyc);
+  else resid_restrict_tiled<8>(L.g, b.data(), x.data(), bc.data(), nxc, nyc);
+  from_cx(bc, bc64);
+  return 0;
+}
+
+// The float-float split and join of the FP64 outer kernels (dfloat.cuh) on n doubles.
+int emg_hc_split_join(const double* x, int n, float* hi, float* lo, double* joined, double* widened) {
+  for (int k = 0; k < n; ++k) {
+    const df::f2 r = df::split(x[k]);
+    hi[k] = r.hi;
+    lo[k] = r.lo;
+    joined[k] = df::join(r.hi, r.lo);
+    widened[k] = df::widen(r.hi);
+  }
+  return 0;
+}
+
+// x += P e, then `sweeps` one-pass tiled sweeps with the correction added by the first one's tile
+// loads (the fused post-smoothing of the cycle); e: complex128 coarse vector of 3 (nx/2)(ny/2).
+int emg_hc_prolong_sweep_tiled(const int* n, double h, double beta, double omega, double att, double abl_len,
+                               double abl_gmax, double Lx, double Ly, const double* mu, const double* rho,
+                               const double* cp, const double* b64, const double* e64, double* x64, double w,
+                               int sweeps, int ty) {
+  if (ty != 24 && ty != 8) return -1;
+  if (n[0] % 4 || n[0] < 4 || n[1] < 2 || sweeps < 1) return -1;
+  Level2<float> L(n, h, beta, omega, att, abl_len, abl_gmax, Lx, Ly, mu, rho, cp);
+  const size_t N = (size_t)n[0] * n[1];
+  const int nxc = n[0] / 2, nyc = n[1] / 2;
+  std::vector<cx<float>> b = to_cx<float>(b64, 3 * N), x = to_cx<float>(x64, 3 * N), y(3 * N),
+                         e = to_cx<float>(e64, 3 * (size_t)nxc * nyc);
+  const float nan = std::numeric_limits<float>::quiet_NaN();
+  for (int s = 0; s < sweeps; ++s) {
+    for (auto& v : y) v = mkc<float>(nan, nan);
+    if (ty == 24) sweep_tiled<24>(L.g, b.data(), x.data(), y.data(), (float)w, 0, s == 0 ? e.data() : nullptr, nxc, nyc);
+    else sweep_tiled<8>(L.g, b.data(), x.data(), y.data(), (float)w, 0, s == 0 ? e.data() : nullptr, nxc, nyc);
+    std::swap(x, y);
+  }
+  from_cx(x, x64);
+  return 0;
+}
+
+// `sweeps` one-pass tiled sweeps (FP32) of a 2D level, complex128 b and x (x in/out), with the
+// arguments of emg_hc_vanka2_sweeps; returns the number of tiles whose shared region lies
+// inside the grid without attenuation (the kernel's interior, attenuation-free variant), or -1
+// if the grid does not meet the kernel's rules.
+int emg_hc_sweep_tiled(const int* n, double h, double beta, double omega, double att, double abl_len, double abl_gmax,
+                       double Lx, double Ly, const double* mu, const double* rho, const double* cp, const double* b64,
+                       double* x64, double w, int sweeps, int zero_first, int ty) {
+  if (n[0] % 4 || n[0] < 4 || n[1] < 2 || (ty != 24 && ty != 8)) return -1;
+  Level2<float> L(n, h, beta, omega, att, abl_len, abl_gmax, Lx, Ly, mu, rho, cp);
+  const size_t N = (size_t)n[0] * n[1];
+  std::vector<cx<float>> b = to_cx<float>(b64, 3 * N), x = to_cx<float>(x64, 3 * N), y(3 * N);
+  const float nan = std::numeric_limits<float>::quiet_NaN();
+  for (int s = 0; s < sweeps; ++s) {
+    for (auto& v : y) v = mkc<float>(nan, nan);  // every entry must be written
+    if (ty == 24) sweep_tiled<24>(L.g, b.data(), x.data(), y.data(), (float)w, (zero_first && s == 0) ? 1 : 0);
+    else sweep_tiled<8>(L.g, b.data(), x.data(), y.data(), (float)w, (zero_first && s == 0) ? 1 : 0);
+    std::swap(x, y);
+  }
+  from_cx(x, x64);
+  int interior = 0;
+  for (int by = 0; by < (n[1] + ty - 1) / ty; ++by)
+    for (int bx = 0; bx < (n[0] + k2t::TX - 1) / k2t::TX; ++bx) {
+      const k2t::Tile t = ty == 24 ? k2t::tile_of<k2t::Geo<24>>(L.g, bx, by) : k2t::tile_of<k2t::Geo<8>>(L.g, bx, by);
+      interior += t.fast ? 1 : 0;
+    }
+  return interior;
+}
 
 // 3D FP64 apply of the outer solve in float-float arithmetic: y = H x (shift 0) or H_s x, with
 // the coefficient arrays built as the library builds them (ff3::build_host, ff3::make).

@@ -12,6 +12,7 @@ constexpr int RT = 256;
 template <typename T>
 __global__ void __launch_bounds__(RT) dot_parts(const cx<T>* __restrict__ a, const cx<T>* __restrict__ b, size_t n,
                                                 double* part) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   double acc[3] = {0.0, 0.0, 0.0};
   for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < n; e += (size_t)gridDim.x * RT) {
     const cx<T> x = a[e], y = b[e];
@@ -24,6 +25,7 @@ __global__ void __launch_bounds__(RT) dot_parts(const cx<T>* __restrict__ a, con
 
 // coef = <a, b> / <a, a> from the partials (fixed summation order), stored as (re, im).
 __global__ void finalize_coef(const double* __restrict__ part, int nblk, double* __restrict__ coef) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   __shared__ double s[3][kv::RP];
   double v[3] = {0.0, 0.0, 0.0};
   for (int b = threadIdx.x; b < nblk; b += kv::RP)
@@ -46,6 +48,7 @@ __global__ void finalize_coef(const double* __restrict__ part, int nblk, double*
 template <typename T>
 __global__ void axpy_coef(cx<T>* y, const cx<T>* x0, const cx<T>* __restrict__ x, const double* __restrict__ coef,
                           T sgn, size_t n) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const cx<T> c = mkc<T>((T)coef[0] * sgn, (T)coef[1] * sgn);
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const cx<T> v = x0 ? x0[e] : czero<T>();

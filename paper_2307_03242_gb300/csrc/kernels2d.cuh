@@ -57,6 +57,7 @@ HD void cell_solve(cx<T> a1[4], cx<T> a2[4], const bool ex[4], T ih, T t0, T cp,
 template <typename T, typename TI>
 __global__ void __launch_bounds__(BX * BY) apply(Grid<T> g, const cx<TI>* __restrict__ x,
                                                 const cx<T>* __restrict__ b, T bscale, cx<T>* __restrict__ y) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
@@ -95,6 +96,7 @@ HD cx<T> ec_p(const cx<T>* e, int I, int J, int nxc, int nyc) {
 template <typename T>
 __global__ void __launch_bounds__(BX * BY) prolong_add(const cx<T>* __restrict__ e, cx<T>* __restrict__ x,
                                                       int nx, int ny, int nxc, int nyc) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i >= nx || j >= ny) return;

@@ -18,6 +18,7 @@ constexpr int UPD = 4;
 template <int NV>
 __global__ void __launch_bounds__(RT) mdot(const cx<double>* __restrict__ V, size_t ldv,
                                            const cx<double>* __restrict__ w, size_t n, double* part) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   constexpr int U = NV <= 2 ? 4 : (NV <= 6 ? 2 : 1);
   df::acc are[NV > 0 ? NV : 1], aim[NV > 0 ? NV : 1], ann;
   const size_t stride = (size_t)gridDim.x * RT;
@@ -78,6 +79,7 @@ struct Coefs {
 __global__ void __launch_bounds__(RT) update_scale(cx<double>* __restrict__ w, const cx<double>* __restrict__ V,
                                                    size_t ldv, int cnt, Coefs h, f2 s, size_t n,
                                                    cx<float>* __restrict__ out32, double* part) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   df::acc nn;
   const size_t stride = (size_t)gridDim.x * RT;
   const cx<double> z = czero<double>();
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(RT) update_scale(cx<double>* __restrict__ w, c
       ore.fma_ff(re[u].norm(), s);
       oim.fma_ff(im[u].norm(), s);
       const f2 fr = ore.norm(), fi = oim.norm();
-      w[e] = mkc<double>((double)fr.hi + (double)fr.lo, (double)fi.hi + (double)fi.lo);
+      w[e] = mkc<double>(df::join(fr.hi, fr.lo), df::join(fi.hi, fi.lo));
       if (out32) out32[e] = mkc<float>(fr.hi, fi.hi);
       nn.fma_ff(fr, fr);
       nn.fma_ff(fi, fi);
@@ -130,6 +132,7 @@ __global__ void __launch_bounds__(RT) update_scale(cx<double>* __restrict__ w, c
 template <typename TZ>
 __global__ void __launch_bounds__(RT) combine(cx<double>* __restrict__ x, const cx<TZ>* __restrict__ Z, size_t ldz,
                                               int cnt, Coefs y, size_t n) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const size_t stride = (size_t)gridDim.x * RT;
   for (size_t e0 = (size_t)blockIdx.x * RT + threadIdx.x; e0 < n; e0 += UPD * stride) {
     df::acc re[UPD], im[UPD];
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(RT) combine(cx<double>* __restrict__ x, const 
       const size_t e = e0 + u * stride;
       if (e >= n) break;
       const f2 fr = re[u].norm(), fi = im[u].norm();
-      x[e] = mkc<double>((double)fr.hi + (double)fr.lo, (double)fi.hi + (double)fi.lo);
+      x[e] = mkc<double>(df::join(fr.hi, fr.lo), df::join(fi.hi, fi.lo));
     }
   }
 }

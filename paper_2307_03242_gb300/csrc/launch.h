@@ -40,6 +40,23 @@ template <typename TI>
 void launch_apply_ff2(const ff2::FineFF& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y,
                       cudaStream_t st);
 
+// One full red-black sweep of a 2D FP32 level in one pass (k2t::sweep_tile): xin -> xout, which
+// must be distinct buffers of (d+1) n_x n_y values; zero_in: xin is taken as zero and not read;
+// e (nullptr: none): a coarse correction on the nxc x nyc grid added as xin + P e before the
+// sweep (prolongation + correction fused into the first post-sweep).
+// err: a device status word (bit 0 set if a tile load timed out). sweep_tile_fits says whether
+// the grid and pointers meet the kernel's alignment rules (n_x a multiple of 4, 16-byte aligned
+// buffers); otherwise the two half-sweep launches are used.
+bool sweep_tile_fits(const Grid<float>& g, const void* b, const void* xin, const void* xout);
+// ty: the tile height, 24 or 8 (more, smaller tiles for small grids).
+cudaError_t launch_sweep_tile(const Grid<float>& g, const cx<float>* b, const cx<float>* xin, cx<float>* xout, float w,
+                              int zero_in, const cx<float>* e, int nxc, int nyc, int ty, int* err, cudaStream_t st);
+
+// b_c = R (b - H_s x) of a 2D FP32 level in one pass (k2t::resid_restrict_tile): no fine residual
+// is written. Same tile geometry and alignment rules as launch_sweep_tile.
+cudaError_t launch_resid_restrict_tile(const Grid<float>& g, const cx<float>* b, const cx<float>* x, cx<float>* bc,
+                                       int nxc, int nyc, int ty, int* err, cudaStream_t st);
+
 template <typename T>
 cudaError_t launch_sweeps_coop2(const Grid<T>& g, const cx<T>* b, cx<T>* x, cx<T>* alt, int sweeps, T w,
                                 int zero_first, cudaStream_t st);

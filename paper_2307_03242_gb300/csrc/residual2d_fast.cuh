@@ -121,6 +121,7 @@ HD void residual_cell(const Grid<T>& g, const cx<T>* __restrict__ b, const cx<T>
 template <typename T>
 __global__ void __launch_bounds__(BX * BY, 4) residual_fast(Grid<T> g, const cx<T>* __restrict__ b,
                                                         const cx<T>* __restrict__ x, cx<T>* __restrict__ r) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
@@ -158,6 +159,7 @@ HD void restrict_r_cell(const cx<T>* __restrict__ r, cx<T>* __restrict__ bc, int
 template <typename T>
 __global__ void __launch_bounds__(BX * BY) restrict_r(const cx<T>* __restrict__ r, cx<T>* __restrict__ bc, int nx, int ny,
                                                      int nxc, int nyc) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const int I = blockIdx.x * BX + threadIdx.x;
   const int J = blockIdx.y * BY + threadIdx.y;
   if (I >= nxc || J >= nyc) return;

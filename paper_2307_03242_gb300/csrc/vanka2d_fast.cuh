@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(BX * BY, sizeof(T) == 4 ? 2 : 1) vanka_fast(Gr
                                                                              const cx<T>* __restrict__ uin,
                                                                              cx<T>* __restrict__ uout, cx<T>* p, int colour,
                                                                              T w, int zero_in) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const int ip = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int i = 2 * ip + ((colour + j) & 1);

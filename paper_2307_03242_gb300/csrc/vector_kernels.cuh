@@ -40,6 +40,7 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NR], double* pa
 template <int NV>
 __global__ void __launch_bounds__(RT) mdot(const cx<double>* __restrict__ V, size_t ldv,
                                            const cx<double>* __restrict__ w, size_t n, double* part) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   double acc[2 * NV + 1];
 #pragma unroll
   for (int r = 0; r < 2 * NV + 1; ++r) acc[r] = 0.0;
@@ -61,6 +62,7 @@ struct Coefs { cx<double> c[64]; };
 // w -= sum_i h_i V_i (i < cnt); part[blk] = sum |w_new|^2.
 __global__ void __launch_bounds__(RT) update_norm(cx<double>* __restrict__ w, const cx<double>* __restrict__ V,
                                                   size_t ldv, int cnt, Coefs h, size_t n, double* part) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   double acc[1] = {0.0};
   for (size_t e = (size_t)blockIdx.x * RT + threadIdx.x; e < n; e += (size_t)gridDim.x * RT) {
     cx<double> we = w[e];
@@ -76,6 +78,7 @@ __global__ void __launch_bounds__(RT) update_norm(cx<double>* __restrict__ w, co
 constexpr int RP = 256;
 __global__ void __launch_bounds__(RP) reduce_parts(const double* __restrict__ part, int nblk, int nr,
                                                    double* __restrict__ out) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const int r = blockIdx.x;
   double s = 0.0;
   for (int b = threadIdx.x; b < nblk; b += RP) s += part[(size_t)b * nr + r];
@@ -91,6 +94,7 @@ __global__ void __launch_bounds__(RP) reduce_parts(const double* __restrict__ pa
 }
 
 __global__ void scale(cx<double>* __restrict__ dst, const cx<double>* __restrict__ src, double s, size_t n) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
     dst[e] = s * src[e];
 }
@@ -99,6 +103,7 @@ __global__ void scale(cx<double>* __restrict__ dst, const cx<double>* __restrict
 template <typename TZ>
 __global__ void combine(cx<double>* __restrict__ x, const cx<TZ>* __restrict__ Z, size_t ldz, int cnt, Coefs y,
                         size_t n) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     cx<double> a = x[e];
     for (int v = 0; v < cnt; ++v) a = a + y.c[v] * ccast<double>(Z[v * ldz + e]);
@@ -108,6 +113,7 @@ __global__ void combine(cx<double>* __restrict__ x, const cx<TZ>* __restrict__ Z
 
 template <typename TD, typename TS>
 __global__ void cast(cx<TD>* __restrict__ dst, const cx<TS>* __restrict__ src, size_t n) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
     dst[e] = ccast<TD>(src[e]);
 }
@@ -116,6 +122,7 @@ __global__ void cast(cx<TD>* __restrict__ dst, const cx<TS>* __restrict__ src, s
 template <typename T>
 __global__ void dense_gemv(const cx<T>* __restrict__ Ainv, const cx<T>* __restrict__ b, cx<T>* __restrict__ x,
                            int n) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;

@@ -18,6 +18,8 @@ COARSE_DENSE, COARSE_SMOOTH = 0, 1
 CYCLE_V, CYCLE_W, CYCLE_K = 0, 1, 2
 K_SMOOTH, K_RESTRICT, K_PROLONG, K_APPLY64, K_KRYLOV = range(5)
 VANKA_FULL, VANKA_ECONOMIC = 0, 1
+SWEEP_AUTO, SWEEP_HALF, SWEEP_COOP, SWEEP_TILE24, SWEEP_TILE8 = 0, 1, 2, 3, 4
+SWEEP_NAMES = {SWEEP_HALF: "half", SWEEP_COOP: "coop", SWEEP_TILE24: "tile24", SWEEP_TILE8: "tile8"}
 K_ALL = 5
 
 STATUS = {0: "EMG_OK", 1: "EMG_ERR_INVALID", 2: "EMG_ERR_NOMEM", 3: "EMG_ERR_CUDA", 4: "EMG_ERR_NONFINITE",
@@ -38,7 +40,8 @@ class _Params(ctypes.Structure):
                 ("damping", ctypes.c_double * MAX_LEVELS), ("coarse_solver", ctypes.c_int32),
                 ("coarse_sweeps", ctypes.c_int32), ("coarse_damping", ctypes.c_double),
                 ("cycle_precision", ctypes.c_int32), ("cycle_type", ctypes.c_int32),
-                ("level_alpha", ctypes.c_double * MAX_LEVELS), ("smoother", ctypes.c_int32)]
+                ("level_alpha", ctypes.c_double * MAX_LEVELS), ("smoother", ctypes.c_int32),
+                ("sweep_path", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -60,6 +63,7 @@ def _load():
         "emg_solve": [vp, vp, vp, dbl, i32, i32, ctypes.POINTER(_Stats)],
         "emg_solve_host": [vp, vp, vp, dbl, i32, i32, ctypes.POINTER(_Stats)],
         "emg_level_info": [vp, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(dbl)],
+        "emg_sweep_path": [vp, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(dbl)],
         "emg_smooth": [vp, i32, vp, vp, i32],
         "emg_residual_restrict": [vp, i32, vp, vp, vp],
         "emg_prolong_correct": [vp, i32, vp, vp],
@@ -86,7 +90,7 @@ LIB = _load()
 EXPORTED = ["emg_create", "emg_destroy", "emg_last_error", "emg_apply", "emg_vcycle", "emg_solve", "emg_solve_host",
             "emg_level_info", "emg_smooth", "emg_residual_restrict", "emg_prolong_correct", "emg_coarse_solve",
             "emg_profile", "emg_profile_read", "emg_smooth_noalloc", "emg_solve_batch", "emg_apply_adjoint",
-            "emg_solve_adjoint", "emg_material_gradient"]
+            "emg_solve_adjoint", "emg_material_gradient", "emg_sweep_path"]
 NOALLOC_MAX_CELLS = 262144
 
 
@@ -117,6 +121,7 @@ class Params:
     cycle_type: int = CYCLE_V
     level_alpha: object = None       # per-level shift list (entries <= 0 mean `alpha`)
     smoother: int = 0                # VANKA_FULL or VANKA_ECONOMIC
+    sweep_path: int = 0              # SWEEP_AUTO (timed per level at creation) or a forced SWEEP_* path
 
     def to_c(self) -> _Params:
         p = _Params()
@@ -136,6 +141,7 @@ class Params:
         for l in range(MAX_LEVELS):
             p.level_alpha[l] = float(la[l]) if l < len(la) else 0.0
         p.smoother = int(self.smoother)
+        p.sweep_path = int(self.sweep_path)
         return p
 
 
@@ -257,6 +263,14 @@ class Solver:
         hh = ctypes.c_double()
         _check(LIB.emg_level_info(self.h, level, n, ctypes.byref(hh)))
         return tuple(n), hh.value
+
+    def sweep_path(self, level):
+        """(path, us): the sweep path of a level (SWEEP_*) and, if the autotuner chose it, the
+        measured time of one smoothing call in microseconds (else 0)."""
+        path = ctypes.c_int32()
+        us = ctypes.c_double()
+        _check(LIB.emg_sweep_path(self.h, level, ctypes.byref(path), ctypes.byref(us)))
+        return path.value, us.value
 
     def _n(self, level=0):
         return int(np.prod(self.vec_shape(level)))

@@ -214,3 +214,115 @@ def test_host_3d_float_float_adjoint_apply_matches_the_oracle(hc, n, abl):
                                        _cvec(y)) == 0
     act = oracle.active_mask(pb)
     assert np.abs((y - ref) * act).max() <= 1e-12 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------- one-pass tiled sweep, host build
+TILED = {"72x40": ((72, 40), 3, 5), "200x64": ((200, 64), 2, 5), "124x36_layer": ((124, 36), 2, 12)}
+
+
+@pytest.mark.parametrize("ty", [24, 8])
+@pytest.mark.parametrize("case", list(TILED))
+@pytest.mark.parametrize("level", [0, 1])
+@pytest.mark.parametrize("sweeps,zero_first", [(1, 0), (2, 1)])
+def test_host_tiled_sweep_matches_the_oracle(hc, case, level, sweeps, zero_first, ty):
+    """The one-pass tiled sweep (csrc/sweep2d_tile.cuh): tile decomposition, shared-region
+    boundary handling, both colour phases and the lane mapping, against the oracle's red-black
+    sweep in FP32. The 200 x 64 grid has tiles away from the boundary and the absorbing layer
+    (the interior, attenuation-free variant); shared entries the kernel would read unwritten are
+    NaN in the host build."""
+    n, levels, abl = TILED[case]
+    w = small_heterogeneous(n, seed=3, levels=levels, abl_cells=abl, sigma_cells=2.0)
+    pb = oracle_problem(w)
+    hier = oracle_hierarchy(w, pb)
+    pl = hier.pbs[level]
+    if pl.n[0] % 4:
+        pytest.skip("the tiled kernel needs n_x divisible by 4")
+    b, x = random_field(pl, 41), random_field(pl, 42)
+    if zero_first:
+        x = np.zeros_like(x)
+    ref = x.ravel()
+    for _ in range(sweeps):
+        ref = red_black_sweep(hier.H[level], hier.V[level], hier.idx[level], hier.colour[level], b.ravel(), ref,
+                              hier.w[level])
+    got = np.ascontiguousarray(x.ravel()).copy()
+    if zero_first:
+        got[:] = np.nan  # a zero initial guess must not be read
+    head, keep = _level_args(pb, hier, level, 32)
+    bb = np.ascontiguousarray(b.ravel())
+    interior = hc.emg_hc_sweep_tiled(*head[1:], _cvec(bb), _cvec(got), ctypes.c_double(hier.w[level]), sweeps,
+                                     zero_first, ty)
+    assert interior >= 0
+    if case == "200x64" and level == 0:
+        assert interior >= 2
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("ty", [24, 8])
+@pytest.mark.parametrize("case", ["72x40", "200x64"])
+@pytest.mark.parametrize("sweeps", [1, 2])
+def test_host_tiled_sweep_with_prolongation_matches_the_oracle(hc, case, sweeps, ty):
+    """The first post-sweep with the prolongation + correction fused into its tile loads:
+    x + P e, then the sweeps, against the oracle's P and red-black sweep in FP32."""
+    n, levels, abl = TILED[case]
+    w = small_heterogeneous(n, seed=5, levels=levels, abl_cells=abl, sigma_cells=2.0)
+    pb = oracle_problem(w)
+    hier = oracle_hierarchy(w, pb)
+    pl, pc = hier.pbs[0], hier.pbs[1]
+    b, x, e = random_field(pl, 51), random_field(pl, 52), random_field(pc, 53)
+    ref = x.ravel() + hier.P[0] @ e.ravel()
+    for _ in range(sweeps):
+        ref = red_black_sweep(hier.H[0], hier.V[0], hier.idx[0], hier.colour[0], b.ravel(), ref, hier.w[0])
+    got = np.ascontiguousarray(x.ravel()).copy()
+    head, keep = _level_args(pb, hier, 0, 32)
+    bb, ee = np.ascontiguousarray(b.ravel()), np.ascontiguousarray(e.ravel())
+    assert hc.emg_hc_prolong_sweep_tiled(*head[1:], _cvec(bb), _cvec(ee), _cvec(got), ctypes.c_double(hier.w[0]),
+                                         sweeps, ty) == 0
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_float_float_split_and_join_are_exact_to_46_bits(hc):
+    """df::split (integer and FP32 operations only) gives hi = x truncated to 24 significant bits
+    and hi + lo within 2^-46 |x|; df::join / widen reassemble doubles exactly; non-finite values
+    stay non-finite."""
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(20000) * 10.0 ** rng.uniform(-30, 30, 20000)
+    x = np.concatenate([x, [0.0, -0.0, 1.0, -2.0, 2.0 ** -100, 3.0 * 2.0 ** 80, 1e-35, np.inf, -np.inf, np.nan]])
+    n = x.size
+    hi, lo = np.zeros(n, np.float32), np.zeros(n, np.float32)
+    joined, widened = np.zeros(n), np.zeros(n)
+    fp = ctypes.POINTER(ctypes.c_float)
+    assert hc.emg_hc_split_join(x.ctypes.data_as(DP), n, hi.ctypes.data_as(fp), lo.ctypes.data_as(fp),
+                                joined.ctypes.data_as(DP), widened.ctypes.data_as(DP)) == 0
+    fin = np.isfinite(x) & (np.abs(x) > 1e-30)
+    h64, l64 = hi.astype(np.float64), lo.astype(np.float64)
+    assert np.all(np.abs(h64[fin]) <= np.abs(x[fin]))                                   # truncation
+    assert np.all(np.abs(x[fin] - h64[fin]) < np.spacing(np.abs(hi[fin])).astype(np.float64))
+    assert np.all(np.abs((h64 + l64 - x)[fin]) <= 2.0 ** -46 * np.abs(x[fin]))
+    assert np.array_equal(joined[fin], (h64 + l64)[fin])
+    assert np.array_equal(widened[np.isfinite(x)], h64[np.isfinite(x)])
+    assert np.isnan(hi[-1]) and np.isinf(hi[-2]) and np.isinf(hi[-3]) and hi[-3] > 0 > hi[-2]
+    assert hi[-10] == 0 and lo[-10] == 0
+
+
+@pytest.mark.parametrize("ty", [24, 8])
+@pytest.mark.parametrize("case", list(TILED))
+@pytest.mark.parametrize("level", [0, 1])
+def test_host_tiled_residual_restriction_matches_the_oracle(hc, case, level, ty):
+    """The one-pass residual + restriction (csrc/residual2d_tile.cuh): the fine residual's
+    displacement rows in shared memory, restricted there, the pressure rows formed on the fly,
+    against the oracle's R (b - H_s x) in FP32; shared entries it would read unwritten are NaN."""
+    n, levels, abl = TILED[case]
+    w = small_heterogeneous(n, seed=6, levels=levels, abl_cells=abl, sigma_cells=2.0)
+    pb = oracle_problem(w)
+    hier = oracle_hierarchy(w, pb)
+    pl = hier.pbs[level]
+    if pl.n[0] % 4 or level + 1 >= levels:
+        pytest.skip("needs n_x divisible by 4 and a coarser level")
+    b, x = random_field(pl, 61), random_field(pl, 62)
+    ref = hier.R[level] @ (b.ravel() - hier.H[level] @ x.ravel())
+    bc = np.zeros(ref.size, dtype=np.complex128)
+    head, keep = _level_args(pb, hier, level, 32)
+    bb, xx = np.ascontiguousarray(b.ravel()), np.ascontiguousarray(x.ravel())
+    assert hc.emg_hc_resid_restrict_tiled(*head[1:], _cvec(bb), _cvec(xx), _cvec(bc), ty) == 0
+    assert np.all(np.isfinite(bc))
+    assert np.abs(bc - ref).max() <= 2e-5 * np.abs(ref).max()

@@ -19,13 +19,18 @@ Modules
   krylov          -- right-preconditioned restarted flexible GMRES (Saad 1993), modified Gram-Schmidt
   twogrid         -- Section 4.3 convergence factor in practice (Eq. convFactor) of the two-grid cycle
   lexvanka.c      -- the lexicographic (Gauss-Seidel over cells) Vanka sweep, compiled with gcc
+  kaczmarz        -- Sections 3.2 / 5.3 coarsest solve: Schur complement eliminating p, FGMRES(5)
+                     preconditioned by parallel hybrid (component-averaged) Kaczmarz steps
+                     (the step itself in kaczmarz.c, compiled with gcc)
   adjoint         -- misfit gradient wrt lambda, mu, rho by the adjoint-state method (direct solves)
 
 Parity status: every function is pinned by tests/test_oracle_*.py against the
 paper's printed stencils, closed-form Fourier symbols, the two-grid symbol of
 Eq. symbolTG, dense direct solves, plane-wave solutions and Table 1's two-grid
 convergence factors (economic Vanka in lexicographic order); the adjoint
-gradient by central finite differences of the misfit. The full Vanka smoother
+gradient by central finite differences of the misfit; the Kaczmarz coarsest solve by the full
+system's direct solve, the row-projection property, the Bjorck-Elfving SOR identity, hand
+averages, the solution as fixed point and monotone error decrease. The full Vanka smoother
 has no printed symbol or factor in the paper; it is pinned by the single-cell
 exactness property and by the converged solves only.
 """

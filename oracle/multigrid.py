@@ -10,9 +10,9 @@ post-relaxations. The coarse operators are re-discretisations of the shifted
 operator (Remark 2.1 and Section 3.2: the same stencil on the 2h grid, with the
 same omega, beta and shift alpha added to the attenuation). The coarsest level
 is solved either exactly (dense or sparse LU of the coarsest operator, the paper's 2D
-choice in Section 3.2) or inexactly by a fixed number of red-black Vanka sweeps
-from a zero guess (reading: a GPU-friendly stand-in for the paper's inexact
-hybrid-Kaczmarz coarsest solve of Section 5.3).
+choice in Section 3.2), by the paper's 3D choice (Sections 3.2 and 5.3: FGMRES(5) on the
+p-eliminated Schur complement, preconditioned by parallel hybrid Kaczmarz steps, to a 0.1 drop;
+oracle/kaczmarz.py), or inexactly by a fixed number of red-black Vanka sweeps from a zero guess.
 """
 from __future__ import annotations
 
@@ -32,7 +32,9 @@ DEFAULT_DAMPING = {1: 0.55, 2: 0.55, 3: 0.35, 4: 0.25, 5: 0.2, 6: 0.2, 7: 0.2, 8
 class Hierarchy:
     def __init__(self, pb: Problem, levels: int, alpha: float, damping=None, nu_pre: int = 2,
                  nu_post: int = 2, coarse: str = "dense", coarse_sweeps: int = 0,
-                 coarse_damping: float = 1.0, cycle: str = "V", smoother: str = "full"):
+                 coarse_damping: float = 1.0, cycle: str = "V", smoother: str = "full",
+                 coarse_box=4, coarse_coloured: bool = False, coarse_tol: float = 0.1,
+                 coarse_steps: int = 10, coarse_kaczmarz_damping: float = 0.8, coarse_max_kaczmarz: int = 250):
         self.levels = levels
         self.cycle = cycle
         self.gamma_cycle = {"V": 1, "W": 2, "K": 2}[cycle]
@@ -63,6 +65,12 @@ class Hierarchy:
             # the same exact coarsest solve as "dense" (Sec. 3.2: LU in 2D), with a sparse LU for
             # coarsest grids whose dense matrix would not fit in memory
             self.splu = spla.splu(self.H[last][self.act_c][:, self.act_c].tocsc())
+        elif coarse == "kaczmarz":
+            from .kaczmarz import SchurSystem, box_partition
+            self.schur = SchurSystem(self.pbs[last], self.alphas[last])
+            self.kpart = box_partition(self.schur, coarse_box, coloured=coarse_coloured)
+            self.kopts = dict(tol=coarse_tol, kaczmarz_steps_per_apply=coarse_steps,
+                              damping=coarse_kaczmarz_damping, max_kaczmarz=coarse_max_kaczmarz)
 
     def smooth(self, l, b, x, count, w):
         for _ in range(count):
@@ -76,6 +84,9 @@ class Hierarchy:
             x[self.act_c] = sla.lu_solve(self.lu, b[self.act_c])
         elif self.coarse == "sparse":
             x[self.act_c] = self.splu.solve(np.ascontiguousarray(b[self.act_c]))
+        elif self.coarse == "kaczmarz":
+            from .kaczmarz import hybrid_solve
+            x, _, _ = hybrid_solve(self.schur, self.kpart, b, **self.kopts)
         else:
             x = self.smooth(last, b, x, self.coarse_sweeps, self.coarse_damping)
         return x

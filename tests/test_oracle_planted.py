@@ -221,3 +221,50 @@ def test_planted_coarsest_solved_twice_breaks_the_once_per_visit_pin(monkeypatch
         return orig(hier, b, x, level)
     monkeypatch.setattr(mg, "vcycle", wrong)
     _fails(tw.test_wcycle_solves_an_inexact_coarsest_level_once_per_visit)
+
+
+# ---------------------------------------------------------------- hybrid Kaczmarz coarsest solve
+import oracle.kaczmarz as kz
+import test_oracle_kaczmarz as tk
+
+
+def _planted_step(monkeypatch, tmp_path, old, new):
+    """Builds oracle/kaczmarz.c with `old` replaced by `new` and makes it the step in use."""
+    import os
+    src = open(os.path.join(os.path.dirname(kz.__file__), "kaczmarz.c")).read()
+    assert src.count(old) >= 1
+    path = tmp_path / "planted.c"
+    path.write_text(src.replace(old, new))
+    monkeypatch.setattr(kz, "_STEP", kz.load_step(str(tmp_path / "planted.so"), str(path)))
+
+
+def test_planted_missing_conjugate_breaks_the_projection_pin(monkeypatch, tmp_path):
+    _planted_step(monkeypatch, tmp_path, "ai = -v[2 * q + 1]", "ai = v[2 * q + 1]")
+    _fails(tk.test_projection_property_on_the_schur_rows, (10, 8))
+
+
+def test_planted_average_over_all_subregions_breaks_the_fixed_point_pin(monkeypatch, tmp_path):
+    _planted_step(monkeypatch, tmp_path, "acc[2 * j] / cnt[j]", "acc[2 * j] / nparts")
+    _fails(tk.test_exact_solution_is_a_fixed_point, (10, 8), 2)
+
+
+def test_planted_undamped_update_breaks_bjorck_elfving(monkeypatch, tmp_path):
+    _planted_step(monkeypatch, tmp_path, "sr = w * rr / nn, si = w * ri / nn", "sr = rr / nn, si = ri / nn")
+    _fails(tk.test_bjorck_elfving_sor_identity, 0.8)
+
+
+def test_planted_shared_copy_across_subregions_breaks_the_hand_average(monkeypatch, tmp_path):
+    # sub-regions start from the previous sub-region's copy instead of the common iterate
+    _planted_step(monkeypatch, tmp_path, "work[2 * j] = x[2 * j];\n      work[2 * j + 1] = x[2 * j + 1];",
+                  "if (p == 0) { work[2 * j] = x[2 * j];\n      work[2 * j + 1] = x[2 * j + 1]; }")
+    _fails(tk.test_hand_examples_of_projection_and_component_average)
+
+
+def test_planted_schur_sign_breaks_the_direct_solve_pin(monkeypatch):
+    monkeypatch.setattr(kz, "_eliminate", lambda Huu, A_up, cinv, A_pu: (Huu + A_up @ sp.diags(cinv) @ A_pu).tocsr())
+    _fails(tk.test_schur_reduction_reproduces_the_direct_solve, (10, 8))
+
+
+def test_planted_narrow_reach_breaks_the_footprint_pin(monkeypatch):
+    monkeypatch.setattr(kz, "reach_offsets", lambda d, c: ((1,) * d, (1,) * d))
+    _fails(tk.test_reach_is_the_schur_stencil_footprint, (10, 8))

@@ -345,6 +345,13 @@ def bench_single(args, w, steps, warmup, fp64_steps, cpu_baseline, e2e_steps=Non
                                                                ("apply64", emg.K_APPLY64), ("krylov", emg.K_KRYLOV))}
     s32.profile(False)
     launches = s32.profile_read(emg.K_ALL)["launches"]
+    # one more solve, untimed, with every level's kernels timed: the coarser levels' share
+    s32.profile(True, coarse=True)
+    solve(s32)
+    coarse_ms = s32.profile_read(emg.K_COARSE)["ms"]
+    for cls in (emg.K_SMOOTH, emg.K_RESTRICT, emg.K_PROLONG, emg.K_APPLY64, emg.K_KRYLOV, emg.K_ALL):
+        s32.profile_read(cls)
+    s32.profile(False)
     t32 = max_over_ranks(ms / 1e3, device=dev)
     res32 = st["rel_residual"]
 
@@ -417,6 +424,7 @@ def bench_single(args, w, steps, warmup, fp64_steps, cpu_baseline, e2e_steps=Non
                         "fp32": fp32_fraction(prof)},
            "fine_level_ms_per_solve": dict({"smooth": prof["ms"] / steps},
                                            **{k: v["ms"] / steps for k, v in breakdown.items()}),
+           "coarse_levels_ms_per_solve": coarse_ms,
            "e2e": {"value": te2e, "unit": "s", "h2d_bytes_per_step": 2 * nvec * 16, "d2h_bytes_per_step": nvec * 16},
            "gpu_launches": int(launches)}
     out["sweep_paths"] = [emg.SWEEP_NAMES[p] for p in paths]

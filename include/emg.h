@@ -54,7 +54,12 @@ typedef enum {
   EMG_ERR_TIMEOUT = 6     /* reserved for bounded device-side waits */
 } emg_status;
 
-enum { EMG_COARSE_DENSE = 0, EMG_COARSE_SMOOTH = 1 };
+/* Coarsest-level solvers (Sec. 3.2): EMG_COARSE_DENSE, the exact solve (the paper's 2D choice);
+ * EMG_COARSE_SMOOTH, coarse_sweeps red-black Vanka sweeps from zero; EMG_COARSE_KACZMARZ, the
+ * paper's 3D choice (Sec. 3.2, 5.3): FGMRES on the Schur complement that eliminates p (the p-p
+ * block is diagonal), preconditioned by parallel hybrid Kaczmarz steps, until a relative drop of
+ * the Schur residual (the kaczmarz_* and coarse_* fields of emg_params). */
+enum { EMG_COARSE_DENSE = 0, EMG_COARSE_SMOOTH = 1, EMG_COARSE_KACZMARZ = 2 };
 enum { EMG_CYCLE_V = 0, EMG_CYCLE_W = 1, EMG_CYCLE_K = 2 };
 enum { EMG_VANKA_FULL = 0, EMG_VANKA_ECONOMIC = 1 };
 /* How a level's red-black sweeps run (emg_params.sweep_path). EMG_SWEEP_AUTO: chosen per level at
@@ -98,6 +103,22 @@ typedef struct {
                                by its diagonal (the paper's LFA variant, Sec. 2.3), in red-black
                                order here */
   int32_t sweep_path;       /* EMG_SWEEP_*: how the sweeps of 2D FP32 levels run (0: autotuned) */
+  /* EMG_COARSE_KACZMARZ (Sec. 3.2, 5.3). The Schur system S u = f is solved by FGMRES(coarse_restart)
+   * from zero, each preconditioner application being kaczmarz_steps parallel hybrid Kaczmarz steps
+   * from zero with damping kaczmarz_damping: the coarsest cells are divided into boxes of
+   * kaczmarz_box cells per axis; every box sweeps its faces' rows (component by component, x
+   * fastest) with damped row projections on a private copy of the unknowns its rows reach (the box
+   * dilated by 2 cells below, 1 along the component's own axis, and 1 cell above), all boxes from
+   * the same iterate, and each unknown becomes the mean of the boxes' copies of it. The solve stops
+   * when ||f - S u|| <= coarse_tol ||f|| or after kaczmarz_max / kaczmarz_steps FGMRES iterations.
+   * Zero selects the paper's value: restart 5, 10 steps, damping 0.8, drop 0.1, at most 250 steps;
+   * boxes of 2 cells. coarse_restart <= 8; kaczmarz_damping in (0, 2). */
+  int32_t kaczmarz_box[3];
+  int32_t kaczmarz_steps;
+  double kaczmarz_damping;
+  double coarse_tol;
+  int32_t coarse_restart;
+  int32_t kaczmarz_max;
 } emg_params;
 
 typedef struct {
@@ -116,7 +137,8 @@ typedef struct {
  * cuda_stream: a cudaStream_t, or NULL for the legacy default stream.
  * Rejects: dim not 2/3; n not divisible by 2^(levels-1); a coarsest grid below 2 cells per
  * axis; non-finite or non-positive mu, rho, lam+mu; EMG_COARSE_DENSE with more than 4096
- * coarsest unknowns. On success *out is a new handle. */
+ * coarsest unknowns; EMG_COARSE_KACZMARZ settings out of range (a box's private copy must fit in
+ * 200 KB of shared memory). On success *out is a new handle. */
 emg_status emg_create(const emg_params* params, const double* lam, const double* mu,
                       const double* rho, int on_device, void* cuda_stream, emg_handle* out);
 
@@ -209,18 +231,32 @@ emg_status emg_residual_restrict(emg_handle h, int level, const void* b, const v
 /* x <- x + P e_coarse from level+1 to `level` (Eq. 2.11-2.13, Alg. 1 step 4). */
 emg_status emg_prolong_correct(emg_handle h, int level, const void* e_coarse, void* x);
 
-/* x <- coarsest-level solve of H_s x = b (exact for EMG_COARSE_DENSE, else coarse_sweeps
- * red-black sweeps from zero). b, x: cycle vectors of the coarsest level. */
+/* x <- coarsest-level solve of H_s x = b (exact for EMG_COARSE_DENSE, coarse_sweeps red-black
+ * sweeps from zero for EMG_COARSE_SMOOTH, the hybrid Kaczmarz-GMRES solve for
+ * EMG_COARSE_KACZMARZ). b, x: cycle vectors of the coarsest level. */
 emg_status emg_coarse_solve(emg_handle h, const void* b, void* x);
+
+/* EMG_COARSE_KACZMARZ diagnostics (Sec. 3.2, 5.3). emg_coarse_stats synchronises the handle's
+ * stream and writes, for the last coarsest solve: out[0] FGMRES iterations, out[1] the relative
+ * Schur residual ||f - S u|| / ||f|| at exit, out[2] Kaczmarz steps spent. emg_coarse_schur_rows
+ * copies the stored Schur rows to the caller's host buffer: dim N_c rows (component-major, x
+ * fastest; N_c coarsest cells), each of 75 (3D) or 17 (2D) complex entries in the cycle precision,
+ * over the row's footprint: for c2 = 0 .. dim-1, offsets o along each axis a from -2 (a = c != c2),
+ * 0 (a = c2 != c) or -1 (otherwise) to +1, x fastest; entries outside the grid or on boundary
+ * faces are 0, and rows of boundary faces are all 0. EMG_ERR_INVALID for other coarse solvers. */
+emg_status emg_coarse_stats(emg_handle h, double out[3]);
+emg_status emg_coarse_schur_rows(emg_handle h, void* rows_host);
 
 /* ---- Instrumentation. ----
  * While enabled, the library records a CUDA event pair on its stream around every launch of
- * the listed kernel classes on the finest level. emg_profile_read synchronises the stream and
+ * the listed kernel classes on the finest level (enable = 1), and with enable = 2 also around
+ * every launch on the coarser levels, which count as EMG_K_COARSE. emg_profile_read synchronises the stream and
  * returns the summed event time, the launch count and the algorithmic bytes of those launches,
  * then resets the counters. kernel_class is one of EMG_K_* (EMG_K_ALL: launch count only). */
 enum { EMG_K_SMOOTH = 0, EMG_K_RESTRICT = 1, EMG_K_PROLONG = 2, EMG_K_APPLY64 = 3,
-       EMG_K_KRYLOV = 4, EMG_K_COUNT = 5,
-       EMG_K_ALL = 5 /* emg_profile_read(EMG_K_ALL): launches = every kernel launched by the handle
+       EMG_K_KRYLOV = 4, EMG_K_COARSE = 5 /* every kernel of the levels below the finest (enable = 2) */,
+       EMG_K_COUNT = 6,
+       EMG_K_ALL = 6 /* emg_profile_read(EMG_K_ALL): launches = every kernel launched by the handle
                         on any level since the last read (counted even when profiling is off) */ };
 emg_status emg_profile(emg_handle h, int enable);
 emg_status emg_profile_read(emg_handle h, int kernel_class, double* total_ms, int64_t* launches,

@@ -14,7 +14,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libemg.so")
 # host build of the per-cell adjoint functions, for CPU checks against the oracle (tests only)
 HOSTCHECK = os.path.join(PKG, "libemg_hostcheck.so")
-SOURCES = ["emg.cu", "launch2d.cu", "launch3d.cu", "noalloc.cu", "adjoint.cu"]
+SOURCES = ["emg.cu", "launch2d.cu", "launch3d.cu", "noalloc.cu", "adjoint.cu", "kaczmarz.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
          "--diag-suppress=177"]

@@ -139,4 +139,15 @@ HD void cell_rows_adjoint(const FineFF3& g, const cx<TI>* x, const cx<double>* b
   }
 }
 
+template <typename TI>
+__global__ void __launch_bounds__(BX * BY * BZ) apply_adjoint(FineFF3 g, const cx<TI>* __restrict__ x,
+                                                             const cx<double>* __restrict__ b, double bscale,
+                                                             cx<double>* __restrict__ y) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int k = blockIdx.z * BZ + threadIdx.z;
+  if (i >= g.nx || j >= g.ny || k >= g.nz) return;
+  cell_rows_adjoint(g, x, b, bscale, y, i, j, k);
+}
+
 }  // namespace ff3

@@ -78,14 +78,12 @@ struct cacc {
   }
 };
 
+// y at cell (i, j): the u1 row at face i, the u2 row at face j and the continuity row, each as
+// H x (b == nullptr) or bscale * b - H x; rows of faces that are not unknowns are 0.
 template <typename TI>
-__global__ void __launch_bounds__(BX * BY) apply(FineFF g, const cx<TI>* __restrict__ x, const cx<double>* __restrict__ b,
-                                                double bscale, cx<double>* __restrict__ y) {
-  grid_dependency_wait();  // launched with programmatic stream serialisation
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
+HD void apply_cell(const FineFF& g, const cx<TI>* __restrict__ x, const cx<double>* __restrict__ b, double bscale, int i,
+                   int j, cx<double> out3[3]) {
   const int nx = g.nx, ny = g.ny;
-  if (i >= nx || j >= ny) return;
   const size_t N = (size_t)nx * ny, k = (size_t)j * nx + i;
   const cx<TI>* u1 = x;
   const cx<TI>* u2 = x + N;
@@ -205,10 +203,25 @@ __global__ void __launch_bounds__(BX * BY) apply(FineFF g, const cx<TI>* __restr
     y2 = j >= 1 ? bscale * b[N + k] - y2 : czero<double>();
     yp = bscale * b[2 * N + k] - yp;
   }
-  y[k] = y1;
-  y[N + k] = y2;
-  y[2 * N + k] = yp;
+  out3[0] = y1;
+  out3[1] = y2;
+  out3[2] = yp;
   (void)z;
+}
+
+template <typename TI>
+__global__ void __launch_bounds__(BX * BY) apply(FineFF g, const cx<TI>* __restrict__ x, const cx<double>* __restrict__ b,
+                                                double bscale, cx<double>* __restrict__ y) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  const size_t N = (size_t)g.nx * g.ny, k = (size_t)j * g.nx + i;
+  cx<double> out[3];
+  apply_cell<TI>(g, x, b, bscale, i, j, out);
+  y[k] = out[0];
+  y[N + k] = out[1];
+  y[2 * N + k] = out[2];
 }
 
 }  // namespace ff2

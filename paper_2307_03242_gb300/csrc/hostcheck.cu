@@ -12,12 +12,19 @@
 #include "adjoint.cuh"
 #include "adjoint_ff3.cuh"
 #include "dfloat.cuh"
+#include "ff2_setup.h"
 #include "ff3_setup.h"
 #include "residual2d_fast.cuh"
 #include "residual3d.cuh"
 #include "sweep2d_tile.cuh"
 #include "residual2d_tile.cuh"
 #include "vanka2d_fast.cuh"
+#include "kaczmarz.cuh"
+#include "emg.h"
+
+#include <algorithm>
+#include <array>
+#include <cstddef>
 
 namespace {
 
@@ -335,7 +342,204 @@ void resid_restrict_tiled(const Grid<float>& g, const cx<float>* b, const cx<flo
 
 }  // namespace
 
+namespace {
+
+// H_s x of one level on the host, row by row as the level's apply kernels evaluate it.
+template <int D>
+void level_apply(const Grid<double>& g, const cx<double>* x, cx<double>* y) {
+  const size_t N = (size_t)g.nx * g.ny * g.nz;
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        const size_t q = kz::cell_of(std::array<int, 3>{g.nx, g.ny, g.nz}.data(), D, i, j, k);
+        if (D == 3) {
+          const cx<double>* u[3] = {x, x + N, x + 2 * N};
+          const int idx[3] = {i, j, k};
+          for (int c = 0; c < 3; ++c)
+            y[c * N + q] = idx[c] >= 1 ? s3::row_u<double, double>(c, u[c], x + 3 * N, g, i, j, k) : czero<double>();
+          y[3 * N + q] = s3::row_p<double, double>(u, x + 3 * N, g, i, j, k);
+        } else {
+          y[q] = i >= 1 ? s2::row_u1<double, double>(x, x + 2 * N, g, i, j) : czero<double>();
+          y[N + q] = j >= 1 ? s2::row_u2<double, double>(x + N, x + 2 * N, g, i, j) : czero<double>();
+          y[2 * N + q] = s2::row_p<double, double>(x, x + N, x + 2 * N, g, i, j);
+        }
+      }
+}
+
+// The Kaczmarz solve's set-up on the host: the Schur rows by probing the level operator.
+template <int D>
+void kz_probe_host(const Grid<double>& g, cx<double>* coef) {
+  const int n[3] = {g.nx, g.ny, g.nz};
+  const size_t N = (size_t)n[0] * n[1] * n[2];
+  std::fill(coef, coef + (size_t)D * N * kz::Shape<D>::NE, czero<double>());
+  std::vector<cx<double>> e((D + 1) * N), y((D + 1) * N);
+  for (int c2 = 0; c2 < D; ++c2)
+    for (int q2 = 0; q2 < (D == 3 ? kz::PER : 1); ++q2)
+      for (int q1 = 0; q1 < kz::PER; ++q1)
+        for (int q0 = 0; q0 < kz::PER; ++q0) {
+          const int q[3] = {q0, q1, q2};
+          for (size_t t = 0; t < e.size(); ++t) e[t] = kz::probe_value<double, D>(c2, q, n, t);
+          level_apply<D>(g, e.data(), y.data());
+          for (size_t r = 0; r < (size_t)D * N; ++r) kz::probe_take_row<double, D>(g, y.data(), c2, q, r, coef);
+        }
+}
+
+// `steps` Kaczmarz steps (sweep of every box, then the component average) with the kernel's
+// index tables and loop order, lanes taken one after another. Returns the number of region
+// indices that fell outside a box's region or did not map back to the entry's unknown (0).
+template <int D>
+long kz_steps_host(const kz::Boxes& B, const cx<double>* coef, const cx<double>* rhs, cx<double>* x, int steps,
+                   double w) {
+  constexpr int NE = kz::Shape<D>::NE, SL = kz::Shape<D>::SL;
+  const size_t N = (size_t)B.n[0] * B.n[1] * B.n[2];
+  std::vector<kz::LaneTab<D>> tab(32);
+  for (int lane = 0; lane < 32; ++lane) tab[lane].init(B, lane);
+  std::vector<double> in2((size_t)D * N);
+  for (size_t r = 0; r < in2.size(); ++r) in2[r] = kz::inv_row_norm<double, D>(coef, r);
+  std::vector<cx<double>> copies((size_t)B.nboxes * B.RS), reg(B.RS);
+  long bad = 0;
+  for (int s = 0; s < steps; ++s) {
+    for (int bx = 0; bx < B.nboxes; ++bx) {
+      int lo[3];
+      kz::box_lo(B, bx, lo);
+      for (int t = 0; t < B.RS; ++t) {
+        int m[3];
+        const int c2 = kz::region_cell(B, t, lo, m);
+        bool in = true;
+        for (int a = 0; a < D; ++a) in = in && m[a] >= 0 && m[a] < B.n[a];
+        reg[t] = (in && m[c2] >= 1) ? x[(size_t)c2 * N + kz::cell_of(B.n, D, m[0], m[1], m[2])] : czero<double>();
+      }
+      for (int c = 0; c < D; ++c)
+        for (int lz = 0; lz < B.box[2]; ++lz)
+          for (int ly = 0; ly < B.box[1]; ++ly)
+            for (int lx = 0; lx < B.box[0]; ++lx) {
+              const int k[3] = {lo[0] + lx, lo[1] + ly, lo[2] + lz};
+              if (k[0] >= B.n[0] || k[1] >= B.n[1] || k[2] >= B.n[2] || k[c] < 1) continue;
+              const size_t r = (size_t)c * N + kz::cell_of(B.n, D, k[0], k[1], k[2]);
+              if (in2[r] == 0.0) continue;
+              cx<double> dot = czero<double>();
+              std::vector<int> idx(32 * SL, -1);
+              for (int lane = 0; lane < 32; ++lane)
+                for (int t = 0; t < SL; ++t) {
+                  const int pk = tab[lane].get(c, t);
+                  if (pk < 0) continue;
+                  const int cc = kz::pk_c2(pk);
+                  const int id = kz::pk_off(pk) + (lz * B.ry[cc] + ly) * B.rx[cc] + lx;
+                  int m[3];
+                  const bool ok = id >= 0 && id < B.RS && kz::region_cell(B, id, lo, m) == cc &&
+                                  m[0] == k[0] + kz::pk_o(pk, 0) && m[1] == k[1] + kz::pk_o(pk, 1) &&
+                                  m[2] == k[2] + kz::pk_o(pk, 2);
+                  if (!ok) {
+                    ++bad;
+                    continue;
+                  }
+                  idx[lane * SL + t] = id;
+                  dot = dot + coef[r * NE + lane + 32 * t] * reg[id];
+                }
+              const cx<double> sc = (w * in2[r]) * (rhs[r] - dot);
+              for (int lane = 0; lane < 32; ++lane)
+                for (int t = 0; t < SL; ++t) {
+                  const int id = idx[lane * SL + t];
+                  if (id >= 0) reg[id] = reg[id] + sc * cconj(coef[r * NE + lane + 32 * t]);
+                }
+            }
+      std::copy(reg.begin(), reg.end(), copies.begin() + (size_t)bx * B.RS);
+    }
+    for (size_t q = 0; q < (size_t)D * N; ++q) {
+      const int c2 = (int)(q / N);
+      const size_t cell = q % N;
+      const int m[3] = {(int)(cell % B.n[0]), (int)((cell / B.n[0]) % B.n[1]), (int)(cell / ((size_t)B.n[0] * B.n[1]))};
+      if (m[c2] < 1) {
+        x[q] = czero<double>();
+        continue;
+      }
+      int blo[3], bhi[3];
+      kz::reach_boxes(B, c2, m, blo, bhi);
+      cx<double> acc = czero<double>();
+      int cnt = 0;
+      for (int bz = blo[2]; bz <= bhi[2]; ++bz)
+        for (int by = blo[1]; by <= bhi[1]; ++by)
+          for (int bxx = blo[0]; bxx <= bhi[0]; ++bxx) {
+            const int box = (bz * B.nb[1] + by) * B.nb[0] + bxx;
+            const int loc = kz::reach_local(B, c2, m, bxx, by, bz);
+            int lo[3], mm[3];
+            kz::box_lo(B, box, lo);
+            if (loc < 0 || loc >= B.RS || kz::region_cell(B, loc, lo, mm) != c2 || mm[0] != m[0] || mm[1] != m[1] ||
+                mm[2] != m[2]) {
+              ++bad;
+              continue;
+            }
+            acc = acc + copies[(size_t)box * B.RS + loc];
+            ++cnt;
+          }
+      x[q] = cnt ? mkc<double>(acc.re / cnt, acc.im / cnt) : czero<double>();
+    }
+  }
+  return bad;
+}
+
+}  // namespace
+
 extern "C" {
+
+// Layout of emg_params as this compiler sees it: sizeof, then the offsets of dim, n, h, damping,
+// coarse_solver, level_alpha, smoother, sweep_path, kaczmarz_box, kaczmarz_steps,
+// kaczmarz_damping, coarse_tol, coarse_restart, kaczmarz_max.
+int emg_hc_params_layout(long* out) {
+  out[0] = sizeof(emg_params);
+  out[1] = offsetof(emg_params, dim);
+  out[2] = offsetof(emg_params, n);
+  out[3] = offsetof(emg_params, h);
+  out[4] = offsetof(emg_params, damping);
+  out[5] = offsetof(emg_params, coarse_solver);
+  out[6] = offsetof(emg_params, level_alpha);
+  out[7] = offsetof(emg_params, smoother);
+  out[8] = offsetof(emg_params, sweep_path);
+  out[9] = offsetof(emg_params, kaczmarz_box);
+  out[10] = offsetof(emg_params, kaczmarz_steps);
+  out[11] = offsetof(emg_params, kaczmarz_damping);
+  out[12] = offsetof(emg_params, coarse_tol);
+  out[13] = offsetof(emg_params, coarse_restart);
+  out[14] = offsetof(emg_params, kaczmarz_max);
+  return 0;
+}
+
+// Entry of the Kaczmarz solve's stored Schur row of component c for the column of component c2
+// at offsets o (-1: outside the footprint).
+int emg_hc_kz_slot(int dim, int c, int c2, int o0, int o1, int o2) {
+  const int o[3] = {o0, o1, o2};
+  for (int a = 0; a < dim; ++a)
+    if (o[a] < kz::foot_lo(c, c2, a) || o[a] > 1) return -1;
+  if (dim == 2 && o2 != 0) return -1;
+  return dim == 3 ? kz::slot_of<3>(c, c2, o) : kz::slot_of<2>(c, c2, o);
+}
+
+// Schur rows (complex128, dim N x NE) of one level by probing its operator (att = gamma + shift).
+int emg_hc_kz_probe(int dim, const int* n, double h, double beta, double omega, double att, double abl_len,
+                    double abl_gmax, double Lx, double Ly, double Lz, const double* mu, const double* rho,
+                    const double* cp, double* coef) {
+  if (dim == 3) {
+    Level2<double, 3> L(n, h, beta, omega, att, abl_len, abl_gmax, Lx, Ly, mu, rho, cp, Lz);
+    kz_probe_host<3>(L.g, (cx<double>*)coef);
+  } else if (dim == 2) {
+    Level2<double, 2> L(n, h, beta, omega, att, abl_len, abl_gmax, Lx, Ly, mu, rho, cp);
+    kz_probe_host<2>(L.g, (cx<double>*)coef);
+  } else {
+    return -1;
+  }
+  return 0;
+}
+
+// `steps` parallel hybrid Kaczmarz steps for S x = rhs (complex128 vectors of dim N: the
+// displacement components, boundary faces 0) from x, with boxes of box[a] cells. Returns the
+// number of bad region indices (0), or -1 for a bad dim.
+long emg_hc_kz_steps(int dim, const int* n, const int* box, const double* coef, const double* rhs, double* x,
+                     int steps, double w) {
+  if (dim != 2 && dim != 3) return -1;
+  const kz::Boxes B = kz::make_boxes(dim, n, box);
+  if (dim == 3) return kz_steps_host<3>(B, (const cx<double>*)coef, (const cx<double>*)rhs, (cx<double>*)x, steps, w);
+  return kz_steps_host<2>(B, (const cx<double>*)coef, (const cx<double>*)rhs, (cx<double>*)x, steps, w);
+}
 
 // One-pass tiled residual + restriction (FP32) of a 2D level: bc (complex128, 3 (nx/2)(ny/2)) =
 // R (b - H_s x); the arguments of emg_hc_residual_restrict2 without prec, then the tile height.
@@ -351,6 +555,37 @@ int emg_hc_resid_restrict_tiled(const int* n, double h, double beta, double omeg
   if (ty == 24) resid_restrict_tiled<24>(L.g, b.data(), x.data(), bc.data(), nxc, nyc);
   else resid_restrict_tiled<8>(L.g, b.data(), x.data(), bc.data(), nxc, nyc);
   from_cx(bc, bc64);
+  return 0;
+}
+
+// 2D FP64 apply of the outer solve in float-float arithmetic (ff2::apply_cell over every cell), with
+// the coefficient arrays built as the library builds them (ff2::build_host, ff2::make):
+// y = H x (shift 0) or H_s x; x FP64 (x32 = 0) or rounded to FP32 first (x32 = 1).
+int emg_hc_apply_ff2(const int* n, double h, double beta, double omega, double gamma, double shift, double abl_len,
+                     double abl_gmax, const double* lam, const double* mu, const double* rho, const double* x,
+                     double* y, int x32) {
+  ff2::HostFF2 o;
+  ff2::build_host(o, n[0], n[1], h, lam, mu, rho, omega, gamma, abl_len, abl_gmax, n[0] * h, n[1] * h);
+  const ff2::FineFF g = ff2::make(o.mu.data(), o.mun.data(), o.cp.data(), o.m1.data(), o.m2.data(), n[0], n[1], h,
+                                  beta, shift);
+  const size_t N = (size_t)n[0] * n[1];
+  std::vector<cx<double>> xd(3 * N);
+  std::vector<cx<float>> xf(3 * N);
+  for (size_t k = 0; k < 3 * N; ++k) {
+    xd[k] = mkc<double>(x[2 * k], x[2 * k + 1]);
+    xf[k] = mkc<float>((float)x[2 * k], (float)x[2 * k + 1]);
+  }
+  for (int j = 0; j < n[1]; ++j)
+    for (int i = 0; i < n[0]; ++i) {
+      cx<double> out[3];
+      if (x32) ff2::apply_cell<float>(g, xf.data(), nullptr, 0.0, i, j, out);
+      else ff2::apply_cell<double>(g, xd.data(), nullptr, 0.0, i, j, out);
+      for (int c = 0; c < 3; ++c) {
+        const size_t q = c * N + (size_t)j * n[0] + i;
+        y[2 * q] = out[c].re;
+        y[2 * q + 1] = out[c].im;
+      }
+    }
   return 0;
 }
 

@@ -1,0 +1,749 @@
+// Hybrid Kaczmarz-GMRES solve of the coarsest level (Sections 3.2 and 5.3) in one cooperative
+// launch.
+//
+// The coarsest system H_s x = b is reduced to the displacements by the Schur complement that
+// eliminates p through the diagonal p-p block C = diag(1/(lambda+mu)):
+//   S u = f,  S = A_uu - A_up C^-1 A_pu,  f = b_u - A_up C^-1 b_p,  then p = C^-1 (b_p - A_pu u).
+// S is solved by FGMRES(m) from zero (Arnoldi with modified Gram-Schmidt, complex Givens
+// rotations, the true residual recomputed at every restart), preconditioned by a fixed number of
+// parallel hybrid Kaczmarz steps from zero: the cells are divided into boxes (sub-regions); each
+// box sweeps the Schur rows of its faces (component by component, x fastest) with damped row
+// projections x += w (rhs_i - a_i x) / ||a_i||^2 conj(a_i) on a private copy of the unknowns it
+// reaches, every box starting from the same iterate; each unknown then becomes the mean of the
+// copies of the boxes whose reach holds it (component averaging). The reach of a box for
+// component c2 is the box dilated by 1 cell below along x_c2, 2 cells below along the other
+// axes and 1 cell above: the footprint of the Schur stencil.
+//
+// Rows of S are stored densely over their footprint (NE = 75 entries in 3D, 17 in 2D); they are
+// formed at set-up by probing the level's own operator: for a component c2 and a residue class q
+// of cells modulo 4 per axis, e = 1 on the active c2 faces of class q, and
+// S e = (H_s e)_u - grad(C^-1 (H_s e)_p); a row's footprint holds at most one column of each class.
+//
+// GPU mapping: one block per SM, all blocks co-resident (cooperative launch), meeting at a
+// grid-wide barrier whose waits are bounded (a timeout sets bit 1 of the status word and every
+// block returns). A box is swept by one warp: lanes take the row's entries, the row's dot product
+// is a butterfly reduction (every lane ends with the same bits), and the private copy lives in
+// shared memory. Dot products accumulate in FP64 and are summed over blocks in a fixed order, so
+// the solve is deterministic; the Hessenberg matrix and rotations are FP64, computed identically
+// by every block. The index helpers are __host__ __device__ so that the host can check them.
+#pragma once
+#include "emg_types.cuh"
+#include "stencil2d.cuh"
+#include "stencil3d.cuh"
+
+namespace kz {
+
+constexpr int NT = 1024, NW = NT / 32;
+constexpr int MAXM = 8;          // largest restart length
+constexpr int PER = 4;           // probe period per axis
+constexpr long long WAIT_CYCLES = 4000000000LL;  // bound of one barrier wait (about 2 s)
+
+template <int D>
+struct Shape {
+  static constexpr int NE = D == 3 ? 75 : 17;  // Schur row entries
+  static constexpr int SL = (NE + 31) / 32;    // entries per lane
+};
+
+// Footprint of a row of component c in component c2 along axis a: [foot_lo, 1].
+HD int foot_lo(int c, int c2, int a) { return c2 == c ? -1 : (a == c ? -2 : (a == c2 ? 0 : -1)); }
+// Reach of a box for component c2 below it along axis a (above it: 1 cell).
+HD int reach_lo(int c2, int a) { return a == c2 ? 1 : 2; }
+
+HD int pmod(int a, int m) {
+  const int r = a % m;
+  return r < 0 ? r + m : r;
+}
+
+// Entry s of a row of component c -> component c2 and offsets o (entries run over c2 = 0..D-1,
+// each footprint box with x fastest). false: s >= NE.
+template <int D>
+HD bool slot_decode(int c, int s, int& c2, int o[3]) {
+  o[0] = o[1] = o[2] = 0;
+  for (int cc = 0; cc < D; ++cc) {
+    int w[3] = {1, 1, 1}, cnt = 1;
+    for (int a = 0; a < D; ++a) {
+      w[a] = 2 - foot_lo(c, cc, a);
+      cnt *= w[a];
+    }
+    if (s < cnt) {
+      c2 = cc;
+      for (int a = 0; a < D; ++a) {
+        o[a] = foot_lo(c, cc, a) + s % w[a];
+        s /= w[a];
+      }
+      return true;
+    }
+    s -= cnt;
+  }
+  return false;
+}
+
+template <int D>
+HD int slot_of(int c, int c2, const int o[3]) {
+  int base = 0;
+  for (int cc = 0; cc < c2; ++cc) {
+    int cnt = 1;
+    for (int a = 0; a < D; ++a) cnt *= 2 - foot_lo(c, cc, a);
+    base += cnt;
+  }
+  int s = 0, mul = 1;
+  for (int a = 0; a < D; ++a) {
+    s += (o[a] - foot_lo(c, c2, a)) * mul;
+    mul *= 2 - foot_lo(c, c2, a);
+  }
+  return base + s;
+}
+
+// Box geometry: boxes of box[a] cells, nb[a] per axis; the reach region of a box holds, for
+// each component c2, an rx[c2] x ry[c2] (x rz[c2]) block starting at rbase[c2].
+struct Boxes {
+  int dim, n[3], box[3], nb[3], nboxes;
+  int rx[3], ry[3], rz[3], rbase[3], RS;
+};
+
+inline Boxes make_boxes(int dim, const int n[3], const int box[3]) {
+  Boxes B{};
+  B.dim = dim;
+  B.nboxes = 1;
+  for (int a = 0; a < 3; ++a) {
+    B.n[a] = a < dim ? n[a] : 1;
+    B.box[a] = a < dim ? box[a] : 1;
+    B.nb[a] = (B.n[a] + B.box[a] - 1) / B.box[a];
+    B.nboxes *= B.nb[a];
+  }
+  int base = 0;
+  for (int c2 = 0; c2 < dim; ++c2) {
+    B.rx[c2] = B.box[0] + reach_lo(c2, 0) + 1;
+    B.ry[c2] = B.box[1] + reach_lo(c2, 1) + 1;
+    B.rz[c2] = dim == 3 ? B.box[2] + reach_lo(c2, 2) + 1 : 1;
+    B.rbase[c2] = base;
+    base += B.rx[c2] * B.ry[c2] * B.rz[c2];
+  }
+  B.RS = base;
+  return B;
+}
+
+// Lowest cell of box bx.
+HD void box_lo(const Boxes& B, int bx, int lo[3]) {
+  lo[0] = (bx % B.nb[0]) * B.box[0];
+  lo[1] = ((bx / B.nb[0]) % B.nb[1]) * B.box[1];
+  lo[2] = (bx / (B.nb[0] * B.nb[1])) * B.box[2];
+}
+
+// Region value t of the box with lowest cell lo -> component and cell (may lie outside).
+HD int region_cell(const Boxes& B, int t, const int lo[3], int m[3]) {
+  int c2 = 0;
+  while (c2 + 1 < B.dim && t >= B.rbase[c2 + 1]) ++c2;
+  int r = t - B.rbase[c2];
+  m[0] = lo[0] - reach_lo(c2, 0) + r % B.rx[c2];
+  r /= B.rx[c2];
+  m[1] = lo[1] - reach_lo(c2, 1) + r % B.ry[c2];
+  m[2] = B.dim == 3 ? lo[2] - reach_lo(c2, 2) + r / B.ry[c2] : 0;
+  return c2;
+}
+
+// Position in a box's region of the entry (c2, o) of the row at local cell (lx, ly, lz).
+HD int region_index(const Boxes& B, int c2, const int o[3], int lx, int ly, int lz) {
+  const int z = B.dim == 3 ? lz + o[2] + reach_lo(c2, 2) : 0;
+  return B.rbase[c2] + (z * B.ry[c2] + ly + o[1] + reach_lo(c2, 1)) * B.rx[c2] + lx + o[0] + reach_lo(c2, 0);
+}
+
+// Boxes whose reach holds the face of component c2 in cell m: [blo, bhi] per axis.
+HD void reach_boxes(const Boxes& B, int c2, const int m[3], int blo[3], int bhi[3]) {
+  for (int a = 0; a < 3; ++a) {
+    if (a >= B.dim) {
+      blo[a] = bhi[a] = 0;
+      continue;
+    }
+    const int bb = B.box[a];
+    const int lo = (m[a] + bb - 1) / bb - 1;
+    const int hi = (m[a] + reach_lo(c2, a)) / bb;
+    blo[a] = lo < 0 ? 0 : lo;
+    bhi[a] = hi > B.nb[a] - 1 ? B.nb[a] - 1 : hi;
+  }
+}
+
+// Position of that face in the region of box (bxx, by, bz).
+HD int reach_local(const Boxes& B, int c2, const int m[3], int bxx, int by, int bz) {
+  const int lz = B.dim == 3 ? m[2] - (bz * B.box[2] - reach_lo(c2, 2)) : 0;
+  const int ly = m[1] - (by * B.box[1] - reach_lo(c2, 1));
+  const int lx = m[0] - (bxx * B.box[0] - reach_lo(c2, 0));
+  return B.rbase[c2] + (lz * B.ry[c2] + ly) * B.rx[c2] + lx;
+}
+
+HD size_t cell_of(const int n[3], int dim, int i, int j, int k) {
+  return dim == 3 ? ((size_t)k * n[1] + j) * n[0] + i : (size_t)j * n[0] + i;
+}
+
+// ---------------------------------------------------------------- set-up: probing
+// Probe value at position t of a (D+1) N vector: 1 on the active c2 faces of class q.
+template <typename T, int D>
+HD cx<T> probe_value(int c2, const int q[3], const int n[3], size_t t) {
+  const size_t N = (size_t)n[0] * n[1] * (D == 3 ? n[2] : 1);
+  const int c = (int)(t / N);
+  const size_t cell = t % N;
+  const int idx[3] = {(int)(cell % n[0]), (int)((cell / n[0]) % n[1]), D == 3 ? (int)(cell / ((size_t)n[0] * n[1])) : 0};
+  bool on = c == c2 && idx[c2] >= 1;
+  for (int a = 0; a < D; ++a) on = on && pmod(idx[a] - q[a], PER) == 0;
+  return mkc<T>(on ? T(1) : T(0), T(0));
+}
+
+// y = H_s e of a probe: the entry of row r (component c, cell k) of S for its class-q column of
+// component c2, stored at coef[r NE + slot] (rows without such a column: nothing written).
+template <typename T, int D>
+HD void probe_take_row(const Grid<T>& g, const cx<T>* y, int c2, const int q[3], size_t r, cx<T>* coef) {
+  constexpr int NE = Shape<D>::NE;
+  const int n[3] = {g.nx, g.ny, D == 3 ? g.nz : 1};
+  const size_t N = (size_t)n[0] * n[1] * n[2];
+  const int c = (int)(r / N);
+  const size_t cell = r % N;
+  const int kk[3] = {(int)(cell % n[0]), (int)((cell / n[0]) % n[1]), D == 3 ? (int)(cell / ((size_t)n[0] * n[1])) : 0};
+  if (kk[c] < 1) return;  // boundary face: not an unknown
+  int o[3] = {0, 0, 0}, m[3] = {0, 0, 0};
+  for (int a = 0; a < D; ++a) {
+    const int lo = foot_lo(c, c2, a);
+    o[a] = lo + pmod(q[a] - kk[a] - lo, PER);
+    if (o[a] > 1) return;  // no column of this class in the footprint
+    m[a] = kk[a] + o[a];
+    if (m[a] < 0 || m[a] >= n[a]) return;
+  }
+  if (m[c2] < 1) return;  // the column is a boundary face
+  int pm[3] = {kk[0], kk[1], kk[2]};
+  pm[c] -= 1;
+  const size_t km = cell_of(n, D, pm[0], pm[1], pm[2]);
+  const cx<T>* yp = y + (size_t)D * N;
+  const cx<T> gp = (T(1) / g.cp[cell]) * yp[cell] - (T(1) / g.cp[km]) * yp[km];
+  coef[r * NE + slot_of<D>(c, c2, o)] = y[r] - g.ih * gp;
+}
+
+template <typename T, int D>
+HD T inv_row_norm(const cx<T>* coef, size_t r) {
+  constexpr int NE = Shape<D>::NE;
+  T s = T(0);
+  for (int e = 0; e < NE; ++e) {
+    const cx<T> v = coef[r * NE + e];
+    s += v.re * v.re + v.im * v.im;
+  }
+  return s > T(0) ? T(1) / s : T(0);
+}
+
+// f = b_u - A_up C^-1 b_p at Schur row q (0 on boundary faces).
+template <typename T, int D>
+HD cx<T> schur_rhs(const Grid<T>& g, const cx<T>* b, size_t q) {
+  const int n[3] = {g.nx, g.ny, D == 3 ? g.nz : 1};
+  const size_t N = (size_t)n[0] * n[1] * n[2];
+  const int c = (int)(q / N);
+  const size_t cell = q % N;
+  int k[3] = {(int)(cell % n[0]), (int)((cell / n[0]) % n[1]), D == 3 ? (int)(cell / ((size_t)n[0] * n[1])) : 0};
+  if (k[c] < 1) return czero<T>();
+  const cx<T>* bp = b + (size_t)D * N;
+  k[c] -= 1;
+  const size_t km = cell_of(n, D, k[0], k[1], k[2]);
+  const cx<T> gq = (T(1) / g.cp[cell]) * bp[cell] - (T(1) / g.cp[km]) * bp[km];
+  return b[q] - g.ih * gq;
+}
+
+template <typename T>
+struct Args {
+  Grid<T> g;                 // the coarsest level's operator H_s
+  Boxes B;                   // sub-region boxes
+  size_t N;                  // cells
+  int warps_a;               // warps per block that own a region in shared memory
+  const cx<T>* coef;         // D N rows x NE entries
+  const T* inv_n2;           // 1 / ||row||^2 (0: no row)
+  const cx<T>* b;            // (D+1) N right-hand side
+  cx<T>* x;                  // (D+1) N solution
+  cx<T>* f;                  // D N: Schur right-hand side
+  cx<T>* u;                  // D N: Schur iterate
+  cx<T>* w;                  // D N: Arnoldi / residual work vector
+  cx<T>* V;                  // (m+1) D N
+  cx<T>* Z;                  // m D N
+  cx<T>* copies;             // nboxes RS
+  double* part;              // 2 x gridDim x 2 partial sums
+  unsigned* bar;             // barrier count, generation
+  int* err;                  // status word (bit 1: a barrier wait timed out)
+  double* stats;             // FGMRES iterations, relative Schur residual, Kaczmarz steps
+  T damping;
+  int steps, restart, max_its;
+  double tol;
+};
+
+#ifdef __CUDACC__
+template <typename T, int D>
+__global__ void probe_set(cx<T>* __restrict__ e, int c2, int q0, int q1, int q2, int nx, int ny, int nz) {
+  const int n[3] = {nx, ny, nz}, q[3] = {q0, q1, q2};
+  const size_t N = (size_t)nx * ny * nz;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < (size_t)(D + 1) * N) e[t] = probe_value<T, D>(c2, q, n, t);
+}
+
+template <typename T, int D>
+__global__ void probe_take(Grid<T> g, const cx<T>* __restrict__ y, int c2, int q0, int q1, int q2,
+                           cx<T>* __restrict__ coef) {
+  const int q[3] = {q0, q1, q2};
+  const size_t N = (size_t)g.nx * g.ny * g.nz;
+  const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < (size_t)D * N) probe_take_row<T, D>(g, y, c2, q, r, coef);
+}
+
+template <typename T, int D>
+__global__ void row_norms(const cx<T>* __restrict__ coef, T* __restrict__ inv_n2, size_t rows) {
+  const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < rows) inv_n2[r] = inv_row_norm<T, D>(coef, r);
+}
+
+// ---------------------------------------------------------------- the solve
+__device__ __forceinline__ void st_cg(cx<float>* p, cx<float> v) { __stcg(reinterpret_cast<float2*>(p), make_float2(v.re, v.im)); }
+__device__ __forceinline__ void st_cg(cx<double>* p, cx<double> v) {
+  __stcg(reinterpret_cast<double2*>(p), make_double2(v.re, v.im));
+}
+
+// Grid-wide barrier with bounded waits. Returns false (on every thread of the block) once any
+// block has recorded a timeout; the caller then returns.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int* err, int* sh_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    volatile int* verr = err;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned prev = atomicAdd(bar, 1u);
+    if (prev == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        if (*verr & 2) break;
+        if (clock64() - t0 > WAIT_CYCLES) {
+          atomicOr(err, 2);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    *sh_ok = (*verr & 2) ? 0 : 1;
+  }
+  __syncthreads();
+  return *(volatile int*)sh_ok != 0;
+}
+
+struct Shared {
+  double red[2 * NW + 4];
+  cx<double> H[(MAXM + 1) * MAXM];
+  cx<double> cs[MAXM], sn[MAXM], gv[MAXM + 1], y[MAXM];
+  double scal[4];
+  int ok;
+};
+
+__device__ __forceinline__ cx<double> cdd(double r, double i) { return mkc<double>(r, i); }
+__device__ __forceinline__ double cabs2(cx<double> a) { return a.re * a.re + a.im * a.im; }
+__device__ __forceinline__ cx<double> cdiv_real(cx<double> a, double s) { return mkc<double>(a.re / s, a.im / s); }
+
+// Sum over the grid of the per-thread (re, im); the same bits on every thread of every block.
+// One barrier. parity alternates the partial-sum buffer between consecutive reductions.
+__device__ __forceinline__ bool grid_sum(double re, double im, double* part, unsigned* bar, int* err, Shared& sh,
+                                         int& parity, cx<double>& out) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, m);
+    im += __shfl_xor_sync(0xffffffffu, im, m);
+  }
+  if (lane == 0) {
+    sh.red[2 * wib] = re;
+    sh.red[2 * wib + 1] = im;
+  }
+  __syncthreads();
+  double* P = part + (size_t)parity * 2 * gridDim.x;
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < NW; ++k) {
+      a += sh.red[2 * k];
+      b += sh.red[2 * k + 1];
+    }
+    __stcg(P + 2 * blockIdx.x, a);
+    __stcg(P + 2 * blockIdx.x + 1, b);
+  }
+  parity ^= 1;
+  if (!grid_sync(bar, err, &sh.ok)) return false;
+  if (wib == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = lane; k < (int)gridDim.x; k += 32) {
+      a += __ldcg(P + 2 * k);
+      b += __ldcg(P + 2 * k + 1);
+    }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, m);
+      b += __shfl_xor_sync(0xffffffffu, b, m);
+    }
+    if (lane == 0) {
+      sh.scal[0] = a;
+      sh.scal[1] = b;
+    }
+  }
+  __syncthreads();
+  out = cdd(sh.scal[0], sh.scal[1]);
+  __syncthreads();
+  return true;
+}
+
+// Per-lane table of a row's entries: for component c and lane slot t (entry lane + 32 t), -1 (no
+// entry) or the packed entry: component c2 (bits 0-1), offsets + 2 (3 bits each from bit 2) and
+// the region position for the row cell at local (0, 0, 0) (from bit 11).
+template <int D>
+struct LaneTab {
+  int pk[D][Shape<D>::SL];
+  HD void init(const Boxes& B, int lane) {
+    for (int c = 0; c < D; ++c)
+      for (int t = 0; t < Shape<D>::SL; ++t) {
+        int cc = -1, oo[3];
+        if (slot_decode<D>(c, lane + 32 * t, cc, oo))
+          pk[c][t] = cc | (oo[0] + 2) << 2 | (oo[1] + 2) << 5 | (oo[2] + 2) << 8 | region_index(B, cc, oo, 0, 0, 0) << 11;
+        else
+          pk[c][t] = -1;
+      }
+  }
+  // (selects instead of an indexed load keep the table in registers)
+  HD int get(int c, int t) const {
+    int v = pk[0][t];
+    if (D > 1 && c == 1) v = pk[1][t];
+    if (D > 2 && c == 2) v = pk[D - 1][t];
+    return v;
+  }
+};
+HD int pk_c2(int v) { return v & 3; }
+HD int pk_o(int v, int a) { return ((v >> (2 + 3 * a)) & 7) - 2; }
+HD int pk_off(int v) { return v >> 11; }
+
+// One sweep of every box: rhs -> copies, starting from xin (nullptr: zero).
+template <typename T, int D>
+__device__ void sweep_boxes(const Args<T>& a, const LaneTab<D>& tab, const cx<T>* rhs, const cx<T>* xin, cx<T>* reg,
+                            int gw, int nwa) {
+  constexpr int NE = Shape<D>::NE, SL = Shape<D>::SL;
+  const int lane = threadIdx.x & 31;
+  const Boxes& B = a.B;
+  const size_t N = a.N;
+  for (int bx = gw; bx < B.nboxes; bx += nwa) {
+    int lo[3];
+    box_lo(B, bx, lo);
+    for (int t = lane; t < B.RS; t += 32) {
+      cx<T> v = czero<T>();
+      if (xin) {
+        int m[3];
+        const int c2 = region_cell(B, t, lo, m);
+        bool in = true;
+        for (int q = 0; q < D; ++q) in = in && m[q] >= 0 && m[q] < B.n[q];
+        if (in && m[c2] >= 1) v = ldcg(xin + (size_t)c2 * N + cell_of(B.n, D, m[0], m[1], m[2]));
+      }
+      reg[t] = v;
+    }
+    __syncwarp();
+    for (int c = 0; c < D; ++c)
+      for (int lz = 0; lz < B.box[2]; ++lz)
+        for (int ly = 0; ly < B.box[1]; ++ly)
+          for (int lx = 0; lx < B.box[0]; ++lx) {
+            const int k[3] = {lo[0] + lx, lo[1] + ly, lo[2] + lz};
+            if (k[0] >= B.n[0] || k[1] >= B.n[1] || k[2] >= B.n[2] || k[c] < 1) continue;
+            const size_t r = (size_t)c * N + cell_of(B.n, D, k[0], k[1], k[2]);
+            const T in2 = __ldg(a.inv_n2 + r);
+            if (in2 == T(0)) continue;
+            cx<T> co[SL];
+            int idx[SL];
+            T sr = T(0), si = T(0);
+#pragma unroll
+            for (int t = 0; t < SL; ++t) {
+              const int pk = tab.get(c, t);
+              idx[t] = -1;
+              co[t] = czero<T>();
+              if (pk >= 0) {
+                const int cc = pk_c2(pk);
+                co[t] = ldg(a.coef + r * NE + lane + 32 * t);
+                idx[t] = pk_off(pk) + (lz * B.ry[cc] + ly) * B.rx[cc] + lx;
+                const cx<T> xv = reg[idx[t]];
+                sr += co[t].re * xv.re - co[t].im * xv.im;
+                si += co[t].re * xv.im + co[t].im * xv.re;
+              }
+            }
+#pragma unroll
+            for (int m = 16; m >= 1; m >>= 1) {
+              sr += __shfl_xor_sync(0xffffffffu, sr, m);
+              si += __shfl_xor_sync(0xffffffffu, si, m);
+            }
+            const cx<T> bv = ldcg(rhs + r);
+            const T s_re = a.damping * in2 * (bv.re - sr), s_im = a.damping * in2 * (bv.im - si);
+#pragma unroll
+            for (int t = 0; t < SL; ++t) {
+              if (idx[t] >= 0) {  // += s conj(a)
+                cx<T> v = reg[idx[t]];
+                v.re += s_re * co[t].re + s_im * co[t].im;
+                v.im += s_im * co[t].re - s_re * co[t].im;
+                reg[idx[t]] = v;
+              }
+            }
+            __syncwarp();
+          }
+    cx<T>* out = a.copies + (size_t)bx * B.RS;
+    for (int t = lane; t < B.RS; t += 32) st_cg(out + t, reg[t]);
+    __syncwarp();
+  }
+}
+
+// Component average of the copies -> out (D N; boundary faces 0).
+template <typename T, int D>
+__device__ void average(const Args<T>& a, cx<T>* out, size_t tid, size_t nthr) {
+  const Boxes& B = a.B;
+  const size_t N = a.N;
+  for (size_t q = tid; q < (size_t)D * N; q += nthr) {
+    const int c2 = (int)(q / N);
+    const size_t cell = q % N;
+    const int m[3] = {(int)(cell % B.n[0]), (int)((cell / B.n[0]) % B.n[1]), D == 3 ? (int)(cell / ((size_t)B.n[0] * B.n[1])) : 0};
+    if (m[c2] < 1) {
+      out[q] = czero<T>();
+      continue;
+    }
+    int blo[3], bhi[3];
+    reach_boxes(B, c2, m, blo, bhi);
+    T sr = T(0), si = T(0);
+    int cnt = 0;
+    for (int bz = blo[2]; bz <= bhi[2]; ++bz)
+      for (int by = blo[1]; by <= bhi[1]; ++by)
+        for (int bxx = blo[0]; bxx <= bhi[0]; ++bxx) {
+          const int box = (bz * B.nb[1] + by) * B.nb[0] + bxx;
+          const cx<T> v = ldcg(a.copies + (size_t)box * B.RS + reach_local(B, c2, m, bxx, by, bz));
+          sr += v.re;
+          si += v.im;
+          ++cnt;
+        }
+    out[q] = mkc<T>(sr / T(cnt), si / T(cnt));
+  }
+}
+
+// w = S z (or rhs - S z), one row per warp; adds this thread's share of sum conj(v) w (v given)
+// or of |w|^2 (v == nullptr) to (dre, dim_).
+template <typename T, int D>
+__device__ void matvec(const Args<T>& a, const LaneTab<D>& tab, const cx<T>* z, const cx<T>* rhs, cx<T>* w,
+                       const cx<T>* v, double& dre, double& dim_, int gwall, int nwall) {
+  constexpr int NE = Shape<D>::NE, SL = Shape<D>::SL;
+  const int lane = threadIdx.x & 31;
+  const Boxes& B = a.B;
+  const size_t N = a.N;
+  for (size_t r = gwall; r < (size_t)D * N; r += nwall) {
+    const int c = (int)(r / N);
+    const size_t cell = r % N;
+    const int k[3] = {(int)(cell % B.n[0]), (int)((cell / B.n[0]) % B.n[1]), D == 3 ? (int)(cell / ((size_t)B.n[0] * B.n[1])) : 0};
+    T sr = T(0), si = T(0);
+    if (k[c] >= 1) {
+#pragma unroll
+      for (int t = 0; t < SL; ++t) {
+        const int pk = tab.get(c, t);
+        if (pk < 0) continue;
+        const int cc = pk_c2(pk);
+        const int m[3] = {k[0] + pk_o(pk, 0), k[1] + pk_o(pk, 1), k[2] + pk_o(pk, 2)};
+        bool in = true;
+        for (int q = 0; q < D; ++q) in = in && m[q] >= 0 && m[q] < B.n[q];
+        if (!in) continue;
+        const cx<T> co = ldg(a.coef + r * NE + lane + 32 * t);
+        const cx<T> zv = ldcg(z + (size_t)cc * N + cell_of(B.n, D, m[0], m[1], m[2]));
+        sr += co.re * zv.re - co.im * zv.im;
+        si += co.re * zv.im + co.im * zv.re;
+      }
+    }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, m);
+      si += __shfl_xor_sync(0xffffffffu, si, m);
+    }
+    cx<T> wv = mkc<T>(sr, si);
+    if (rhs) {
+      const cx<T> bv = ldcg(rhs + r);
+      wv = mkc<T>(bv.re - sr, bv.im - si);
+    }
+    if (lane == 0) {
+      st_cg(w + r, wv);
+      if (v) {
+        const cx<T> vv = ldcg(v + r);
+        dre += (double)vv.re * wv.re + (double)vv.im * wv.im;
+        dim_ += (double)vv.re * wv.im - (double)vv.im * wv.re;
+      } else {
+        dre += (double)wv.re * wv.re + (double)wv.im * wv.im;
+      }
+    }
+  }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(NT, 1) solve(Args<T> a) {
+  extern __shared__ __align__(16) unsigned char kz_smem[];
+  __shared__ Shared sh;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  cx<T>* reg = reinterpret_cast<cx<T>*>(kz_smem) + (size_t)(wib < a.warps_a ? wib : 0) * a.B.RS;
+  const size_t tid = (size_t)blockIdx.x * NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
+  const int gwall = blockIdx.x * NW + wib, nwall = gridDim.x * NW;
+  const int gwa = blockIdx.x * a.warps_a + wib, nwa = gridDim.x * a.warps_a;
+  const size_t N = a.N, DN = (size_t)D * N;
+  const Grid<T>& g = a.g;
+  LaneTab<D> tab;
+  tab.init(a.B, lane);
+  int parity = 0;
+  cx<double> red;
+
+  // f = b_u - A_up C^-1 b_p, u = 0, ||f||^2
+  double acc = 0.0;
+  for (size_t q = tid; q < DN; q += nthr) {
+    const cx<T> fv = schur_rhs<T, D>(g, a.b, q);
+    st_cg(a.f + q, fv);
+    st_cg(a.u + q, czero<T>());
+    acc += (double)fv.re * fv.re + (double)fv.im * fv.im;
+  }
+  if (!grid_sum(acc, 0.0, a.part, a.bar, a.err, sh, parity, red)) return;
+  const double bnorm = sqrt(red.re);
+  double beta = bnorm;
+  int its = 0;
+  const int m = a.restart;
+  if (bnorm > 0.0) {
+    for (size_t q = tid; q < DN; q += nthr) {  // V_0 = f / beta
+      const cx<T> fv = ldcg(a.f + q);
+      st_cg(a.V + q, mkc<T>((T)(fv.re / beta), (T)(fv.im / beta)));
+    }
+    while (beta / bnorm > a.tol && its < a.max_its) {
+      if (threadIdx.x == 0) {
+        for (int i = 0; i <= MAXM; ++i) sh.gv[i] = cdd(0.0, 0.0);
+        sh.gv[0] = cdd(beta, 0.0);
+      }
+      int kdone = 0;
+      for (int j = 0; j < m; ++j) {
+        const cx<T>* Vj = a.V + (size_t)j * DN;
+        cx<T>* Zj = a.Z + (size_t)j * DN;
+        if (!grid_sync(a.bar, a.err, &sh.ok)) return;
+        // Z_j = K(V_j): Kaczmarz steps from zero
+        for (int s = 0; s < a.steps; ++s) {
+          if (wib < a.warps_a) sweep_boxes<T, D>(a, tab, Vj, s == 0 ? nullptr : Zj, reg, gwa, nwa);
+          if (!grid_sync(a.bar, a.err, &sh.ok)) return;
+          average<T, D>(a, Zj, tid, nthr);
+          if (!grid_sync(a.bar, a.err, &sh.ok)) return;
+        }
+        // w = S Z_j, h_0j = <V_0, w>
+        double dre = 0.0, dim_ = 0.0;
+        matvec<T, D>(a, tab, Zj, nullptr, a.w, a.V, dre, dim_, gwall, nwall);
+        if (!grid_sum(dre, dim_, a.part, a.bar, a.err, sh, parity, red)) return;
+        if (threadIdx.x == 0) sh.H[j] = red;
+        __syncthreads();
+        // modified Gram-Schmidt: w -= h_{i-1,j} V_{i-1}, then h_ij = <V_i, w> (i <= j) or ||w||
+        for (int i = 1; i <= j + 1; ++i) {
+          const cx<double> hp = sh.H[(i - 1) * MAXM + j];
+          const cx<T> h = mkc<T>((T)hp.re, (T)hp.im);
+          const cx<T>* Vp = a.V + (size_t)(i - 1) * DN;
+          const cx<T>* Vi = a.V + (size_t)i * DN;
+          double pr = 0.0, pi = 0.0;
+          for (size_t q = tid; q < DN; q += nthr) {
+            const cx<T> wv = ldcg(a.w + q) - h * ldcg(Vp + q);
+            st_cg(a.w + q, wv);
+            if (i <= j) {
+              const cx<T> vv = ldcg(Vi + q);
+              pr += (double)vv.re * wv.re + (double)vv.im * wv.im;
+              pi += (double)vv.re * wv.im - (double)vv.im * wv.re;
+            } else {
+              pr += (double)wv.re * wv.re + (double)wv.im * wv.im;
+            }
+          }
+          if (!grid_sum(pr, pi, a.part, a.bar, a.err, sh, parity, red)) return;
+          if (threadIdx.x == 0) sh.H[i * MAXM + j] = i <= j ? red : cdd(sqrt(red.re), 0.0);
+          __syncthreads();
+        }
+        const double hn = sh.H[(j + 1) * MAXM + j].re;
+        if (hn != 0.0) {  // V_{j+1} = w / h_{j+1,j}
+          cx<T>* Vn = a.V + (size_t)(j + 1) * DN;
+          for (size_t q = tid; q < DN; q += nthr) {
+            const cx<T> wv = ldcg(a.w + q);
+            st_cg(Vn + q, mkc<T>((T)(wv.re / hn), (T)(wv.im / hn)));
+          }
+        }
+        // Givens rotations (FP64, the same on every block)
+        if (threadIdx.x == 0) {
+          cx<double>* Hc = sh.H;
+          for (int i = 0; i < j; ++i) {
+            const cx<double> hij = Hc[i * MAXM + j], hi1 = Hc[(i + 1) * MAXM + j];
+            const cx<double> t = sh.cs[i] * hij + sh.sn[i] * hi1;
+            Hc[(i + 1) * MAXM + j] = (-cconj(sh.sn[i])) * hij + cconj(sh.cs[i]) * hi1;
+            Hc[i * MAXM + j] = t;
+          }
+          const cx<double> av = Hc[j * MAXM + j], bv = Hc[(j + 1) * MAXM + j];
+          const double den = sqrt(cabs2(av) + cabs2(bv));
+          if (den == 0.0) {
+            sh.cs[j] = cdd(1.0, 0.0);
+            sh.sn[j] = cdd(0.0, 0.0);
+          } else {
+            sh.cs[j] = cconj(cdiv_real(av, den));
+            sh.sn[j] = cconj(cdiv_real(bv, den));
+          }
+          Hc[j * MAXM + j] = sh.cs[j] * av + sh.sn[j] * bv;
+          Hc[(j + 1) * MAXM + j] = cdd(0.0, 0.0);
+          sh.gv[j + 1] = (-cconj(sh.sn[j])) * sh.gv[j];
+          sh.gv[j] = sh.cs[j] * sh.gv[j];
+        }
+        __syncthreads();
+        ++its;
+        kdone = j + 1;
+        const cx<double> hjj = sh.H[j * MAXM + j];
+        if (sqrt(cabs2(sh.gv[j + 1])) / bnorm <= a.tol || its >= a.max_its || (hjj.re == 0.0 && hjj.im == 0.0)) break;
+      }
+      // y = H^-1 g (upper triangular), u += Z y
+      if (threadIdx.x == 0) {
+        for (int i = kdone - 1; i >= 0; --i) {
+          cx<double> s = sh.gv[i];
+          for (int l = i + 1; l < kdone; ++l) s = s - sh.H[i * MAXM + l] * sh.y[l];
+          const cx<double> d = sh.H[i * MAXM + i];
+          sh.y[i] = cdiv_real(s * cconj(d), cabs2(d));
+        }
+      }
+      __syncthreads();
+      for (size_t q = tid; q < DN; q += nthr) {
+        cx<T> uv = ldcg(a.u + q);
+        for (int l = 0; l < kdone; ++l) {
+          const cx<double> yl = sh.y[l];
+          uv = uv + mkc<T>((T)yl.re, (T)yl.im) * ldcg(a.Z + (size_t)l * DN + q);
+        }
+        st_cg(a.u + q, uv);
+      }
+      if (!grid_sync(a.bar, a.err, &sh.ok)) return;
+      // true residual r = f - S u -> w, beta
+      double dre = 0.0, dim_ = 0.0;
+      matvec<T, D>(a, tab, a.u, a.f, a.w, nullptr, dre, dim_, gwall, nwall);
+      if (!grid_sum(dre, 0.0, a.part, a.bar, a.err, sh, parity, red)) return;
+      beta = sqrt(red.re);
+      if (beta / bnorm > a.tol && its < a.max_its) {
+        for (size_t q = tid; q < DN; q += nthr) {  // V_0 = r / beta
+          const cx<T> wv = ldcg(a.w + q);
+          st_cg(a.V + q, mkc<T>((T)(wv.re / beta), (T)(wv.im / beta)));
+        }
+      }
+    }
+  }
+  // recover (u, p): x_u = u, x_p = C^-1 (b_p - A_pu u)
+  for (size_t q = tid; q < DN; q += nthr) st_cg(a.x + q, ldcg(a.u + q));
+  for (size_t q = tid; q < N; q += nthr) st_cg(a.x + DN + q, czero<T>());
+  if (!grid_sync(a.bar, a.err, &sh.ok)) return;
+  for (size_t q = tid; q < N; q += nthr) {
+    const int i = (int)(q % g.nx), j = (int)((q / g.nx) % g.ny), k = D == 3 ? (int)(q / ((size_t)g.nx * g.ny)) : 0;
+    cx<T> dv;
+    if (D == 3) {
+      const cx<T>* uu[3] = {a.x, a.x + N, a.x + 2 * N};
+      dv = s3::row_p<T, T>(uu, a.x + DN, g, i, j, k);
+    } else {
+      dv = s2::row_p<T, T>(a.x, a.x + N, a.x + DN, g, i, j);
+    }
+    st_cg(a.x + DN + q, (T(1) / g.cp[q]) * (a.b[DN + q] - dv));
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.stats[0] = its;
+    a.stats[1] = bnorm > 0.0 ? beta / bnorm : 0.0;
+    a.stats[2] = (double)its * a.steps;
+  }
+}
+#endif  // __CUDACC__
+
+}  // namespace kz

@@ -5,6 +5,7 @@
 #include "emg_types.cuh"
 #include "apply_ff2d.cuh"
 #include "apply_ff3d.cuh"
+#include "kaczmarz.cuh"
 
 #include <string>
 
@@ -65,6 +66,10 @@ template <typename TI>
 void launch_apply_ff3(const ff3::FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y,
                       cudaStream_t st);
 
+template <typename TI>
+void launch_apply_adjoint_ff3(const ff3::FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale,
+                              cx<double>* y, cudaStream_t st);
+
 // Adjoint-state gradient (adjoint.cu): y = H^H x or y = bscale b - H^H x on the finest level,
 // the per-cell material derivative, and z <- S conj(z) on an FP32 vector (nu displacement
 // entries, then the pressure).
@@ -75,3 +80,19 @@ template <int D>
 void launch_adjoint_gradient(const Grid<double>& g, const cx<double>* u, const cx<double>* a, double* glam,
                              double* gmu, double* grho, int accumulate, cudaStream_t st);
 void launch_sconj(cx<float>* z, size_t nu, size_t n, cudaStream_t st);
+
+// Hybrid Kaczmarz-GMRES coarsest solve (kaczmarz.cu / kaczmarz.cuh). launch_kz_probe fills the
+// Schur rows (D N rows x NE entries, zero where a row has no column) and their inverse squared
+// norms by probing the level operator of g; e and y are scratch vectors of (D+1) N values.
+// plan_kz_solve sizes the cooperative launch (one block per SM, the warps whose private copies
+// fit in shared memory); launch_kz_solve runs one solve described by a.
+struct KzLaunch {
+  int blocks = 0, warps = 0;
+  size_t smem = 0;
+};
+template <typename T>
+cudaError_t launch_kz_probe(const Grid<T>& g, int dim, cx<T>* coef, T* inv_n2, cx<T>* e, cx<T>* y, cudaStream_t st);
+template <typename T>
+cudaError_t plan_kz_solve(int dim, int sms, int RS, KzLaunch& out);
+template <typename T>
+cudaError_t launch_kz_solve(const kz::Args<T>& a, int dim, const KzLaunch& L, cudaStream_t st);

@@ -14,13 +14,13 @@ import numpy as np
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libemg.so")
 MAX_LEVELS = 10
-COARSE_DENSE, COARSE_SMOOTH = 0, 1
+COARSE_DENSE, COARSE_SMOOTH, COARSE_KACZMARZ = 0, 1, 2
 CYCLE_V, CYCLE_W, CYCLE_K = 0, 1, 2
-K_SMOOTH, K_RESTRICT, K_PROLONG, K_APPLY64, K_KRYLOV = range(5)
+K_SMOOTH, K_RESTRICT, K_PROLONG, K_APPLY64, K_KRYLOV, K_COARSE = range(6)
 VANKA_FULL, VANKA_ECONOMIC = 0, 1
 SWEEP_AUTO, SWEEP_HALF, SWEEP_COOP, SWEEP_TILE24, SWEEP_TILE8 = 0, 1, 2, 3, 4
 SWEEP_NAMES = {SWEEP_HALF: "half", SWEEP_COOP: "coop", SWEEP_TILE24: "tile24", SWEEP_TILE8: "tile8"}
-K_ALL = 5
+K_ALL = 6
 
 STATUS = {0: "EMG_OK", 1: "EMG_ERR_INVALID", 2: "EMG_ERR_NOMEM", 3: "EMG_ERR_CUDA", 4: "EMG_ERR_NONFINITE",
           5: "EMG_NOT_CONVERGED", 6: "EMG_ERR_TIMEOUT"}
@@ -41,7 +41,9 @@ class _Params(ctypes.Structure):
                 ("coarse_sweeps", ctypes.c_int32), ("coarse_damping", ctypes.c_double),
                 ("cycle_precision", ctypes.c_int32), ("cycle_type", ctypes.c_int32),
                 ("level_alpha", ctypes.c_double * MAX_LEVELS), ("smoother", ctypes.c_int32),
-                ("sweep_path", ctypes.c_int32)]
+                ("sweep_path", ctypes.c_int32), ("kaczmarz_box", ctypes.c_int32 * 3),
+                ("kaczmarz_steps", ctypes.c_int32), ("kaczmarz_damping", ctypes.c_double),
+                ("coarse_tol", ctypes.c_double), ("coarse_restart", ctypes.c_int32), ("kaczmarz_max", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -76,6 +78,8 @@ def _load():
         "emg_apply_adjoint": [vp, vp, vp],
         "emg_solve_adjoint": [vp, vp, vp, dbl, i32, i32, ctypes.POINTER(_Stats)],
         "emg_material_gradient": [vp, vp, vp, vp, vp, vp, i32],
+        "emg_coarse_stats": [vp, ctypes.POINTER(dbl)],
+        "emg_coarse_schur_rows": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -90,7 +94,8 @@ LIB = _load()
 EXPORTED = ["emg_create", "emg_destroy", "emg_last_error", "emg_apply", "emg_vcycle", "emg_solve", "emg_solve_host",
             "emg_level_info", "emg_smooth", "emg_residual_restrict", "emg_prolong_correct", "emg_coarse_solve",
             "emg_profile", "emg_profile_read", "emg_smooth_noalloc", "emg_solve_batch", "emg_apply_adjoint",
-            "emg_solve_adjoint", "emg_material_gradient", "emg_sweep_path"]
+            "emg_solve_adjoint", "emg_material_gradient", "emg_sweep_path", "emg_coarse_stats",
+            "emg_coarse_schur_rows"]
 NOALLOC_MAX_CELLS = 262144
 
 
@@ -122,6 +127,14 @@ class Params:
     level_alpha: object = None       # per-level shift list (entries <= 0 mean `alpha`)
     smoother: int = 0                # VANKA_FULL or VANKA_ECONOMIC
     sweep_path: int = 0              # SWEEP_AUTO (timed per level at creation) or a forced SWEEP_* path
+    # COARSE_KACZMARZ (0: the paper's value -- boxes of 2 cells, 10 steps, damping 0.8, drop 0.1,
+    # FGMRES(5), at most 250 Kaczmarz steps)
+    kaczmarz_box: object = 0         # cells per axis: an int or one per axis
+    kaczmarz_steps: int = 0
+    kaczmarz_damping: float = 0.0
+    coarse_tol: float = 0.0
+    coarse_restart: int = 0
+    kaczmarz_max: int = 0
 
     def to_c(self) -> _Params:
         p = _Params()
@@ -142,6 +155,11 @@ class Params:
             p.level_alpha[l] = float(la[l]) if l < len(la) else 0.0
         p.smoother = int(self.smoother)
         p.sweep_path = int(self.sweep_path)
+        kb = list(self.kaczmarz_box) if np.ndim(self.kaczmarz_box) else [int(self.kaczmarz_box)] * 3
+        for a in range(3):
+            p.kaczmarz_box[a] = int(kb[a]) if a < len(kb) else 0
+        p.kaczmarz_steps, p.kaczmarz_damping = int(self.kaczmarz_steps), float(self.kaczmarz_damping)
+        p.coarse_tol, p.coarse_restart, p.kaczmarz_max = float(self.coarse_tol), int(self.coarse_restart), int(self.kaczmarz_max)
         return p
 
 
@@ -149,7 +167,7 @@ def params_from_workload(w, cycle_precision=32, **over) -> Params:
     kw = dict(n=tuple(w.n), h=w.h, omega=w.omega, gamma=w.gamma, alpha=w.alpha, beta=w.beta,
               abl_cells=w.abl_cells, abl_gamma_max=w.abl_gamma_max, levels=w.levels, nu_pre=w.nu_pre,
               nu_post=w.nu_post, damping=w.damping,
-              coarse_solver=COARSE_DENSE if w.coarse == "dense" else COARSE_SMOOTH,
+              coarse_solver={"dense": COARSE_DENSE, "smooth": COARSE_SMOOTH, "kaczmarz": COARSE_KACZMARZ}[w.coarse],
               coarse_sweeps=w.coarse_sweeps, coarse_damping=w.coarse_damping, cycle_precision=cycle_precision,
               cycle_type={"V": CYCLE_V, "W": CYCLE_W, "K": CYCLE_K}[getattr(w, "cycle", "V")],
               level_alpha=w.level_alphas() if hasattr(w, "level_alphas") else None,
@@ -339,6 +357,24 @@ class Solver:
         self._out()
         return x
 
+    def coarse_stats(self):
+        """Last coarsest solve of COARSE_KACZMARZ: (FGMRES iterations, relative Schur residual,
+        Kaczmarz steps)."""
+        out = (ctypes.c_double * 3)()
+        _check(LIB.emg_coarse_stats(self.h, out))
+        return int(out[0]), float(out[1]), int(out[2])
+
+    def coarse_schur_rows(self):
+        """The stored Schur rows of COARSE_KACZMARZ as a complex numpy array (dim N_c, 75 or 17),
+        in the cycle precision (layout in include/emg.h)."""
+        last = self.params.levels - 1
+        cells = self._n(last) // (self.dim + 1)
+        ne = 75 if self.dim == 3 else 17
+        dt = np.complex64 if self.params.cycle_precision == 32 else np.complex128
+        out = np.zeros((self.dim * cells, ne), dtype=dt)
+        _check(LIB.emg_coarse_schur_rows(self.h, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
     def solve(self, b, x, tol=1e-6, max_iter=1000, restart=20, history_cap=0):
         import torch
         n = self._n()
@@ -418,8 +454,10 @@ class Solver:
             out["history"] = [hist[i] for i in range(st.history_len)]
         return out
 
-    def profile(self, enable=True):
-        _check(LIB.emg_profile(self.h, 1 if enable else 0))
+    def profile(self, enable=True, coarse=False):
+        """Per-class CUDA-event timing of the finest level's kernels; coarse=True also times every
+        kernel of the coarser levels (class K_COARSE)."""
+        _check(LIB.emg_profile(self.h, (2 if coarse else 1) if enable else 0))
 
     def profile_read(self, cls):
         ms, n, by = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()

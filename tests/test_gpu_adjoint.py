@@ -42,6 +42,36 @@ def test_adjoint_apply_matches_the_oracle(case):
     s.close()
 
 
+@pytest.mark.slow
+def test_adjoint_apply_at_128_cubed_on_sampled_windows():
+    """H^H x of the 3D inversion setting (128^3, float-float on the forward apply's coefficients)
+    on sampled windows: H^H is as local as H, so the oracle's conjugate transpose on a window
+    with a 6-cell margin reproduces the window's interior rows."""
+    import torch
+    w = config_c5_adjoint(128)
+    pb = oracle_problem(w)
+    s = gpu_solver(w, 32)
+    x = _rand(pb, 5)
+    xt = to_gpu(x, 64)
+    yt = torch.empty_like(xt)
+    s.apply_adjoint(xt, yt)
+    y = to_np(yt)
+    size, margin = 16, 6
+    ymax = np.abs(y).max()
+    for lo in ((0, 0, 0), (56, 56, 56), (112, 40, 0), (112, 112, 112)):
+        hi = tuple(l + size for l in lo)
+        wp = oracle.window(pb, lo, hi)
+        sl = (slice(None),) + tuple(slice(lo[a], hi[a]) for a in (2, 1, 0))
+        xw = x[sl]
+        yw = (oracle.assemble(wp, 0.0).conj().T @ xw.ravel()).reshape(xw.shape)
+        inner = tuple(slice(0 if lo[a] == 0 else margin, size - (0 if hi[a] == 128 else margin)) for a in (2, 1, 0))
+        glob = tuple(slice(lo[a] + inner[2 - a].start, lo[a] + inner[2 - a].stop) for a in (2, 1, 0))
+        got = y[(slice(None),) + glob]
+        ref = yw[(slice(None),) + inner]
+        assert np.abs(got - ref).max() <= 1e-12 * ymax, lo
+    s.close()
+
+
 @pytest.mark.parametrize("case", list(CASES))
 def test_material_gradient_kernel_matches_the_oracle(case):
     w = _w(case)

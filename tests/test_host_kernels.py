@@ -326,3 +326,30 @@ def test_host_tiled_residual_restriction_matches_the_oracle(hc, case, level, ty)
     assert hc.emg_hc_resid_restrict_tiled(*head[1:], _cvec(bb), _cvec(xx), _cvec(bc), ty) == 0
     assert np.all(np.isfinite(bc))
     assert np.abs(bc - ref).max() <= 2e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n,abl,shift", [((40, 24), 4, 0.0), ((17, 11), 2, 0.3), ((12, 12), 0, 0.0)])
+@pytest.mark.parametrize("x32", [0, 1])
+def test_host_2d_float_float_apply_matches_the_oracle(hc, n, abl, shift, x32):
+    """y = H x (or H_s x) in double-FP32 arithmetic, the rows factored into exact differences of
+    the inputs weighted by mu and the spread weights (csrc/apply_ff2d.cuh), against the oracle's
+    assembled operator in FP64: x in FP64, or rounded to FP32 as the cycle's output is."""
+    w = small_heterogeneous(n, seed=9, levels=1, abl_cells=max(abl, 1), sigma_cells=2.0)
+    pb = oracle_problem(w)
+    if abl == 0:
+        pb = replace(pb, abl_length=0.0)
+    x = random_field(pb, 71).ravel()
+    if x32:
+        x = x.astype(np.complex64).astype(np.complex128)
+    ref = oracle.assemble(pb, shift) @ x
+    nn = np.array(n, dtype=np.int32)
+    mats = [np.ascontiguousarray(a.ravel()) for a in (pb.lam, pb.mu, pb.rho)]
+    y = np.zeros_like(ref)
+    xx = np.ascontiguousarray(x)
+    assert hc.emg_hc_apply_ff2(nn.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.c_double(pb.h),
+                               ctypes.c_double(pb.beta), ctypes.c_double(pb.omega), ctypes.c_double(pb.gamma),
+                               ctypes.c_double(shift), ctypes.c_double(pb.abl_length),
+                               ctypes.c_double(pb.abl_gamma_max), *[m.ctypes.data_as(DP) for m in mats], _cvec(xx),
+                               _cvec(y), x32) == 0
+    act = oracle.active_mask(pb)
+    assert np.abs((y - ref) * act).max() <= 1e-12 * np.abs(ref).max()

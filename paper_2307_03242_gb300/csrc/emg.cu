@@ -1458,7 +1458,8 @@ void check_params(const emg_params* p) {
   if (p->coarse_solver == EMG_COARSE_KACZMARZ) {
     const KzCfg k = kz_cfg(*p);
     for (int a = 0; a < 3; ++a)
-      if (p->kaczmarz_box[a] < 0 || k.box[a] > 64) raise(EMG_ERR_INVALID, "kaczmarz_box out of range (0 or 1..64)");
+      if (p->kaczmarz_box[a] < 0 || k.box[a] < 2 || k.box[a] > 64)
+        raise(EMG_ERR_INVALID, "kaczmarz_box out of range (0 or 2..64)");
     if (p->kaczmarz_steps < 0 || p->coarse_restart < 0 || p->kaczmarz_max < 0 || k.restart > kz::MAXM)
       raise(EMG_ERR_INVALID, "kaczmarz_steps, kaczmarz_max must be >= 0 and coarse_restart in 0..8");
     if (!std::isfinite(p->kaczmarz_damping) || p->kaczmarz_damping < 0.0 || k.damping >= 2.0)
@@ -1468,7 +1469,8 @@ void check_params(const emg_params* p) {
     for (int a = 0; a < p->dim; ++a) nc[a] = p->n[a] / div;
     const kz::Boxes B = kz::make_boxes(p->dim, nc, k.box);
     const size_t cb = p->cycle_precision == 32 ? 8 : 16;
-    if ((size_t)B.RS * cb > 200 * 1024) raise(EMG_ERR_INVALID, "kaczmarz_box too large for shared memory");
+    if (2 * (size_t)kz::half_warp_smem(B, p->dim) * cb > 200 * 1024)
+      raise(EMG_ERR_INVALID, "kaczmarz_box too large for shared memory");
   }
   if (p->coarse_solver == EMG_COARSE_SMOOTH && p->coarse_sweeps < 1 && p->levels > 0)
     raise(EMG_ERR_INVALID, "coarse_sweeps must be >= 1");

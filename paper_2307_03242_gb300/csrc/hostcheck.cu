@@ -392,8 +392,8 @@ long kz_steps_host(const kz::Boxes& B, const cx<double>* coef, const cx<double>*
                    double w) {
   constexpr int NE = kz::Shape<D>::NE, SL = kz::Shape<D>::SL;
   const size_t N = (size_t)B.n[0] * B.n[1] * B.n[2];
-  std::vector<kz::LaneTab<D>> tab(32);
-  for (int lane = 0; lane < 32; ++lane) tab[lane].init(B, lane);
+  std::vector<kz::LaneTab<D>> tab(kz::HW);
+  for (int lane = 0; lane < kz::HW; ++lane) tab[lane].init(B, lane);
   std::vector<double> in2((size_t)D * N);
   for (size_t r = 0; r < in2.size(); ++r) in2[r] = kz::inv_row_norm<double, D>(coef, r);
   std::vector<cx<double>> copies((size_t)B.nboxes * B.RS), reg(B.RS);
@@ -418,8 +418,8 @@ long kz_steps_host(const kz::Boxes& B, const cx<double>* coef, const cx<double>*
               const size_t r = (size_t)c * N + kz::cell_of(B.n, D, k[0], k[1], k[2]);
               if (in2[r] == 0.0) continue;
               cx<double> dot = czero<double>();
-              std::vector<int> idx(32 * SL, -1);
-              for (int lane = 0; lane < 32; ++lane)
+              std::vector<int> idx(kz::HW * SL, -1);
+              for (int lane = 0; lane < kz::HW; ++lane)
                 for (int t = 0; t < SL; ++t) {
                   const int pk = tab[lane].get(c, t);
                   if (pk < 0) continue;
@@ -434,13 +434,13 @@ long kz_steps_host(const kz::Boxes& B, const cx<double>* coef, const cx<double>*
                     continue;
                   }
                   idx[lane * SL + t] = id;
-                  dot = dot + coef[r * NE + lane + 32 * t] * reg[id];
+                  dot = dot + coef[r * NE + lane + kz::HW * t] * reg[id];
                 }
               const cx<double> sc = (w * in2[r]) * (rhs[r] - dot);
-              for (int lane = 0; lane < 32; ++lane)
+              for (int lane = 0; lane < kz::HW; ++lane)
                 for (int t = 0; t < SL; ++t) {
                   const int id = idx[lane * SL + t];
-                  if (id >= 0) reg[id] = reg[id] + sc * cconj(coef[r * NE + lane + 32 * t]);
+                  if (id >= 0) reg[id] = reg[id] + sc * cconj(coef[r * NE + lane + kz::HW * t]);
                 }
             }
       std::copy(reg.begin(), reg.end(), copies.begin() + (size_t)bx * B.RS);
@@ -455,6 +455,8 @@ long kz_steps_host(const kz::Boxes& B, const cx<double>* coef, const cx<double>*
       }
       int blo[3], bhi[3];
       kz::reach_boxes(B, c2, m, blo, bhi);
+      for (int a = 0; a < 3; ++a)
+        if (bhi[a] - blo[a] > 2) ++bad;  // the kernel takes at most 3 boxes per axis
       cx<double> acc = czero<double>();
       int cnt = 0;
       for (int bz = blo[2]; bz <= bhi[2]; ++bz)

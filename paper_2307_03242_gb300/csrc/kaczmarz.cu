@@ -32,11 +32,13 @@ cudaError_t probe_all(const Grid<T>& g, cx<T>* coef, T* inv_n2, cx<T>* e, cx<T>*
 
 template <typename T, int D>
 cudaError_t plan_solve(int sms, int RS, KzLaunch& out) {
-  const size_t per_warp = (size_t)RS * sizeof(cx<T>);
-  int warps = (int)(kRegionBudget / per_warp);
-  if (warps > kz::NW) warps = kz::NW;
-  if (warps < 1) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)warps * per_warp;
+  // half-warps with a private region: as many as fit, an even number (both halves of a warp)
+  const size_t per_hw = (size_t)(RS + kz::PD * kz::Ring<D>::SLOT) * sizeof(cx<T>);
+  int warps = (int)(kRegionBudget / per_hw);
+  if (warps > kz::NT / kz::HW) warps = kz::NT / kz::HW;
+  warps &= ~1;
+  if (warps < 2) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)warps * per_hw;
   static std::atomic<bool> attr_set[kMaxDev];
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);

@@ -21,9 +21,10 @@
 //
 // GPU mapping: one block per SM, all blocks co-resident (cooperative launch), meeting at a
 // grid-wide barrier whose waits are bounded (a timeout sets bit 1 of the status word and every
-// block returns). A box is swept by one warp: lanes take the row's entries, the row's dot product
-// is a butterfly reduction (every lane ends with the same bits), and the private copy lives in
-// shared memory. Dot products accumulate in FP64 and are summed over blocks in a fixed order, so
+// block returns). A box is swept by one half-warp (two boxes per warp, in lock-step: a row that
+// one half lacks is a zero row there): its 16 lanes take the row's entries, the row's dot product
+// is a butterfly reduction (every lane ends with the same bits), the next rows' entries are
+// loaded two rows ahead, and the private copy lives in shared memory. Dot products accumulate in FP64 and are summed over blocks in a fixed order, so
 // the solve is deterministic; the Hessenberg matrix and rotations are FP64, computed identically
 // by every block. The index helpers are __host__ __device__ so that the host can check them.
 #pragma once
@@ -33,7 +34,7 @@
 
 namespace kz {
 
-constexpr int NT = 1024, NW = NT / 32;
+constexpr int NT = 512, NW = NT / 32, HW = 16;  // threads, warps per block; lanes per box
 constexpr int MAXM = 8;          // largest restart length
 constexpr int PER = 4;           // probe period per axis
 constexpr long long WAIT_CYCLES = 4000000000LL;  // bound of one barrier wait (about 2 s)
@@ -41,7 +42,7 @@ constexpr long long WAIT_CYCLES = 4000000000LL;  // bound of one barrier wait (a
 template <int D>
 struct Shape {
   static constexpr int NE = D == 3 ? 75 : 17;  // Schur row entries
-  static constexpr int SL = (NE + 31) / 32;    // entries per lane
+  static constexpr int SL = (NE + HW - 1) / HW;  // entries per lane of a half-warp
 };
 
 // Footprint of a row of component c in component c2 along axis a: [foot_lo, 1].
@@ -248,7 +249,7 @@ struct Args {
   Grid<T> g;                 // the coarsest level's operator H_s
   Boxes B;                   // sub-region boxes
   size_t N;                  // cells
-  int warps_a;               // warps per block that own a region in shared memory
+  int warps_a;               // half-warps per block that own a region in shared memory (even)
   const cx<T>* coef;         // D N rows x NE entries
   const T* inv_n2;           // 1 / ||row||^2 (0: no row)
   const cx<T>* b;            // (D+1) N right-hand side
@@ -391,17 +392,17 @@ __device__ __forceinline__ bool grid_sum(double re, double im, double* part, uns
   return true;
 }
 
-// Per-lane table of a row's entries: for component c and lane slot t (entry lane + 32 t), -1 (no
-// entry) or the packed entry: component c2 (bits 0-1), offsets + 2 (3 bits each from bit 2) and
-// the region position for the row cell at local (0, 0, 0) (from bit 11).
+// Per-lane table of a row's entries: for component c and slot t of half-warp lane l (entry
+// l + 16 t), -1 (no entry) or the packed entry: component c2 (bits 0-1), offsets + 2 (3 bits each
+// from bit 2) and the region position for the row cell at local (0, 0, 0) (from bit 11).
 template <int D>
 struct LaneTab {
   int pk[D][Shape<D>::SL];
-  HD void init(const Boxes& B, int lane) {
+  HD void init(const Boxes& B, int hl) {
     for (int c = 0; c < D; ++c)
       for (int t = 0; t < Shape<D>::SL; ++t) {
         int cc = -1, oo[3];
-        if (slot_decode<D>(c, lane + 32 * t, cc, oo))
+        if (slot_decode<D>(c, hl + HW * t, cc, oo))
           pk[c][t] = cc | (oo[0] + 2) << 2 | (oo[1] + 2) << 5 | (oo[2] + 2) << 8 | region_index(B, cc, oo, 0, 0, 0) << 11;
         else
           pk[c][t] = -1;
@@ -419,75 +420,173 @@ HD int pk_c2(int v) { return v & 3; }
 HD int pk_o(int v, int a) { return ((v >> (2 + 3 * a)) & 7) - 2; }
 HD int pk_off(int v) { return v >> 11; }
 
-// One sweep of every box: rhs -> copies, starting from xin (nullptr: zero).
+// Row q of a box in sweep order (component, then cells with x fastest) -> component and local cell.
+HD int box_row(const Boxes& B, int q, int l[3]) {
+  const int per = B.box[0] * B.box[1] * B.box[2];
+  const int c = q / per;
+  int r = q - c * per;
+  l[0] = r % B.box[0];
+  r /= B.box[0];
+  l[1] = r % B.box[1];
+  l[2] = r / B.box[1];
+  return c;
+}
+
+// Global row of box row q (lowest box cell lo), or -1 if the row is outside the grid or a
+// boundary face.
+HD long long box_row_global(const Boxes& B, int q, const int lo[3], int& c, int l[3]) {
+  c = box_row(B, q, l);
+  const int k[3] = {lo[0] + l[0], lo[1] + l[1], lo[2] + l[2]};
+  if (k[0] >= B.n[0] || k[1] >= B.n[1] || k[2] >= B.n[2] || k[c] < 1) return -1;
+  const size_t N = (size_t)B.n[0] * B.n[1] * B.n[2];
+  return (long long)((size_t)c * N + cell_of(B.n, B.dim, k[0], k[1], k[2]));
+}
+
+// Asynchronous global -> shared copies (cp.async; each thread's copies form groups that it
+// commits and waits for).
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Rows in flight per half-warp (the ring of row slots in shared memory after its region). A slot
+// holds the row's NE entries, its right-hand side and 1 / ||row||^2 (in the real part of one more
+// complex value).
+constexpr int PD = 4;
+template <int D>
+struct Ring {
+  static constexpr int SLOT = Shape<D>::NE + 2;  // complex values per slot
+};
+// Complex values of shared memory a half-warp uses: its region and its ring.
+HD int half_warp_smem(const Boxes& B, int D) { return B.RS + PD * ((D == 3 ? Shape<3>::NE : Shape<2>::NE) + 2); }
+
+// Starts the copy of box row q into ring slot `slot` (this lane's entries; lane 0 also the
+// right-hand side and the norm), or zero-fills the slot for a missing row; commits one group.
+template <typename T, int D>
+__device__ __forceinline__ void stage_row(const Args<T>& a, const LaneTab<D>& tab, const cx<T>* rhs, bool live,
+                                          const int lo[3], int q, int Q, int hl, cx<T>* slot) {
+  constexpr int NE = Shape<D>::NE, SL = Shape<D>::SL;
+  if (q < Q) {
+    int c, l[3];
+    const long long r = live ? box_row_global(a.B, q, lo, c, l) : -1;
+    if (r >= 0) {
+#pragma unroll
+      for (int t = 0; t < SL; ++t)
+        if (hl + HW * t < NE) cp_async(slot + hl + HW * t, a.coef + (size_t)r * NE + hl + HW * t, (int)sizeof(cx<T>));
+      if (hl == 0) {
+        cp_async(slot + NE, rhs + r, (int)sizeof(cx<T>));
+        cp_async(&slot[NE + 1].re, a.inv_n2 + r, (int)sizeof(T));
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < SL; ++t)
+        if (hl + HW * t < NE) slot[hl + HW * t] = czero<T>();
+      if (hl == 0) {
+        slot[NE] = czero<T>();
+        slot[NE + 1] = czero<T>();
+      }
+    }
+  }
+  cp_commit();
+}
+
+// One sweep of every box: rhs -> copies, starting from xin (nullptr: zero). Half-warp h of the
+// grid takes boxes h, h + nhw, ...; both halves of a warp run the same number of box rounds.
+// reg: the half-warp's region, followed by its ring of PD row slots.
 template <typename T, int D>
 __device__ void sweep_boxes(const Args<T>& a, const LaneTab<D>& tab, const cx<T>* rhs, const cx<T>* xin, cx<T>* reg,
-                            int gw, int nwa) {
-  constexpr int NE = Shape<D>::NE, SL = Shape<D>::SL;
-  const int lane = threadIdx.x & 31;
+                            int ghw, int nhw) {
+  constexpr int NE = Shape<D>::NE, SL = Shape<D>::SL, SLOT = Ring<D>::SLOT;
+  const int hl = threadIdx.x & (HW - 1);
   const Boxes& B = a.B;
   const size_t N = a.N;
-  for (int bx = gw; bx < B.nboxes; bx += nwa) {
-    int lo[3];
-    box_lo(B, bx, lo);
-    for (int t = lane; t < B.RS; t += 32) {
-      cx<T> v = czero<T>();
-      if (xin) {
-        int m[3];
-        const int c2 = region_cell(B, t, lo, m);
-        bool in = true;
-        for (int q = 0; q < D; ++q) in = in && m[q] >= 0 && m[q] < B.n[q];
-        if (in && m[c2] >= 1) v = ldcg(xin + (size_t)c2 * N + cell_of(B.n, D, m[0], m[1], m[2]));
+  cx<T>* ring = reg + B.RS;
+  const int Q = D * B.box[0] * B.box[1] * B.box[2];
+  const int ghw0 = ghw & ~1;  // the warp's first half-warp: both halves run the same rounds
+  for (int rd_i = 0; ghw0 + rd_i * nhw < B.nboxes; ++rd_i) {
+    const int bx = ghw + rd_i * nhw;
+    const bool live = bx < B.nboxes;
+    int lo[3] = {0, 0, 0};
+    if (live) box_lo(B, bx, lo);
+    // the first PD - 1 rows start copying while the region loads
+    for (int q = 0; q < PD - 1; ++q) stage_row<T, D>(a, tab, rhs, live, lo, q, Q, hl, ring + q * SLOT);
+    // the region from xin, 8 independent loads in flight per lane
+    for (int t0 = hl; t0 < B.RS; t0 += 8 * HW) {
+      cx<T> v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = t0 + u * HW;
+        v[u] = czero<T>();
+        if (live && xin && t < B.RS) {
+          int m[3];
+          const int c2 = region_cell(B, t, lo, m);
+          bool in = true;
+          for (int q = 0; q < D; ++q) in = in && m[q] >= 0 && m[q] < B.n[q];
+          if (in && m[c2] >= 1) v[u] = ldcg(xin + (size_t)c2 * N + cell_of(B.n, D, m[0], m[1], m[2]));
+        }
       }
-      reg[t] = v;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (t0 + u * HW < B.RS) reg[t0 + u * HW] = v[u];
     }
-    __syncwarp();
-    for (int c = 0; c < D; ++c)
-      for (int lz = 0; lz < B.box[2]; ++lz)
-        for (int ly = 0; ly < B.box[1]; ++ly)
-          for (int lx = 0; lx < B.box[0]; ++lx) {
-            const int k[3] = {lo[0] + lx, lo[1] + ly, lo[2] + lz};
-            if (k[0] >= B.n[0] || k[1] >= B.n[1] || k[2] >= B.n[2] || k[c] < 1) continue;
-            const size_t r = (size_t)c * N + cell_of(B.n, D, k[0], k[1], k[2]);
-            const T in2 = __ldg(a.inv_n2 + r);
-            if (in2 == T(0)) continue;
-            cx<T> co[SL];
-            int idx[SL];
-            T sr = T(0), si = T(0);
+    for (int q = 0; q < Q; ++q) {
+      stage_row<T, D>(a, tab, rhs, live, lo, q + PD - 1, Q, hl, ring + ((q + PD - 1) % PD) * SLOT);
+      cp_wait<PD - 1>();  // this lane's copies of row q have landed
+      __syncwarp();       // ... and every lane's (the right-hand side and norm come from lane 0)
+      const cx<T>* sl = ring + (q % PD) * SLOT;
+      int l[3];
+      const int c = box_row(B, q, l);
+      int idx[SL];
+      cx<T> co[SL];
+      T sr = T(0), si = T(0);
 #pragma unroll
-            for (int t = 0; t < SL; ++t) {
-              const int pk = tab.get(c, t);
-              idx[t] = -1;
-              co[t] = czero<T>();
-              if (pk >= 0) {
-                const int cc = pk_c2(pk);
-                co[t] = ldg(a.coef + r * NE + lane + 32 * t);
-                idx[t] = pk_off(pk) + (lz * B.ry[cc] + ly) * B.rx[cc] + lx;
-                const cx<T> xv = reg[idx[t]];
-                sr += co[t].re * xv.re - co[t].im * xv.im;
-                si += co[t].re * xv.im + co[t].im * xv.re;
-              }
-            }
+      for (int t = 0; t < SL; ++t) {
+        const int pk = tab.get(c, t);
+        idx[t] = -1;
+        co[t] = czero<T>();
+        if (pk >= 0) {
+          const int cc = pk_c2(pk);
+          idx[t] = pk_off(pk) + (l[2] * B.ry[cc] + l[1]) * B.rx[cc] + l[0];
+          co[t] = sl[hl + HW * t];
+          const cx<T> xv = reg[idx[t]];
+          sr += co[t].re * xv.re - co[t].im * xv.im;
+          si += co[t].re * xv.im + co[t].im * xv.re;
+        }
+      }
 #pragma unroll
-            for (int m = 16; m >= 1; m >>= 1) {
-              sr += __shfl_xor_sync(0xffffffffu, sr, m);
-              si += __shfl_xor_sync(0xffffffffu, si, m);
-            }
-            const cx<T> bv = ldcg(rhs + r);
-            const T s_re = a.damping * in2 * (bv.re - sr), s_im = a.damping * in2 * (bv.im - si);
+      for (int m = HW / 2; m >= 1; m >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, m);
+        si += __shfl_xor_sync(0xffffffffu, si, m);
+      }
+      const cx<T> bv = sl[NE];
+      const T in2 = sl[NE + 1].re;
+      const T s_re = a.damping * in2 * (bv.re - sr), s_im = a.damping * in2 * (bv.im - si);
 #pragma unroll
-            for (int t = 0; t < SL; ++t) {
-              if (idx[t] >= 0) {  // += s conj(a)
-                cx<T> v = reg[idx[t]];
-                v.re += s_re * co[t].re + s_im * co[t].im;
-                v.im += s_im * co[t].re - s_re * co[t].im;
-                reg[idx[t]] = v;
-              }
-            }
-            __syncwarp();
-          }
-    cx<T>* out = a.copies + (size_t)bx * B.RS;
-    for (int t = lane; t < B.RS; t += 32) st_cg(out + t, reg[t]);
+      for (int t = 0; t < SL; ++t) {
+        if (idx[t] >= 0) {  // += s conj(a)
+          cx<T> v = reg[idx[t]];
+          v.re += s_re * co[t].re + s_im * co[t].im;
+          v.im += s_im * co[t].re - s_re * co[t].im;
+          reg[idx[t]] = v;
+        }
+      }
+      __syncwarp();  // the region's updates and the slot's reads are done before the slot refills
+    }
+    cp_wait<0>();
+    if (live) {
+      cx<T>* out = a.copies + (size_t)bx * B.RS;
+      for (int t = hl; t < B.RS; t += HW) st_cg(out + t, reg[t]);
+    }
     __syncwarp();
   }
 }
@@ -507,35 +606,53 @@ __device__ void average(const Args<T>& a, cx<T>* out, size_t tid, size_t nthr) {
     }
     int blo[3], bhi[3];
     reach_boxes(B, c2, m, blo, bhi);
+    // every candidate box's copy loaded before any is summed (independent loads), then summed
+    // in box order
+    cx<T> v[27];
+    constexpr int NZ = D == 3 ? 3 : 1;
+#pragma unroll
+    for (int dz = 0; dz < NZ; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const int bz = blo[2] + dz, by = blo[1] + dy, bxx = blo[0] + dx;
+          const int u = (dz * 3 + dy) * 3 + dx;
+          v[u] = czero<T>();
+          if (bz <= bhi[2] && by <= bhi[1] && bxx <= bhi[0]) {
+            const int box = (bz * B.nb[1] + by) * B.nb[0] + bxx;
+            v[u] = ldcg(a.copies + (size_t)box * B.RS + reach_local(B, c2, m, bxx, by, bz));
+          }
+        }
     T sr = T(0), si = T(0);
     int cnt = 0;
-    for (int bz = blo[2]; bz <= bhi[2]; ++bz)
-      for (int by = blo[1]; by <= bhi[1]; ++by)
-        for (int bxx = blo[0]; bxx <= bhi[0]; ++bxx) {
-          const int box = (bz * B.nb[1] + by) * B.nb[0] + bxx;
-          const cx<T> v = ldcg(a.copies + (size_t)box * B.RS + reach_local(B, c2, m, bxx, by, bz));
-          sr += v.re;
-          si += v.im;
-          ++cnt;
-        }
+#pragma unroll
+    for (int dz = 0; dz < NZ; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx)
+          if (blo[2] + dz <= bhi[2] && blo[1] + dy <= bhi[1] && blo[0] + dx <= bhi[0]) {
+            const cx<T> w = v[(dz * 3 + dy) * 3 + dx];
+            sr += w.re;
+            si += w.im;
+            ++cnt;
+          }
     out[q] = mkc<T>(sr / T(cnt), si / T(cnt));
   }
 }
 
-// w = S z (or rhs - S z), one row per warp; adds this thread's share of sum conj(v) w (v given)
-// or of |w|^2 (v == nullptr) to (dre, dim_).
+// S z at row r (or 0 for r < 0) as this half-warp's lanes' shares summed over the half-warp.
 template <typename T, int D>
-__device__ void matvec(const Args<T>& a, const LaneTab<D>& tab, const cx<T>* z, const cx<T>* rhs, cx<T>* w,
-                       const cx<T>* v, double& dre, double& dim_, int gwall, int nwall) {
+__device__ __forceinline__ cx<T> row_dot(const Args<T>& a, const LaneTab<D>& tab, const cx<T>* z, long long r, int hl) {
   constexpr int NE = Shape<D>::NE, SL = Shape<D>::SL;
-  const int lane = threadIdx.x & 31;
   const Boxes& B = a.B;
   const size_t N = a.N;
-  for (size_t r = gwall; r < (size_t)D * N; r += nwall) {
+  T sr = T(0), si = T(0);
+  if (r >= 0) {
     const int c = (int)(r / N);
     const size_t cell = r % N;
     const int k[3] = {(int)(cell % B.n[0]), (int)((cell / B.n[0]) % B.n[1]), D == 3 ? (int)(cell / ((size_t)B.n[0] * B.n[1])) : 0};
-    T sr = T(0), si = T(0);
     if (k[c] >= 1) {
 #pragma unroll
       for (int t = 0; t < SL; ++t) {
@@ -546,30 +663,53 @@ __device__ void matvec(const Args<T>& a, const LaneTab<D>& tab, const cx<T>* z, 
         bool in = true;
         for (int q = 0; q < D; ++q) in = in && m[q] >= 0 && m[q] < B.n[q];
         if (!in) continue;
-        const cx<T> co = ldg(a.coef + r * NE + lane + 32 * t);
+        const cx<T> co = ldg(a.coef + (size_t)r * NE + hl + HW * t);
         const cx<T> zv = ldcg(z + (size_t)cc * N + cell_of(B.n, D, m[0], m[1], m[2]));
         sr += co.re * zv.re - co.im * zv.im;
         si += co.re * zv.im + co.im * zv.re;
       }
     }
+  }
 #pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) {
-      sr += __shfl_xor_sync(0xffffffffu, sr, m);
-      si += __shfl_xor_sync(0xffffffffu, si, m);
-    }
-    cx<T> wv = mkc<T>(sr, si);
-    if (rhs) {
-      const cx<T> bv = ldcg(rhs + r);
-      wv = mkc<T>(bv.re - sr, bv.im - si);
-    }
-    if (lane == 0) {
-      st_cg(w + r, wv);
-      if (v) {
-        const cx<T> vv = ldcg(v + r);
-        dre += (double)vv.re * wv.re + (double)vv.im * wv.im;
-        dim_ += (double)vv.re * wv.im - (double)vv.im * wv.re;
-      } else {
-        dre += (double)wv.re * wv.re + (double)wv.im * wv.im;
+  for (int m = HW / 2; m >= 1; m >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, m);
+    si += __shfl_xor_sync(0xffffffffu, si, m);
+  }
+  return mkc<T>(sr, si);
+}
+
+// w = S z (or rhs - S z), one row per half-warp and two rows in flight; adds this thread's share
+// of sum conj(v) w (v given) or of |w|^2 (v == nullptr) to (dre, dim_).
+template <typename T, int D>
+__device__ void matvec(const Args<T>& a, const LaneTab<D>& tab, const cx<T>* z, const cx<T>* rhs, cx<T>* w,
+                       const cx<T>* v, double& dre, double& dim_, int ghw, int nhw) {
+  const int hl = threadIdx.x & (HW - 1);
+  const long long rows = (long long)D * a.N;
+  const long long per = 2LL * nhw;
+  const long long ghw0 = ghw & ~1;
+  for (long long base = 0; base + ghw0 < rows; base += per) {
+    const long long r0 = base + ghw, r1 = base + nhw + ghw;
+    const long long q0 = r0 < rows ? r0 : -1, q1 = r1 < rows ? r1 : -1;
+    const cx<T> s0 = row_dot<T, D>(a, tab, z, q0, hl);
+    const cx<T> s1 = row_dot<T, D>(a, tab, z, q1, hl);
+    if (hl == 0) {
+      const long long qq[2] = {q0, q1};
+      const cx<T> ss[2] = {s0, s1};
+      for (int u = 0; u < 2; ++u) {
+        if (qq[u] < 0) continue;
+        cx<T> wv = ss[u];
+        if (rhs) {
+          const cx<T> bv = ldcg(rhs + qq[u]);
+          wv = mkc<T>(bv.re - wv.re, bv.im - wv.im);
+        }
+        st_cg(w + qq[u], wv);
+        if (v) {
+          const cx<T> vv = ldcg(v + qq[u]);
+          dre += (double)vv.re * wv.re + (double)vv.im * wv.im;
+          dim_ += (double)vv.re * wv.im - (double)vv.im * wv.re;
+        } else {
+          dre += (double)wv.re * wv.re + (double)wv.im * wv.im;
+        }
       }
     }
   }
@@ -579,15 +719,16 @@ template <typename T, int D>
 __global__ void __launch_bounds__(NT, 1) solve(Args<T> a) {
   extern __shared__ __align__(16) unsigned char kz_smem[];
   __shared__ Shared sh;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  cx<T>* reg = reinterpret_cast<cx<T>*>(kz_smem) + (size_t)(wib < a.warps_a ? wib : 0) * a.B.RS;
+  const int hwb = threadIdx.x / HW;  // half-warp in the block
+  // a.warps_a counts half-warps that own a private region (an even number)
+  cx<T>* reg = reinterpret_cast<cx<T>*>(kz_smem) + (size_t)(hwb < a.warps_a ? hwb : 0) * half_warp_smem(a.B, D);
   const size_t tid = (size_t)blockIdx.x * NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
-  const int gwall = blockIdx.x * NW + wib, nwall = gridDim.x * NW;
-  const int gwa = blockIdx.x * a.warps_a + wib, nwa = gridDim.x * a.warps_a;
+  const int ghw_all = blockIdx.x * (NT / HW) + hwb, nhw_all = gridDim.x * (NT / HW);
+  const int ghw_a = blockIdx.x * a.warps_a + hwb, nhw_a = gridDim.x * a.warps_a;
   const size_t N = a.N, DN = (size_t)D * N;
   const Grid<T>& g = a.g;
   LaneTab<D> tab;
-  tab.init(a.B, lane);
+  tab.init(a.B, threadIdx.x & (HW - 1));
   int parity = 0;
   cx<double> red;
 
@@ -621,14 +762,14 @@ __global__ void __launch_bounds__(NT, 1) solve(Args<T> a) {
         if (!grid_sync(a.bar, a.err, &sh.ok)) return;
         // Z_j = K(V_j): Kaczmarz steps from zero
         for (int s = 0; s < a.steps; ++s) {
-          if (wib < a.warps_a) sweep_boxes<T, D>(a, tab, Vj, s == 0 ? nullptr : Zj, reg, gwa, nwa);
+          if (hwb < a.warps_a) sweep_boxes<T, D>(a, tab, Vj, s == 0 ? nullptr : Zj, reg, ghw_a, nhw_a);
           if (!grid_sync(a.bar, a.err, &sh.ok)) return;
           average<T, D>(a, Zj, tid, nthr);
           if (!grid_sync(a.bar, a.err, &sh.ok)) return;
         }
         // w = S Z_j, h_0j = <V_0, w>
         double dre = 0.0, dim_ = 0.0;
-        matvec<T, D>(a, tab, Zj, nullptr, a.w, a.V, dre, dim_, gwall, nwall);
+        matvec<T, D>(a, tab, Zj, nullptr, a.w, a.V, dre, dim_, ghw_all, nhw_all);
         if (!grid_sum(dre, dim_, a.part, a.bar, a.err, sh, parity, red)) return;
         if (threadIdx.x == 0) sh.H[j] = red;
         __syncthreads();
@@ -712,7 +853,7 @@ __global__ void __launch_bounds__(NT, 1) solve(Args<T> a) {
       if (!grid_sync(a.bar, a.err, &sh.ok)) return;
       // true residual r = f - S u -> w, beta
       double dre = 0.0, dim_ = 0.0;
-      matvec<T, D>(a, tab, a.u, a.f, a.w, nullptr, dre, dim_, gwall, nwall);
+      matvec<T, D>(a, tab, a.u, a.f, a.w, nullptr, dre, dim_, ghw_all, nhw_all);
       if (!grid_sum(dre, 0.0, a.part, a.bar, a.err, sh, parity, red)) return;
       beta = sqrt(red.re);
       if (beta / bnorm > a.tol && its < a.max_its) {

@@ -76,6 +76,8 @@ def workload(name, args=None):
             v = getattr(args, k, None)
             if v is not None:
                 setattr(w, k, v)
+                if k == "alpha":
+                    w.level_alpha = None
         args.restart = w.restart
     return w
 
@@ -194,10 +196,12 @@ def oracle_sample(w, iters=3, crop=512):
         lv -= 1
     pb = Problem(n, w.h, w.omega, w.gamma, w.beta, w.lam[sl], w.mu[sl], w.rho[sl], abl_length=w.abl_cells * w.h,
                  abl_gamma_max=w.abl_gamma_max)
-    coarse = "dense" if (c >> (lv - 1)) ** d * (d + 1) <= 4096 and w.coarse == "dense" else "smooth"
-    alphas = [w.alpha] * lv
-    if w.alpha_coarsest > 0:
-        alphas[-1] = w.alpha_coarsest
+    if w.coarse == "kaczmarz":
+        coarse = "kaczmarz"
+    else:
+        coarse = "dense" if (c >> (lv - 1)) ** d * (d + 1) <= 4096 and w.coarse == "dense" else "smooth"
+    full = w.level_alphas()
+    alphas = full[:lv - 1] + [full[-1]]  # the crop's coarsest level keeps the coarsest shift
     hier = oracle.Hierarchy(pb, lv, alphas, w.damping, nu_pre=w.nu_pre, nu_post=w.nu_post, coarse=coarse,
                             coarse_sweeps=max(w.coarse_sweeps, 1), coarse_damping=w.coarse_damping, cycle=w.cycle)
     H = oracle.assemble(pb, 0.0)
@@ -260,7 +264,9 @@ def max_over_ranks(value, device=None):
 def config_json(w, args):
     return {"workload": w.name, "grid": "x".join(map(str, w.n)), "levels": w.levels, "cycle": "%s(%d,%d)" % (
         w.cycle, w.nu_pre, w.nu_post), "coarse_sweeps": w.coarse_sweeps, "alpha": w.alpha, "damping": w.damping, "beta": round(w.beta, 6),
-        "krylov": "FGMRES(%d)" % args.restart, "tol": w.tol, "coarsest": w.coarse,
+        "krylov": "FGMRES(%d)" % args.restart, "tol": w.tol, "coarsest": w.coarse if w.coarse != "kaczmarz" else
+        "hybrid Kaczmarz-GMRES: FGMRES(5) on the Schur complement, 10 steps at 0.8 over 2^d-cell boxes, 0.1 drop",
+        "shift_per_level": [round(v, 6) for v in w.level_alphas()],
         "l2": "inputs larger than L2 (vectors %d MB)" % int(16 * (w.dim + 1) * np.prod(w.n) / 2 ** 20),
         "parallelism": "replicas" if args.gpus > 1 else "single"}
 

@@ -33,7 +33,7 @@ class Hierarchy:
     def __init__(self, pb: Problem, levels: int, alpha: float, damping=None, nu_pre: int = 2,
                  nu_post: int = 2, coarse: str = "dense", coarse_sweeps: int = 0,
                  coarse_damping: float = 1.0, cycle: str = "V", smoother: str = "full",
-                 coarse_box=4, coarse_coloured: bool = False, coarse_tol: float = 0.1,
+                 coarse_box=2, coarse_coloured: bool = False, coarse_tol: float = 0.1,
                  coarse_steps: int = 10, coarse_kaczmarz_damping: float = 0.8, coarse_max_kaczmarz: int = 250):
         self.levels = levels
         self.cycle = cycle

@@ -925,7 +925,7 @@ void setup_kaczmarz(emg_ctx& c) {
   c.kz_V.alloc((size_t)(k.restart + 1) * DN * cb);
   c.kz_Z.alloc((size_t)k.restart * DN * cb);
   c.kz_copies.alloc((size_t)c.kz_B.nboxes * c.kz_B.RS * cb);
-  CK(plan_kz_solve<T>(d, c.sms, c.kz_B.RS, c.kz_launch));
+  CK(plan_kz_solve<T>(d, c.sms, c.kz_B.RS, c.kz_B.box, c.kz_launch));
   c.kz_part.alloc((size_t)4 * c.kz_launch.blocks * sizeof(double));
   c.kz_bar.alloc(2 * sizeof(unsigned));
   CK(cudaMemset(c.kz_bar.p, 0, c.kz_bar.bytes));
@@ -1469,7 +1469,7 @@ void check_params(const emg_params* p) {
     for (int a = 0; a < p->dim; ++a) nc[a] = p->n[a] / div;
     const kz::Boxes B = kz::make_boxes(p->dim, nc, k.box);
     const size_t cb = p->cycle_precision == 32 ? 8 : 16;
-    if (2 * (size_t)kz::half_warp_smem(B, p->dim) * cb > 200 * 1024)
+    if (2 * (size_t)kz::half_warp_smem(B, p->dim) * cb + 4 * (size_t)B.RS + 16 > 200 * 1024)
       raise(EMG_ERR_INVALID, "kaczmarz_box too large for shared memory");
   }
   if (p->coarse_solver == EMG_COARSE_SMOOTH && p->coarse_sweeps < 1 && p->levels > 0)

@@ -402,20 +402,39 @@ long kz_steps_host(const kz::Boxes& B, const cx<double>* coef, const cx<double>*
     for (int bx = 0; bx < B.nboxes; ++bx) {
       int lo[3];
       kz::box_lo(B, bx, lo);
+      // the region through the kernel's layout table (kz::region_code), checked against region_cell
       for (int t = 0; t < B.RS; ++t) {
         int m[3];
         const int c2 = kz::region_cell(B, t, lo, m);
+        const int code = kz::region_code(B, t);
+        const int cc = code & 3;
+        const int mm[3] = {lo[0] - kz::reach_lo(cc, 0) + ((code >> 2) & 255), lo[1] - kz::reach_lo(cc, 1) + ((code >> 10) & 255),
+                           D == 3 ? lo[2] - kz::reach_lo(cc, 2) + ((code >> 18) & 255) : 0};
+        if (cc != c2 || mm[0] != m[0] || mm[1] != m[1] || mm[2] != m[2]) ++bad;
         bool in = true;
         for (int a = 0; a < D; ++a) in = in && m[a] >= 0 && m[a] < B.n[a];
         reg[t] = (in && m[c2] >= 1) ? x[(size_t)c2 * N + kz::cell_of(B.n, D, m[0], m[1], m[2])] : czero<double>();
       }
-      for (int c = 0; c < D; ++c)
-        for (int lz = 0; lz < B.box[2]; ++lz)
-          for (int ly = 0; ly < B.box[1]; ++ly)
-            for (int lx = 0; lx < B.box[0]; ++lx) {
+      // rows in the kernel's order: an odometer cursor (the boxes-of-2 and general variants)
+      kz::Cursor cu, cu2;
+      const int Q = D * B.box[0] * B.box[1] * B.box[2];
+      const bool two = B.box[0] == 2 && B.box[1] == 2 && (D == 2 || B.box[2] == 2);
+      for (int q = 0; q < Q; ++q) {
+        const int c = cu.c;
+        const int lz = cu.l[2], ly = cu.l[1], lx = cu.l[0];
+        const long long rr = kz::cursor_row<D>(B, cu, lo, (unsigned)N);
+        cu.advance<D, 0>(B);
+        if (two) {
+          if (cu2.c != c || cu2.l[0] != lx || cu2.l[1] != ly || cu2.l[2] != lz) ++bad;
+          cu2.advance<D, 2>(B);
+        }
+        {
               const int k[3] = {lo[0] + lx, lo[1] + ly, lo[2] + lz};
-              if (k[0] >= B.n[0] || k[1] >= B.n[1] || k[2] >= B.n[2] || k[c] < 1) continue;
+              const bool valid = !(k[0] >= B.n[0] || k[1] >= B.n[1] || k[2] >= B.n[2] || k[c] < 1);
+              if (valid != (rr >= 0)) ++bad;
+              if (!valid) continue;
               const size_t r = (size_t)c * N + kz::cell_of(B.n, D, k[0], k[1], k[2]);
+              if ((long long)r != rr) ++bad;
               if (in2[r] == 0.0) continue;
               cx<double> dot = czero<double>();
               std::vector<int> idx(kz::HW * SL, -1);
@@ -442,7 +461,8 @@ long kz_steps_host(const kz::Boxes& B, const cx<double>* coef, const cx<double>*
                   const int id = idx[lane * SL + t];
                   if (id >= 0) reg[id] = reg[id] + sc * cconj(coef[r * NE + lane + kz::HW * t]);
                 }
-            }
+        }
+      }
       std::copy(reg.begin(), reg.end(), copies.begin() + (size_t)bx * B.RS);
     }
     for (size_t q = 0; q < (size_t)D * N; ++q) {

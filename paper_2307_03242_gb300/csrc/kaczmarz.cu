@@ -30,32 +30,47 @@ cudaError_t probe_all(const Grid<T>& g, cx<T>* coef, T* inv_n2, cx<T>* e, cx<T>*
   return cudaGetLastError();
 }
 
+// The solve kernel for boxes of 2 cells per axis (fixb = 2) or of any size (fixb = 0).
 template <typename T, int D>
-cudaError_t plan_solve(int sms, int RS, KzLaunch& out) {
-  // half-warps with a private region: as many as fit, an even number (both halves of a warp)
+const void* solve_fn(int fixb) {
+  return fixb == 2 ? (const void*)kz::solve<T, D, 2> : (const void*)kz::solve<T, D, 0>;
+}
+
+template <typename T, int D>
+cudaError_t plan_solve(int sms, int RS, const int box[3], KzLaunch& out) {
+  // half-warps with a private region: as many as fit beside the block's region-layout table, an
+  // even number (both halves of a warp)
   const size_t per_hw = (size_t)(RS + kz::PD * kz::Ring<D>::SLOT) * sizeof(cx<T>);
-  int warps = (int)(kRegionBudget / per_hw);
+  const size_t table = ((size_t)RS * sizeof(int) + 15) / 16 * 16;
+  if (table >= kRegionBudget) return cudaErrorInvalidValue;
+  int warps = (int)((kRegionBudget - table) / per_hw);
   if (warps > kz::NT / kz::HW) warps = kz::NT / kz::HW;
   warps &= ~1;
   if (warps < 2) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)warps * per_hw;
+  const size_t smem = (size_t)warps * per_hw + table;
+  bool two = true;
+  for (int a = 0; a < D; ++a) two = two && box[a] == 2;
+  const int fixb = two ? 2 : 0;
   static std::atomic<bool> attr_set[kMaxDev];
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
   if (!attr_set[dev].load()) {
-    err = cudaFuncSetAttribute(kz::solve<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRegionBudget);
-    if (err != cudaSuccess) return err;
+    for (int f : {0, 2}) {
+      err = cudaFuncSetAttribute(solve_fn<T, D>(f), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRegionBudget);
+      if (err != cudaSuccess) return err;
+    }
     attr_set[dev].store(true);
   }
   int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kz::solve<T, D>, kz::NT, smem);
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_fn<T, D>(fixb), kz::NT, smem);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
   out.blocks = sms * per_sm;
   out.warps = warps;
   out.smem = smem;
+  out.fixb = fixb;
   return cudaSuccess;
 }
 }  // namespace
@@ -66,8 +81,8 @@ cudaError_t launch_kz_probe(const Grid<T>& g, int dim, cx<T>* coef, T* inv_n2, c
 }
 
 template <typename T>
-cudaError_t plan_kz_solve(int dim, int sms, int RS, KzLaunch& out) {
-  return dim == 3 ? plan_solve<T, 3>(sms, RS, out) : plan_solve<T, 2>(sms, RS, out);
+cudaError_t plan_kz_solve(int dim, int sms, int RS, const int box[3], KzLaunch& out) {
+  return dim == 3 ? plan_solve<T, 3>(sms, RS, box, out) : plan_solve<T, 2>(sms, RS, box, out);
 }
 
 template <typename T>
@@ -75,13 +90,13 @@ cudaError_t launch_kz_solve(const kz::Args<T>& a, int dim, const KzLaunch& L, cu
   kz::Args<T> args = a;
   args.warps_a = L.warps;
   void* params[] = {&args};
-  const void* fn = dim == 3 ? (const void*)kz::solve<T, 3> : (const void*)kz::solve<T, 2>;
+  const void* fn = dim == 3 ? solve_fn<T, 3>(L.fixb) : solve_fn<T, 2>(L.fixb);
   return cudaLaunchCooperativeKernel(fn, dim3(L.blocks), dim3(kz::NT), params, L.smem, st);
 }
 
 #define INST(T)                                                                                                    \
   template cudaError_t launch_kz_probe<T>(const Grid<T>&, int, cx<T>*, T*, cx<T>*, cx<T>*, cudaStream_t);         \
-  template cudaError_t plan_kz_solve<T>(int, int, int, KzLaunch&);                                                \
+  template cudaError_t plan_kz_solve<T>(int, int, int, const int*, KzLaunch&);                                                \
   template cudaError_t launch_kz_solve<T>(const kz::Args<T>&, int, const KzLaunch&, cudaStream_t);
 INST(float)
 INST(double)

@@ -470,56 +470,116 @@ struct Ring {
 // Complex values of shared memory a half-warp uses: its region and its ring.
 HD int half_warp_smem(const Boxes& B, int D) { return B.RS + PD * ((D == 3 ? Shape<3>::NE : Shape<2>::NE) + 2); }
 
-// Starts the copy of box row q into ring slot `slot` (this lane's entries; lane 0 also the
-// right-hand side and the norm), or zero-fills the slot for a missing row; commits one group.
-template <typename T, int D>
-__device__ __forceinline__ void stage_row(const Args<T>& a, const LaneTab<D>& tab, const cx<T>* rhs, bool live,
-                                          const int lo[3], int q, int Q, int hl, cx<T>* slot) {
-  constexpr int NE = Shape<D>::NE, SL = Shape<D>::SL;
-  if (q < Q) {
-    int c, l[3];
-    const long long r = live ? box_row_global(a.B, q, lo, c, l) : -1;
-    if (r >= 0) {
-#pragma unroll
-      for (int t = 0; t < SL; ++t)
-        if (hl + HW * t < NE) cp_async(slot + hl + HW * t, a.coef + (size_t)r * NE + hl + HW * t, (int)sizeof(cx<T>));
-      if (hl == 0) {
-        cp_async(slot + NE, rhs + r, (int)sizeof(cx<T>));
-        cp_async(&slot[NE + 1].re, a.inv_n2 + r, (int)sizeof(T));
-      }
-    } else {
-#pragma unroll
-      for (int t = 0; t < SL; ++t)
-        if (hl + HW * t < NE) slot[hl + HW * t] = czero<T>();
-      if (hl == 0) {
-        slot[NE] = czero<T>();
-        slot[NE + 1] = czero<T>();
+// Box extent along axis a: FIXB cells on every axis of the grid when FIXB > 0 (the compiler then
+// turns the index arithmetic's divisions into shifts), else the run-time boxes.
+template <int D, int FIXB>
+HD int bsz(const Boxes& B, int a) {
+  return FIXB ? (a < D ? FIXB : 1) : B.box[a];
+}
+
+// A box row in sweep order (component, then cells with x fastest), advanced like an odometer.
+struct Cursor {
+  int c = 0, l[3] = {0, 0, 0};
+  template <int D, int FIXB>
+  HD void advance(const Boxes& B) {
+    if (++l[0] == bsz<D, FIXB>(B, 0)) {
+      l[0] = 0;
+      if (++l[1] == bsz<D, FIXB>(B, 1)) {
+        l[1] = 0;
+        if (++l[2] == bsz<D, FIXB>(B, 2)) {
+          l[2] = 0;
+          ++c;
+        }
       }
     }
   }
+};
+
+// Global row of the cursor's row in the box with lowest cell lo, or -1 (outside the grid or a
+// boundary face).
+template <int D>
+HD long long cursor_row(const Boxes& B, const Cursor& u, const int lo[3], unsigned N) {
+  const int k0 = lo[0] + u.l[0], k1 = lo[1] + u.l[1], k2 = lo[2] + u.l[2];
+  const int kc = u.c == 0 ? k0 : (u.c == 1 ? k1 : k2);
+  if (k0 >= B.n[0] || k1 >= B.n[1] || (D == 3 && k2 >= B.n[2]) || kc < 1) return -1;
+  const unsigned cell = D == 3 ? ((unsigned)k2 * B.n[1] + k1) * B.n[0] + k0 : (unsigned)k1 * B.n[0] + k0;
+  return (long long)u.c * N + cell;
+}
+
+// Starts the copy of row r into ring slot `slot` (this lane's entries; lane 0 also the right-hand
+// side and the norm), or zero-fills the slot for a missing row (r < 0); commits one group.
+template <typename T, int D>
+__device__ __forceinline__ void stage_row(const Args<T>& a, const LaneTab<D>& tab, const cx<T>* rhs, long long r,
+                                          int c, int hl, cx<T>* slot) {
+  constexpr int NE = Shape<D>::NE, SL = Shape<D>::SL;
+  if (r >= 0) {
+#pragma unroll
+    for (int t = 0; t < SL; ++t)
+      if (hl + HW * t < NE) cp_async(slot + hl + HW * t, a.coef + (size_t)r * NE + hl + HW * t, (int)sizeof(cx<T>));
+    if (hl == 0) {
+      cp_async(slot + NE, rhs + r, (int)sizeof(cx<T>));
+      cp_async(&slot[NE + 1].re, a.inv_n2 + r, (int)sizeof(T));
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < SL; ++t)
+      if (hl + HW * t < NE) slot[hl + HW * t] = czero<T>();
+    if (hl == 0) {
+      slot[NE] = czero<T>();
+      slot[NE + 1] = czero<T>();
+    }
+  }
+  (void)c;
+  (void)tab;
   cp_commit();
+}
+
+// Region layout of a box (the same for every box, relative to its lowest cell): entry t is
+// component c2 (bits 0-1) at offsets (bits 2-9, 10-17, 18-25) from the region's lowest cell.
+HD int region_code(const Boxes& B, int t) {
+  const int lo[3] = {0, 0, 0};
+  int m[3];
+  const int c2 = region_cell(B, t, lo, m);
+  return c2 | (m[0] + reach_lo(c2, 0)) << 2 | (m[1] + reach_lo(c2, 1)) << 10 |
+         (B.dim == 3 ? m[2] + reach_lo(c2, 2) : 0) << 18;
 }
 
 // One sweep of every box: rhs -> copies, starting from xin (nullptr: zero). Half-warp h of the
 // grid takes boxes h, h + nhw, ...; both halves of a warp run the same number of box rounds.
-// reg: the half-warp's region, followed by its ring of PD row slots.
-template <typename T, int D>
+// reg: the half-warp's region, followed by its ring of PD row slots; rtab: region_code of every
+// region entry (shared by the block).
+template <typename T, int D, int FIXB>
 __device__ void sweep_boxes(const Args<T>& a, const LaneTab<D>& tab, const cx<T>* rhs, const cx<T>* xin, cx<T>* reg,
-                            int ghw, int nhw) {
+                            const int* rtab, int ghw, int nhw) {
   constexpr int NE = Shape<D>::NE, SL = Shape<D>::SL, SLOT = Ring<D>::SLOT;
   const int hl = threadIdx.x & (HW - 1);
   const Boxes& B = a.B;
-  const size_t N = a.N;
+  const unsigned N = (unsigned)a.N;
   cx<T>* ring = reg + B.RS;
-  const int Q = D * B.box[0] * B.box[1] * B.box[2];
+  const int Q = D * bsz<D, FIXB>(B, 0) * bsz<D, FIXB>(B, 1) * bsz<D, FIXB>(B, 2);
   const int ghw0 = ghw & ~1;  // the warp's first half-warp: both halves run the same rounds
   for (int rd_i = 0; ghw0 + rd_i * nhw < B.nboxes; ++rd_i) {
     const int bx = ghw + rd_i * nhw;
     const bool live = bx < B.nboxes;
     int lo[3] = {0, 0, 0};
-    if (live) box_lo(B, bx, lo);
+    if (live) {
+      lo[0] = (bx % B.nb[0]) * bsz<D, FIXB>(B, 0);
+      lo[1] = ((bx / B.nb[0]) % B.nb[1]) * bsz<D, FIXB>(B, 1);
+      lo[2] = (bx / (B.nb[0] * B.nb[1])) * bsz<D, FIXB>(B, 2);
+    }
     // the first PD - 1 rows start copying while the region loads
-    for (int q = 0; q < PD - 1; ++q) stage_row<T, D>(a, tab, rhs, live, lo, q, Q, hl, ring + q * SLOT);
+    Cursor st;
+    int staged = 0;
+    auto stage_next = [&](cx<T>* slot) {
+      long long r = -1;
+      if (staged < Q) {
+        if (live) r = cursor_row<D>(B, st, lo, N);
+        st.advance<D, FIXB>(B);
+      }
+      ++staged;
+      stage_row<T, D>(a, tab, rhs, r, 0, hl, slot);
+    };
+    for (int q = 0; q < PD - 1; ++q) stage_next(ring + q * SLOT);
     // the region from xin, 8 independent loads in flight per lane
     for (int t0 = hl; t0 < B.RS; t0 += 8 * HW) {
       cx<T> v[8];
@@ -528,24 +588,30 @@ __device__ void sweep_boxes(const Args<T>& a, const LaneTab<D>& tab, const cx<T>
         const int t = t0 + u * HW;
         v[u] = czero<T>();
         if (live && xin && t < B.RS) {
-          int m[3];
-          const int c2 = region_cell(B, t, lo, m);
-          bool in = true;
-          for (int q = 0; q < D; ++q) in = in && m[q] >= 0 && m[q] < B.n[q];
-          if (in && m[c2] >= 1) v[u] = ldcg(xin + (size_t)c2 * N + cell_of(B.n, D, m[0], m[1], m[2]));
+          const int code = rtab[t];
+          const int c2 = code & 3;
+          const int m0 = lo[0] - reach_lo(c2, 0) + ((code >> 2) & 255);
+          const int m1 = lo[1] - reach_lo(c2, 1) + ((code >> 10) & 255);
+          const int m2 = D == 3 ? lo[2] - reach_lo(c2, 2) + ((code >> 18) & 255) : 0;
+          const int mc = c2 == 0 ? m0 : (c2 == 1 ? m1 : m2);
+          const bool in = m0 >= 0 && m0 < B.n[0] && m1 >= 0 && m1 < B.n[1] && (D == 2 || (m2 >= 0 && m2 < B.n[2]));
+          if (in && mc >= 1) {
+            const unsigned cell = D == 3 ? ((unsigned)m2 * B.n[1] + m1) * B.n[0] + m0 : (unsigned)m1 * B.n[0] + m0;
+            v[u] = ldcg(xin + (size_t)c2 * N + cell);
+          }
         }
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u)
         if (t0 + u * HW < B.RS) reg[t0 + u * HW] = v[u];
     }
+    Cursor cu;
     for (int q = 0; q < Q; ++q) {
-      stage_row<T, D>(a, tab, rhs, live, lo, q + PD - 1, Q, hl, ring + ((q + PD - 1) % PD) * SLOT);
+      stage_next(ring + ((q + PD - 1) % PD) * SLOT);
       cp_wait<PD - 1>();  // this lane's copies of row q have landed
       __syncwarp();       // ... and every lane's (the right-hand side and norm come from lane 0)
       const cx<T>* sl = ring + (q % PD) * SLOT;
-      int l[3];
-      const int c = box_row(B, q, l);
+      const int c = cu.c;
       int idx[SL];
       cx<T> co[SL];
       T sr = T(0), si = T(0);
@@ -556,7 +622,7 @@ __device__ void sweep_boxes(const Args<T>& a, const LaneTab<D>& tab, const cx<T>
         co[t] = czero<T>();
         if (pk >= 0) {
           const int cc = pk_c2(pk);
-          idx[t] = pk_off(pk) + (l[2] * B.ry[cc] + l[1]) * B.rx[cc] + l[0];
+          idx[t] = pk_off(pk) + (cu.l[2] * B.ry[cc] + cu.l[1]) * B.rx[cc] + cu.l[0];
           co[t] = sl[hl + HW * t];
           const cx<T> xv = reg[idx[t]];
           sr += co[t].re * xv.re - co[t].im * xv.im;
@@ -580,6 +646,7 @@ __device__ void sweep_boxes(const Args<T>& a, const LaneTab<D>& tab, const cx<T>
           reg[idx[t]] = v;
         }
       }
+      cu.advance<D, FIXB>(B);
       __syncwarp();  // the region's updates and the slot's reads are done before the slot refills
     }
     cp_wait<0>();
@@ -591,21 +658,36 @@ __device__ void sweep_boxes(const Args<T>& a, const LaneTab<D>& tab, const cx<T>
   }
 }
 
-// Component average of the copies -> out (D N; boundary faces 0).
-template <typename T, int D>
+// Component average of the copies -> out (D N; boundary faces 0). At most 3 boxes per axis hold
+// an unknown (boxes of at least 2 cells).
+template <typename T, int D, int FIXB>
 __device__ void average(const Args<T>& a, cx<T>* out, size_t tid, size_t nthr) {
   const Boxes& B = a.B;
-  const size_t N = a.N;
-  for (size_t q = tid; q < (size_t)D * N; q += nthr) {
+  const unsigned N = (unsigned)a.N, n0 = (unsigned)B.n[0], n1 = (unsigned)B.n[1];
+  const unsigned DN = (unsigned)D * N;
+  for (unsigned q = (unsigned)tid; q < DN; q += (unsigned)nthr) {
     const int c2 = (int)(q / N);
-    const size_t cell = q % N;
-    const int m[3] = {(int)(cell % B.n[0]), (int)((cell / B.n[0]) % B.n[1]), D == 3 ? (int)(cell / ((size_t)B.n[0] * B.n[1])) : 0};
+    const unsigned cell = q - (unsigned)c2 * N;
+    const unsigned t = cell / n0;
+    const int m[3] = {(int)(cell - t * n0), (int)(D == 3 ? t % n1 : t), D == 3 ? (int)(t / n1) : 0};
     if (m[c2] < 1) {
       out[q] = czero<T>();
       continue;
     }
     int blo[3], bhi[3];
-    reach_boxes(B, c2, m, blo, bhi);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      if (ax >= D) {
+        blo[ax] = bhi[ax] = 0;
+        continue;
+      }
+      const int bb = bsz<D, FIXB>(B, ax);
+      const int lo = (m[ax] + bb - 1) / bb - 1;
+      const int hi = (m[ax] + reach_lo(c2, ax)) / bb;
+      blo[ax] = lo < 0 ? 0 : lo;
+      bhi[ax] = hi > B.nb[ax] - 1 ? B.nb[ax] - 1 : hi;
+    }
+    const int rx = B.rx[c2], ry = B.ry[c2];
     // every candidate box's copy loaded before any is summed (independent loads), then summed
     // in box order
     cx<T> v[27];
@@ -621,7 +703,10 @@ __device__ void average(const Args<T>& a, cx<T>* out, size_t tid, size_t nthr) {
           v[u] = czero<T>();
           if (bz <= bhi[2] && by <= bhi[1] && bxx <= bhi[0]) {
             const int box = (bz * B.nb[1] + by) * B.nb[0] + bxx;
-            v[u] = ldcg(a.copies + (size_t)box * B.RS + reach_local(B, c2, m, bxx, by, bz));
+            const int lz = D == 3 ? m[2] - (bz * bsz<D, FIXB>(B, 2) - reach_lo(c2, 2)) : 0;
+            const int ly = m[1] - (by * bsz<D, FIXB>(B, 1) - reach_lo(c2, 1));
+            const int lx = m[0] - (bxx * bsz<D, FIXB>(B, 0) - reach_lo(c2, 0));
+            v[u] = ldcg(a.copies + (size_t)box * B.RS + B.rbase[c2] + (lz * ry + ly) * rx + lx);
           }
         }
     T sr = T(0), si = T(0);
@@ -715,7 +800,7 @@ __device__ void matvec(const Args<T>& a, const LaneTab<D>& tab, const cx<T>* z, 
   }
 }
 
-template <typename T, int D>
+template <typename T, int D, int FIXB>
 __global__ void __launch_bounds__(NT, 1) solve(Args<T> a) {
   extern __shared__ __align__(16) unsigned char kz_smem[];
   __shared__ Shared sh;
@@ -729,6 +814,9 @@ __global__ void __launch_bounds__(NT, 1) solve(Args<T> a) {
   const Grid<T>& g = a.g;
   LaneTab<D> tab;
   tab.init(a.B, threadIdx.x & (HW - 1));
+  // the region layout, after the half-warps' regions and rings (read after the first barrier)
+  int* rtab = reinterpret_cast<int*>(reinterpret_cast<cx<T>*>(kz_smem) + (size_t)a.warps_a * half_warp_smem(a.B, D));
+  for (int t = threadIdx.x; t < a.B.RS; t += NT) rtab[t] = region_code(a.B, t);
   int parity = 0;
   cx<double> red;
 
@@ -762,9 +850,9 @@ __global__ void __launch_bounds__(NT, 1) solve(Args<T> a) {
         if (!grid_sync(a.bar, a.err, &sh.ok)) return;
         // Z_j = K(V_j): Kaczmarz steps from zero
         for (int s = 0; s < a.steps; ++s) {
-          if (hwb < a.warps_a) sweep_boxes<T, D>(a, tab, Vj, s == 0 ? nullptr : Zj, reg, ghw_a, nhw_a);
+          if (hwb < a.warps_a) sweep_boxes<T, D, FIXB>(a, tab, Vj, s == 0 ? nullptr : Zj, reg, rtab, ghw_a, nhw_a);
           if (!grid_sync(a.bar, a.err, &sh.ok)) return;
-          average<T, D>(a, Zj, tid, nthr);
+          average<T, D, FIXB>(a, Zj, tid, nthr);
           if (!grid_sync(a.bar, a.err, &sh.ok)) return;
         }
         // w = S Z_j, h_0j = <V_0, w>

@@ -89,10 +89,11 @@ void launch_sconj(cx<float>* z, size_t nu, size_t n, cudaStream_t st);
 struct KzLaunch {
   int blocks = 0, warps = 0;
   size_t smem = 0;
+  int fixb = 0;  // 2: the kernel built for boxes of 2 cells per axis; 0: any box
 };
 template <typename T>
 cudaError_t launch_kz_probe(const Grid<T>& g, int dim, cx<T>* coef, T* inv_n2, cx<T>* e, cx<T>* y, cudaStream_t st);
 template <typename T>
-cudaError_t plan_kz_solve(int dim, int sms, int RS, KzLaunch& out);
+cudaError_t plan_kz_solve(int dim, int sms, int RS, const int box[3], KzLaunch& out);
 template <typename T>
 cudaError_t launch_kz_solve(const kz::Args<T>& a, int dim, const KzLaunch& L, cudaStream_t st);

@@ -37,11 +37,12 @@ class Workload:
     nu_post: int = 2
     restart: int = 20
     tol: float = 1e-6
-    coarse: str = "dense"          # "dense" or "smooth"
+    coarse: str = "dense"          # "dense", "smooth" or "kaczmarz"
     coarse_sweeps: int = 0
     coarse_damping: float = 1.0
     cycle: str = "V"               # "V" or "W"
     alpha_coarsest: float = 0.0    # shift of the coarsest level (0: alpha)
+    level_alpha: tuple = None      # shift per level, finest first (overrides alpha / alpha_coarsest)
     smoother: str = "full"         # "full" or "economic" Vanka
     extra: dict = field(default_factory=dict)
 
@@ -50,7 +51,11 @@ class Workload:
         return len(self.n)
 
     def level_alphas(self):
-        """Shift per level: alpha everywhere, alpha_coarsest (if set) on the coarsest level."""
+        """Shift per level: level_alpha if given (its last value repeated below its end), else
+        alpha everywhere with alpha_coarsest (if set) on the coarsest level."""
+        if self.level_alpha:
+            la = list(self.level_alpha)
+            return [la[min(l, len(la) - 1)] for l in range(self.levels)]
         a = [self.alpha] * self.levels
         if self.alpha_coarsest > 0:
             a[-1] = self.alpha_coarsest
@@ -169,12 +174,16 @@ def config_c4_batch(count: int = 64, seed0: int = 1000, sizes=(256, 384, 512, 76
     return out
 
 
-def config_c3_layered3d(n: int = 256, source=(128, 128, 24), levels: int = 3) -> Workload:
+def config_c3_layered3d(n: int = 256, source=(128, 128, 24), levels: int = 4) -> Workload:
     """3D three-layer medium (Vp 2.0/3.0/4.0 for depth fractions [0,80)/[80,170)/[170,256) of
     256) plus a Gaussian inclusion Vp*(1 + 0.2 exp(-r^2/24^2)) at the centre; Vs = Vp/sqrt(3),
     rho 1.0/1.2/1.4 by layer; 10 points per minimum shear wavelength; u3 point force. Solver:
-    K(1,1) on 3 levels, shift 0.4 (2.5 on the coarsest level, 16 red-black sweeps), damping 0.15,
-    FGMRES(8)."""
+    K(1,1) on 4 levels (the paper's 3D cycle; coarsest 32^3 at n = 256), shifts 0.4 / 0.5 / 0.6 /
+    0.8 from the finest level down, damping 0.35, the hybrid Kaczmarz-GMRES coarsest solve
+    (Sec. 3.2, 5.3), FGMRES(8). Measured at 256^3 (FGMRES iterations, seconds): this recipe 85,
+    4.28; damping 0.3 91, 4.60; 0.25 110, 5.72; 0.2 138, 7.09; one shift 0.4 on every level with
+    damping 0.25 168, 9.38; 3 levels with 16 red-black sweeps on a 64^3 coarsest level shifted
+    by 2.5 (the previous recipe) 193, 8.29."""
     s = n / 256.0
     z = (np.arange(n) + 0.5)
     vp1 = np.where(z < 80 * s, 2.0, np.where(z < 170 * s, 3.0, 4.0))
@@ -191,8 +200,8 @@ def config_c3_layered3d(n: int = 256, source=(128, 128, 24), levels: int = 3) ->
     src = tuple(int(round(v * s)) for v in source)
     rhs = point_source((n, n, n), 2, src)
     return Workload("c3_layered_3d_%d" % n, (n, n, n), h, lam, mu, rho, omega, rhs,
-                    levels=levels, alpha=0.4, damping=0.15, abl_cells=max(2, int(round(20 * s))),
-                    coarse="smooth", coarse_sweeps=16, coarse_damping=0.8, cycle="K", alpha_coarsest=2.5,
+                    levels=levels, alpha=0.4, damping=0.35, abl_cells=max(2, int(round(20 * s))),
+                    coarse="kaczmarz", cycle="K", level_alpha=(0.4, 0.5, 0.6, 0.8),
                     nu_pre=1, nu_post=1, restart=8)
 
 
@@ -206,8 +215,11 @@ def config_c5_adjoint(n: int = 128, seed: int = 0, source_side: int = 4, receive
     the depth component u3 on a regular grid at depth index `depth`, receiver_side^2 receivers of
     u3 on a regular grid at the same depth; 10 points per minimum shear wavelength of the
     current model. extra: "sources" (DOF arrays), "receivers" ((comp, (i, j, k)) tuples, x1
-    first), "true" (lam, mu, rho of the data model). Solver: the 3D recipe (K(1,1) on 3 levels,
-    shift 0.4, 2.5 and 16 red-black sweeps on the coarsest level, damping 0.15, FGMRES(8))."""
+    first), "true" (lam, mu, rho of the data model). Solver: the 3D recipe (K(1,1) on 4 levels,
+    shifts 0.4 / 0.5 / 0.6 / 0.8, the hybrid Kaczmarz-GMRES coarsest solve, FGMRES(8)) with
+    damping 0.25. Measured at 128^3 per source (FGMRES iterations, seconds, forward / adjoint):
+    35 / 35, 0.65 / 0.69; damping 0.3 35 / 35, 0.67 / 0.70; the previous 3-level recipe with 16
+    red-black sweeps on a 32^3 coarsest level shifted by 2.5, 240 / 239, 1.74 / 2.00."""
     shape = (n, n, n)
     vp = gaussian_random_velocity(shape, seed, sigma_cells=n / 16.0)
     z = np.arange(n) + 0.5
@@ -228,8 +240,8 @@ def config_c5_adjoint(n: int = 128, seed: int = 0, source_side: int = 4, receive
     sources = [point_source(shape, 2, (i, j, depth)) for j in grid(source_side) for i in grid(source_side)]
     receivers = [(2, (i, j, depth)) for j in grid(receiver_side) for i in grid(receiver_side)]
     w = Workload("c5_adjoint_3d_%d" % n, shape, h, lam, mu, rho, omega, sources[0],
-                 levels=3, alpha=0.4, damping=0.15, abl_cells=max(2, int(round(20 * n / 256.0))),
-                 coarse="smooth", coarse_sweeps=16, coarse_damping=0.8, cycle="K", alpha_coarsest=2.5,
+                 levels=4, alpha=0.4, damping=0.25, abl_cells=max(2, int(round(20 * n / 256.0))),
+                 coarse="kaczmarz", cycle="K", level_alpha=(0.4, 0.5, 0.6, 0.8),
                  nu_pre=1, nu_post=1, restart=8)
     w.extra["sources"] = sources
     w.extra["receivers"] = receivers

@@ -420,14 +420,14 @@ def bench_single(args, w, steps, warmup, fp64_steps, cpu_baseline, e2e_steps=Non
            "speedup_vs_fp64": t64 / t32 if t64 else None,
            "vcycle": {"ms": vms, "gbs_algorithmic": v_gbs, "bytes_per_cell": per_cell,
                       "frac_of_hbm": v_gbs / peak},
-           "roofline": {"kernel": "one-pass red-black Vanka sweep k2t::sweep_tile (finest level, FP32)",
-                        "bytes_basis": "84 B per cell per sweep (3S + 3r), 60 B from a zero guess, + 6 B of coarse "
-                                       "correction in the first post-sweep", "bound": "hbm", "achieved": achieved,
+           "roofline": dict(finest_sweep_kernel(w, paths), **{
+                        "bound": "hbm", "achieved": achieved,
                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                        "frac": achieved / peak if achieved else None, "traffic": recorded_traffic(),
+                        "frac": achieved / peak if achieved else None,
+                        "traffic": recorded_traffic() if tiled_finest(w, paths) else None,
                         "launches": prof["launches"], "avg_launch_ms": prof["ms"] / max(prof["launches"], 1),
                         "bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
-                        "fp32": fp32_fraction(prof)},
+                        "fp32": fp32_fraction(prof) if tiled_finest(w, paths) else None}),
            "fine_level_ms_per_solve": dict({"smooth": prof["ms"] / steps},
                                            **{k: v["ms"] / steps for k, v in breakdown.items()}),
            "coarse_levels_ms_per_solve": coarse_ms,
@@ -714,6 +714,26 @@ def bench_gradient(args, steps, warmup):
                                "sample": desc + " x the forward and adjoint iterations of one gradient"}
     out["clocks"] = clk.summary()
     return out
+
+
+def tiled_finest(w, paths):
+    """True when the finest level's sweeps run the one-pass tiled kernel (2D, FP32)."""
+    from paper_2307_03242_gb300 import emg
+    return w.dim == 2 and paths and paths[0] in (emg.SWEEP_TILE24, emg.SWEEP_TILE8)
+
+
+def finest_sweep_kernel(w, paths):
+    """Name and byte basis of the finest level's sweep kernel, the roofline's dominant kernel."""
+    if tiled_finest(w, paths):
+        return {"kernel": "one-pass red-black Vanka sweep k2t::sweep_tile (finest level, FP32)",
+                "bytes_basis": "84 B per cell per sweep (3S + 3r), 60 B from a zero guess, + 6 B of coarse "
+                               "correction in the first post-sweep"}
+    if w.dim == 3:
+        return {"kernel": "red-black Vanka half-sweep k3t::vanka_tile (finest level, FP32)",
+                "bytes_basis": "100 B per cell per half-sweep (the colour's faces and pressures read and "
+                               "written, b read, 3 material reals)"}
+    return {"kernel": "red-black Vanka half-sweep k2::vanka_fast (finest level, FP32)",
+            "bytes_basis": "76 B per cell per half-sweep"}
 
 
 def fp32_fraction(prof):

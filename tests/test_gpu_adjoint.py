@@ -129,7 +129,9 @@ def test_misfit_gradient_through_autograd_matches_the_oracle(keep_fields):
     J_ref, g_ref = misfit_and_gradient(pb, [q.ravel() for q in srcs], rec, data)
     lam, mu, rho = (torch.from_numpy(np.ascontiguousarray(a)).cuda().requires_grad_(True) for a in (w.lam, w.mu, w.rho))
     params = emg.params_from_workload(w, 32)
-    J = inversion.misfit(lam, mu, rho, params, t["sources"], t["receivers"], t["data"], tol=1e-11,
+    # J is small (the data model differs from the current one by a 5 % blob), so the solves must
+    # be tighter than J's tolerance: a 1e-12 residual leaves J within ~1e-9 of the direct solve
+    J = inversion.misfit(lam, mu, rho, params, t["sources"], t["receivers"], t["data"], tol=1e-12,
                          keep_fields=keep_fields)
     J.backward()
     assert abs(J.item() - J_ref) <= 1e-8 * J_ref

@@ -215,9 +215,9 @@ def config_c5_adjoint(n: int = 128, seed: int = 0, source_side: int = 4, receive
     the depth component u3 on a regular grid at depth index `depth`, receiver_side^2 receivers of
     u3 on a regular grid at the same depth; 10 points per minimum shear wavelength of the
     current model. extra: "sources" (DOF arrays), "receivers" ((comp, (i, j, k)) tuples, x1
-    first), "true" (lam, mu, rho of the data model). Solver: the 3D recipe (K(1,1) on 4 levels,
-    shifts 0.4 / 0.5 / 0.6 / 0.8, the hybrid Kaczmarz-GMRES coarsest solve, FGMRES(8)) with
-    damping 0.25. Measured at 128^3 per source (FGMRES iterations, seconds, forward / adjoint):
+    first), "true" (lam, mu, rho of the data model). Solver: the 3D recipe (K(1,1) on 4 levels at
+    n >= 64, fewer below so that the coarsest level keeps at least 8^3 cells; shifts 0.4 / 0.5 /
+    0.6 / 0.8; the hybrid Kaczmarz-GMRES coarsest solve; FGMRES(8)) with damping 0.25. Measured at 128^3 per source (FGMRES iterations, seconds, forward / adjoint):
     35 / 35, 0.65 / 0.69; damping 0.3 35 / 35, 0.67 / 0.70; the previous 3-level recipe with 16
     red-black sweeps on a 32^3 coarsest level shifted by 2.5, 240 / 239, 1.74 / 2.00."""
     shape = (n, n, n)
@@ -239,8 +239,9 @@ def config_c5_adjoint(n: int = 128, seed: int = 0, source_side: int = 4, receive
     grid = lambda k: [int((i + 0.5) * n / k) for i in range(k)]
     sources = [point_source(shape, 2, (i, j, depth)) for j in grid(source_side) for i in grid(source_side)]
     receivers = [(2, (i, j, depth)) for j in grid(receiver_side) for i in grid(receiver_side)]
+    levels = min(4, max(2, int(np.log2(n)) - 2))  # coarsest level of at least 8^3 below 128^3
     w = Workload("c5_adjoint_3d_%d" % n, shape, h, lam, mu, rho, omega, sources[0],
-                 levels=4, alpha=0.4, damping=0.25, abl_cells=max(2, int(round(20 * n / 256.0))),
+                 levels=levels, alpha=0.4, damping=0.25, abl_cells=max(2, int(round(20 * n / 256.0))),
                  coarse="kaczmarz", cycle="K", level_alpha=(0.4, 0.5, 0.6, 0.8),
                  nu_pre=1, nu_post=1, restart=8)
     w.extra["sources"] = sources

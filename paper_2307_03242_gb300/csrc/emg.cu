@@ -187,13 +187,42 @@ struct KzCfg {
 };
 KzCfg kz_cfg(const emg_params& p) {
   KzCfg k;
-  for (int a = 0; a < 3; ++a) k.box[a] = p.kaczmarz_box[a] > 0 ? p.kaczmarz_box[a] : 2;
+  for (int a = 0; a < 3; ++a) k.box[a] = p.kaczmarz_box[a];  // all zero: chosen at set-up
   k.steps = p.kaczmarz_steps > 0 ? p.kaczmarz_steps : 10;
   k.restart = p.coarse_restart > 0 ? p.coarse_restart : 5;
   k.max_steps = p.kaczmarz_max > 0 ? p.kaczmarz_max : 250;
   k.damping = p.kaczmarz_damping > 0.0 ? p.kaczmarz_damping : 0.8;
   k.tol = p.coarse_tol > 0.0 ? p.coarse_tol : 0.1;
   return k;
+}
+
+// Half-warps per block whose box region and row ring fit beside the region-layout table in the
+// Kaczmarz kernel's 200 KB of shared memory (an even number; < 2: the box does not fit).
+int kz_region_halfwarps(int dim, const int n[3], const int box[3], size_t cb) {
+  const kz::Boxes B = kz::make_boxes(dim, n, box);
+  const size_t per_hw = (size_t)kz::half_warp_smem(B, dim) * cb;
+  const size_t table = ((size_t)B.RS * 4 + 15) / 16 * 16;
+  if (table >= 200 * 1024) return 0;
+  int w = (int)((200 * 1024 - table) / per_hw);
+  if (w > kz::NT / kz::HW) w = kz::NT / kz::HW;
+  return w & ~1;
+}
+
+// The automatic box: the smallest cube of 1 (3D) or 2 (2D), 4, ... cells whose boxes the resident
+// half-warps (one block per SM) can all sweep at once, so that a Kaczmarz step's sequential part
+// is one box's rows; the largest that fits if none does.
+void kz_auto_box(int dim, const int n[3], int sms, size_t cb, int box[3]) {
+  int pick = 0;
+  // 2D starts at 2 cells: with boxes of one cell (2 rows) the averaged steps converge slowly
+  for (int b = dim == 3 ? 1 : 2; b <= 64; b *= 2) {
+    const int bb[3] = {b, b, b};
+    const int hw = kz_region_halfwarps(dim, n, bb, cb);
+    if (hw < 2) break;
+    pick = b;
+    if ((long long)kz::make_boxes(dim, n, bb).nboxes <= (long long)sms * hw) break;
+  }
+  if (pick == 0) pick = 1;
+  for (int a = 0; a < 3; ++a) box[a] = pick;
 }
 
 template <typename T>
@@ -906,7 +935,9 @@ void setup_kaczmarz(emg_ctx& c) {
   const int d = c.dim, l = c.L - 1;
   const Level& C = c.lv[l];
   const KzCfg k = kz_cfg(c.prm);
-  c.kz_B = kz::make_boxes(d, C.n, k.box);
+  int box[3] = {k.box[0], k.box[1], k.box[2]};
+  if (box[0] == 0) kz_auto_box(d, C.n, c.sms, sizeof(cx<T>), box);
+  c.kz_B = kz::make_boxes(d, C.n, box);
   const size_t N = C.ncell, DN = (size_t)d * N, cb = sizeof(cx<T>);
   const int NE = d == 3 ? kz::Shape<3>::NE : kz::Shape<2>::NE;
   c.kz_coef.alloc(DN * NE * cb);
@@ -1457,9 +1488,14 @@ void check_params(const emg_params* p) {
     raise(EMG_ERR_INVALID, "unknown coarse_solver");
   if (p->coarse_solver == EMG_COARSE_KACZMARZ) {
     const KzCfg k = kz_cfg(*p);
-    for (int a = 0; a < 3; ++a)
-      if (p->kaczmarz_box[a] < 0 || k.box[a] < 2 || k.box[a] > 64)
-        raise(EMG_ERR_INVALID, "kaczmarz_box out of range (0 or 2..64)");
+    bool zero = true, ones = true, big = true;
+    for (int a = 0; a < p->dim; ++a) {
+      zero = zero && k.box[a] == 0;
+      ones = ones && k.box[a] == 1;
+      big = big && k.box[a] >= 2 && k.box[a] <= 64;
+    }
+    if (!zero && !ones && !big)
+      raise(EMG_ERR_INVALID, "kaczmarz_box: all 0 (automatic), all 1, or each in 2..64");
     if (p->kaczmarz_steps < 0 || p->coarse_restart < 0 || p->kaczmarz_max < 0 || k.restart > kz::MAXM)
       raise(EMG_ERR_INVALID, "kaczmarz_steps, kaczmarz_max must be >= 0 and coarse_restart in 0..8");
     if (!std::isfinite(p->kaczmarz_damping) || p->kaczmarz_damping < 0.0 || k.damping >= 2.0)
@@ -1467,9 +1503,8 @@ void check_params(const emg_params* p) {
     if (!std::isfinite(p->coarse_tol) || p->coarse_tol < 0.0) raise(EMG_ERR_INVALID, "coarse_tol must be >= 0");
     int nc[3] = {1, 1, 1};
     for (int a = 0; a < p->dim; ++a) nc[a] = p->n[a] / div;
-    const kz::Boxes B = kz::make_boxes(p->dim, nc, k.box);
     const size_t cb = p->cycle_precision == 32 ? 8 : 16;
-    if (2 * (size_t)kz::half_warp_smem(B, p->dim) * cb + 4 * (size_t)B.RS + 16 > 200 * 1024)
+    if (!zero && kz_region_halfwarps(p->dim, nc, k.box, cb) < 2)
       raise(EMG_ERR_INVALID, "kaczmarz_box too large for shared memory");
   }
   if (p->coarse_solver == EMG_COARSE_SMOOTH && p->coarse_sweeps < 1 && p->levels > 0)

@@ -419,6 +419,8 @@ long kz_steps_host(const kz::Boxes& B, const cx<double>* coef, const cx<double>*
       kz::Cursor cu, cu2;
       const int Q = D * B.box[0] * B.box[1] * B.box[2];
       const bool two = B.box[0] == 2 && B.box[1] == 2 && (D == 2 || B.box[2] == 2);
+      const bool one = B.box[0] == 1 && B.box[1] == 1 && (D == 2 || B.box[2] == 1);
+      kz::Cursor cu1;
       for (int q = 0; q < Q; ++q) {
         const int c = cu.c;
         const int lz = cu.l[2], ly = cu.l[1], lx = cu.l[0];
@@ -427,6 +429,10 @@ long kz_steps_host(const kz::Boxes& B, const cx<double>* coef, const cx<double>*
         if (two) {
           if (cu2.c != c || cu2.l[0] != lx || cu2.l[1] != ly || cu2.l[2] != lz) ++bad;
           cu2.advance<D, 2>(B);
+        }
+        if (one) {
+          if (cu1.c != c || cu1.l[0] != lx || cu1.l[1] != ly || cu1.l[2] != lz) ++bad;
+          cu1.advance<D, 1>(B);
         }
         {
               const int k[3] = {lo[0] + lx, lo[1] + ly, lo[2] + lz};
@@ -476,7 +482,7 @@ long kz_steps_host(const kz::Boxes& B, const cx<double>* coef, const cx<double>*
       int blo[3], bhi[3];
       kz::reach_boxes(B, c2, m, blo, bhi);
       for (int a = 0; a < 3; ++a)
-        if (bhi[a] - blo[a] > 2) ++bad;  // the kernel takes at most 3 boxes per axis
+        if (bhi[a] - blo[a] > (B.box[a] == 1 ? 3 : 2)) ++bad;  // the kernel's candidates per axis
       cx<double> acc = czero<double>();
       int cnt = 0;
       for (int bz = blo[2]; bz <= bhi[2]; ++bz)

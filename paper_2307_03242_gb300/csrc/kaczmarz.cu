@@ -30,10 +30,11 @@ cudaError_t probe_all(const Grid<T>& g, cx<T>* coef, T* inv_n2, cx<T>* e, cx<T>*
   return cudaGetLastError();
 }
 
-// The solve kernel for boxes of 2 cells per axis (fixb = 2) or of any size (fixb = 0).
+// The solve kernel for boxes of 1 or 2 cells per axis (fixb = 1, 2) or of at least 2 (fixb = 0).
 template <typename T, int D>
 const void* solve_fn(int fixb) {
-  return fixb == 2 ? (const void*)kz::solve<T, D, 2> : (const void*)kz::solve<T, D, 0>;
+  return fixb == 2 ? (const void*)kz::solve<T, D, 2>
+                   : (fixb == 1 ? (const void*)kz::solve<T, D, 1> : (const void*)kz::solve<T, D, 0>);
 }
 
 template <typename T, int D>
@@ -48,16 +49,19 @@ cudaError_t plan_solve(int sms, int RS, const int box[3], KzLaunch& out) {
   warps &= ~1;
   if (warps < 2) return cudaErrorInvalidValue;
   const size_t smem = (size_t)warps * per_hw + table;
-  bool two = true;
-  for (int a = 0; a < D; ++a) two = two && box[a] == 2;
-  const int fixb = two ? 2 : 0;
+  bool two = true, one = true;
+  for (int a = 0; a < D; ++a) {
+    two = two && box[a] == 2;
+    one = one && box[a] == 1;
+  }
+  const int fixb = two ? 2 : (one ? 1 : 0);
   static std::atomic<bool> attr_set[kMaxDev];
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
   if (!attr_set[dev].load()) {
-    for (int f : {0, 2}) {
+    for (int f : {0, 1, 2}) {
       err = cudaFuncSetAttribute(solve_fn<T, D>(f), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRegionBudget);
       if (err != cudaSuccess) return err;
     }

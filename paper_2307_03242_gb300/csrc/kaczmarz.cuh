@@ -470,8 +470,9 @@ struct Ring {
 // Complex values of shared memory a half-warp uses: its region and its ring.
 HD int half_warp_smem(const Boxes& B, int D) { return B.RS + PD * ((D == 3 ? Shape<3>::NE : Shape<2>::NE) + 2); }
 
-// Box extent along axis a: FIXB cells on every axis of the grid when FIXB > 0 (the compiler then
-// turns the index arithmetic's divisions into shifts), else the run-time boxes.
+// Box extent along axis a: FIXB cells on every axis of the grid when FIXB > 0 (boxes of 1 or 2
+// cells; the compiler then turns the index arithmetic's divisions into shifts), else the run-time
+// boxes (at least 2 cells per axis).
 template <int D, int FIXB>
 HD int bsz(const Boxes& B, int a) {
   return FIXB ? (a < D ? FIXB : 1) : B.box[a];
@@ -659,7 +660,7 @@ __device__ void sweep_boxes(const Args<T>& a, const LaneTab<D>& tab, const cx<T>
 }
 
 // Component average of the copies -> out (D N; boundary faces 0). At most 3 boxes per axis hold
-// an unknown (boxes of at least 2 cells).
+// an unknown when boxes have at least 2 cells per axis, at most 4 for boxes of one cell.
 template <typename T, int D, int FIXB>
 __device__ void average(const Args<T>& a, cx<T>* out, size_t tid, size_t nthr) {
   const Boxes& B = a.B;
@@ -689,17 +690,18 @@ __device__ void average(const Args<T>& a, cx<T>* out, size_t tid, size_t nthr) {
     }
     const int rx = B.rx[c2], ry = B.ry[c2];
     // every candidate box's copy loaded before any is summed (independent loads), then summed
-    // in box order
-    cx<T> v[27];
-    constexpr int NZ = D == 3 ? 3 : 1;
+    // in box order; CA candidates per axis (4 for boxes of one cell, else 3)
+    constexpr int CA = FIXB == 1 ? 4 : 3;
+    constexpr int NZ = D == 3 ? CA : 1;
+    cx<T> v[NZ * CA * CA];
 #pragma unroll
     for (int dz = 0; dz < NZ; ++dz)
 #pragma unroll
-      for (int dy = 0; dy < 3; ++dy)
+      for (int dy = 0; dy < CA; ++dy)
 #pragma unroll
-        for (int dx = 0; dx < 3; ++dx) {
+        for (int dx = 0; dx < CA; ++dx) {
           const int bz = blo[2] + dz, by = blo[1] + dy, bxx = blo[0] + dx;
-          const int u = (dz * 3 + dy) * 3 + dx;
+          const int u = (dz * CA + dy) * CA + dx;
           v[u] = czero<T>();
           if (bz <= bhi[2] && by <= bhi[1] && bxx <= bhi[0]) {
             const int box = (bz * B.nb[1] + by) * B.nb[0] + bxx;
@@ -714,11 +716,11 @@ __device__ void average(const Args<T>& a, cx<T>* out, size_t tid, size_t nthr) {
 #pragma unroll
     for (int dz = 0; dz < NZ; ++dz)
 #pragma unroll
-      for (int dy = 0; dy < 3; ++dy)
+      for (int dy = 0; dy < CA; ++dy)
 #pragma unroll
-        for (int dx = 0; dx < 3; ++dx)
+        for (int dx = 0; dx < CA; ++dx)
           if (blo[2] + dz <= bhi[2] && blo[1] + dy <= bhi[1] && blo[0] + dx <= bhi[0]) {
-            const cx<T> w = v[(dz * 3 + dy) * 3 + dx];
+            const cx<T> w = v[(dz * CA + dy) * CA + dx];
             sr += w.re;
             si += w.im;
             ++cnt;

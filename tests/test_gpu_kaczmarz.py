@@ -16,7 +16,8 @@ pytestmark = pytest.mark.gpu
 
 # name -> (finest cells, levels, box)
 CASES = {"3d_box2": ((16, 16, 12), 2, (2, 2, 2)), "3d_ragged": ((20, 16, 12), 2, (4, 3, 2)),
-         "2d_box2": ((48, 40), 2, (2, 2)), "3d_three_levels": ((24, 24, 16), 3, (2, 2, 2))}
+         "2d_box2": ((48, 40), 2, (2, 2)), "3d_three_levels": ((24, 24, 16), 3, (2, 2, 2)),
+         "3d_box1": ((16, 12, 12), 2, (1, 1, 1)), "2d_box1": ((40, 36), 2, (1, 1))}
 
 
 @pytest.fixture(scope="module")
@@ -43,7 +44,7 @@ def _setup(case, prec, **over):
     return w, pb, hier, s
 
 
-@pytest.mark.parametrize("case", ["3d_box2", "3d_ragged", "2d_box2"])
+@pytest.mark.parametrize("case", ["3d_box2", "3d_ragged", "2d_box2", "3d_box1"])
 @pytest.mark.parametrize("prec", [64, 32])
 def test_probed_schur_rows_match_the_oracle(hc, case, prec):
     from test_host_kaczmarz import stored_rows
@@ -101,7 +102,11 @@ def test_coarsest_solve_reaches_the_paper_drop(case, prec):
         assert abs(its - its_ref) <= 1
     x = to_np(xt).ravel()
     f = sysm.reduce(b.ravel())
-    assert np.linalg.norm(f - sysm.S @ x[sysm.u_act]) / np.linalg.norm(f) <= 0.1 * (1 + 1e-4)
+    got = np.linalg.norm(f - sysm.S @ x[sysm.u_act]) / np.linalg.norm(f)
+    if its_ref < 25:
+        assert got <= 0.1 * (1 + 1e-4)
+    else:  # the oracle too spent the 250 Kaczmarz steps (1-cell boxes in 2D converge slowly)
+        assert its == 25 and abs(got - relres) <= (1e-9 if prec == 64 else 1e-4)
     # the pressure is recovered exactly from u: the continuity rows of the full residual vanish
     r = b.ravel() - hier.H[last] @ x
     assert np.abs(r[sysm.nu:]).max() <= (1e-10 if prec == 64 else 1e-4) * np.abs(b).max()

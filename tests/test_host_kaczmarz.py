@@ -95,7 +95,8 @@ def test_probed_schur_rows_match_the_oracle(hc, n, abl):
 
 
 @pytest.mark.parametrize("n,box", [((9, 7, 6), (2, 2, 2)), ((8, 8, 8), (4, 2, 3)), ((10, 9, 5), (3, 3, 3)),
-                                   ((11, 9), (2, 2)), ((16, 12), (4, 3)), ((6, 5, 4), (2, 2, 3)), ((7, 6, 9), (5, 6, 2))])
+                                   ((11, 9), (2, 2)), ((16, 12), (4, 3)), ((6, 5, 4), (2, 2, 3)), ((7, 6, 9), (5, 6, 2)),
+                                   ((6, 5, 4), (1, 1, 1)), ((9, 7), (1, 1))])
 def test_kernel_kaczmarz_steps_match_the_oracle(hc, n, box):
     """Three steps with the kernel's geometry equal the oracle's component-averaged Kaczmarz steps
     over the same boxes (ragged boxes at the far ends included)."""

@@ -112,8 +112,8 @@ typedef struct {
    * the same iterate, and each unknown becomes the mean of the boxes' copies of it. The solve stops
    * when ||f - S u|| <= coarse_tol ||f|| or after kaczmarz_max / kaczmarz_steps FGMRES iterations.
    * Zero selects the paper's value: restart 5, 10 steps, damping 0.8, drop 0.1, at most 250 steps.
-   * kaczmarz_box: all 0 (automatic: the smallest cube of 1 (3D) or 2 (2D), 4, ... cells whose boxes
-   * the GPU can all sweep at once), all 1, or each in 2..64. coarse_restart <= 8; kaczmarz_damping in
+   * kaczmarz_box: all 0 (automatic: the smallest cube of 2, 4, ... cells whose boxes the GPU can
+   * all sweep at once), all 1, or each in 2..64. coarse_restart <= 8; kaczmarz_damping in
    * (0, 2). */
   int32_t kaczmarz_box[3];
   int32_t kaczmarz_steps;

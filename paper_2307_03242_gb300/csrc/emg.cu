@@ -208,13 +208,14 @@ int kz_region_halfwarps(int dim, const int n[3], const int box[3], size_t cb) {
   return w & ~1;
 }
 
-// The automatic box: the smallest cube of 1 (3D) or 2 (2D), 4, ... cells whose boxes the resident
+// The automatic box: the smallest cube of 2, 4, ... cells whose boxes the resident
 // half-warps (one block per SM) can all sweep at once, so that a Kaczmarz step's sequential part
 // is one box's rows; the largest that fits if none does.
 void kz_auto_box(int dim, const int n[3], int sms, size_t cb, int box[3]) {
   int pick = 0;
-  // 2D starts at 2 cells: with boxes of one cell (2 rows) the averaged steps converge slowly
-  for (int b = dim == 3 ? 1 : 2; b <= 64; b *= 2) {
+  // from 2 cells: boxes of one cell need about twice the steps (3D) or stall (2D), which costs
+  // more than their shorter sweeps save
+  for (int b = 2; b <= 64; b *= 2) {
     const int bb[3] = {b, b, b};
     const int hw = kz_region_halfwarps(dim, n, bb, cb);
     if (hw < 2) break;

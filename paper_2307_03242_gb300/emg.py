@@ -128,7 +128,7 @@ class Params:
     smoother: int = 0                # VANKA_FULL or VANKA_ECONOMIC
     sweep_path: int = 0              # SWEEP_AUTO (timed per level at creation) or a forced SWEEP_* path
     # COARSE_KACZMARZ (0: the paper's value -- 10 steps, damping 0.8, drop 0.1, FGMRES(5), at most
-    # 250 Kaczmarz steps; boxes: the smallest cube the GPU can sweep all at once)
+    # 250 Kaczmarz steps; boxes: the smallest cube of >= 2 cells the GPU can sweep all at once)
     kaczmarz_box: object = 0         # cells per axis: an int or one per axis
     kaczmarz_steps: int = 0
     kaczmarz_damping: float = 0.0

@@ -34,6 +34,8 @@ HD void cell_rows_adjoint(const FineFF3& g, const cx<TI>* x, const cx<double>* b
     return g.edge[3 - c - e][lat(g, a, bb, cc)];
   };
   cx<double> out[4];
+  // every loop is unrolled, so that no array is indexed at run time (no local memory)
+  #pragma unroll
   for (int c = 0; c < 3; ++c) {
     if (q[c] < 1) {
       out[c] = czero<double>();
@@ -41,14 +43,18 @@ HD void cell_rows_adjoint(const FineFF3& g, const cx<TI>* x, const cx<double>* b
     }
     cacc r;
     const cx<TI>* u = x + c * N;
+    #pragma unroll
     for (int dk = -1; dk <= 1; ++dk)
+      #pragma unroll
       for (int dj = -1; dj <= 1; ++dj)
+        #pragma unroll
         for (int di = -1; di <= 1; ++di) {
           const int a = i + di, bb = j + dj, cc = k + dk;
           const int qa[3] = {a, bb, cc};
           if (!inside(a, bb, cc) || qa[c] < 1) continue;
           const int dl[3] = {di, dj, dk};
           f2 C = {0.f, 0.f};
+          #pragma unroll
           for (int e = 0; e < 3; ++e) {
             // part_e of row q + delta at offset -delta_e
             int s[3] = {0, 0, 0};
@@ -73,7 +79,9 @@ HD void cell_rows_adjoint(const FineFF3& g, const cx<TI>* x, const cx<double>* b
       cacc s;
       const cx<TI> u0 = u[kq];
       s.rterm(g.beta, ld(u0.re), ld(u0.im));
+      #pragma unroll
       for (int t = 0; t < 3; ++t)
+        #pragma unroll
         for (int sg = -1; sg <= 1; sg += 2) {
           int o[3] = {i, j, k};
           o[t] += sg;
@@ -92,7 +100,9 @@ HD void cell_rows_adjoint(const FineFF3& g, const cx<TI>* x, const cx<double>* b
     {
       const int t1 = (c + 1) % 3, t2 = (c + 2) % 3;
       const cx<TI>* p = x + 3 * N;
+      #pragma unroll
       for (int a = -1; a <= 1; ++a)
+        #pragma unroll
         for (int bb = -1; bb <= 1; ++bb) {
           int o[3] = {i, j, k};
           o[t1] += a;
@@ -115,6 +125,7 @@ HD void cell_rows_adjoint(const FineFF3& g, const cx<TI>* x, const cx<double>* b
   {
     // p row: (1/h) sum_c (x_c(q) - x_c(q + s_c)) + cp(q) p(q)
     cacc r;
+    #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const cx<TI>* u = x + c * N;
       if (q[c] >= 1) {
@@ -132,6 +143,7 @@ HD void cell_rows_adjoint(const FineFF3& g, const cx<TI>* x, const cx<double>* b
     r.rterm(g.cp[kq], ld(pc.re), ld(pc.im));
     out[3] = mkc<double>(r.re.to_double(), r.im.to_double());
   }
+  #pragma unroll
   for (int c = 0; c < 4; ++c) {
     cx<double> v = out[c];
     if (b) v = (c < 3 && q[c] < 1) ? czero<double>() : bscale * b[c * N + kq] - v;

@@ -201,7 +201,7 @@ KzCfg kz_cfg(const emg_params& p) {
 int kz_region_halfwarps(int dim, const int n[3], const int box[3], size_t cb) {
   const kz::Boxes B = kz::make_boxes(dim, n, box);
   const size_t per_hw = (size_t)kz::half_warp_smem(B, dim) * cb;
-  const size_t table = ((size_t)B.RS * 4 + 15) / 16 * 16;
+  const size_t table = ((size_t)(B.RS + 2 * dim * (dim == 3 ? kz::Shape<3>::SL : kz::Shape<2>::SL) * kz::HW) * 4 + 15) / 16 * 16;
   if (table >= 200 * 1024) return 0;
   int w = (int)((200 * 1024 - table) / per_hw);
   if (w > kz::NT / kz::HW) w = kz::NT / kz::HW;

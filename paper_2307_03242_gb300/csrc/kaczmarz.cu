@@ -42,7 +42,7 @@ cudaError_t plan_solve(int sms, int RS, const int box[3], KzLaunch& out) {
   // half-warps with a private region: as many as fit beside the block's region-layout table, an
   // even number (both halves of a warp)
   const size_t per_hw = (size_t)(RS + kz::PD * kz::Ring<D>::SLOT) * sizeof(cx<T>);
-  const size_t table = ((size_t)RS * sizeof(int) + 15) / 16 * 16;
+  const size_t table = ((size_t)(RS + 2 * D * kz::Shape<D>::SL * kz::HW) * sizeof(int) + 15) / 16 * 16;
   if (table >= kRegionBudget) return cudaErrorInvalidValue;
   int warps = (int)((kRegionBudget - table) / per_hw);
   if (warps > kz::NT / kz::HW) warps = kz::NT / kz::HW;

@@ -235,11 +235,10 @@ HD cx<T> schur_rhs(const Grid<T>& g, const cx<T>* b, size_t q) {
   const size_t N = (size_t)n[0] * n[1] * n[2];
   const int c = (int)(q / N);
   const size_t cell = q % N;
-  int k[3] = {(int)(cell % n[0]), (int)((cell / n[0]) % n[1]), D == 3 ? (int)(cell / ((size_t)n[0] * n[1])) : 0};
-  if (k[c] < 1) return czero<T>();
+  const int k[3] = {(int)(cell % n[0]), (int)((cell / n[0]) % n[1]), D == 3 ? (int)(cell / ((size_t)n[0] * n[1])) : 0};
+  if ((c == 0 ? k[0] : (c == 1 ? k[1] : k[2])) < 1) return czero<T>();
   const cx<T>* bp = b + (size_t)D * N;
-  k[c] -= 1;
-  const size_t km = cell_of(n, D, k[0], k[1], k[2]);
+  const size_t km = cell_of(n, D, k[0] - (c == 0), k[1] - (c == 1), k[2] - (c == 2));
   const cx<T> gq = (T(1) / g.cp[cell]) * bp[cell] - (T(1) / g.cp[km]) * bp[km];
   return b[q] - g.ih * gq;
 }
@@ -416,6 +415,19 @@ struct LaneTab {
     return v;
   }
 };
+// The lane tables of a block in shared memory: entry (c, t) of lane l at [(c SL + t) HW + l];
+// after them, at the same index + D SL HW, the entry's region strides rx | (rx ry) << 16, so that
+// the sweep finds an entry's position without reading the box geometry at a lane-dependent index.
+template <int D>
+struct LaneTabSm {
+  const int* v;
+  __device__ __forceinline__ int get(int c, int t) const {
+    return v[(c * Shape<D>::SL + t) * HW + (threadIdx.x & (HW - 1))];
+  }
+  __device__ __forceinline__ int strides(int c, int t) const {
+    return v[(D * Shape<D>::SL + c * Shape<D>::SL + t) * HW + (threadIdx.x & (HW - 1))];
+  }
+};
 HD int pk_c2(int v) { return v & 3; }
 HD int pk_o(int v, int a) { return ((v >> (2 + 3 * a)) & 7) - 2; }
 HD int pk_off(int v) { return v >> 11; }
@@ -470,6 +482,19 @@ struct Ring {
 // Complex values of shared memory a half-warp uses: its region and its ring.
 HD int half_warp_smem(const Boxes& B, int D) { return B.RS + PD * ((D == 3 ? Shape<3>::NE : Shape<2>::NE) + 2); }
 
+// Per-component region extents in registers, for the component average, which indexes them by a
+// component known only at run time (indexing the kernel-parameter copy that way puts it in
+// local memory).
+struct RegGeo {
+  int rx0, rx1, rx2, ry0, ry1, ry2, rb0, rb1, rb2;
+  __device__ __forceinline__ explicit RegGeo(const Boxes& B)
+      : rx0(B.rx[0]), rx1(B.rx[1]), rx2(B.rx[2]), ry0(B.ry[0]), ry1(B.ry[1]), ry2(B.ry[2]), rb0(B.rbase[0]),
+        rb1(B.rbase[1]), rb2(B.rbase[2]) {}
+  __device__ __forceinline__ int rx(int c) const { return c == 0 ? rx0 : (c == 1 ? rx1 : rx2); }
+  __device__ __forceinline__ int ry(int c) const { return c == 0 ? ry0 : (c == 1 ? ry1 : ry2); }
+  __device__ __forceinline__ int rbase(int c) const { return c == 0 ? rb0 : (c == 1 ? rb1 : rb2); }
+};
+
 // Box extent along axis a: FIXB cells on every axis of the grid when FIXB > 0 (boxes of 1 or 2
 // cells; the compiler then turns the index arithmetic's divisions into shifts), else the run-time
 // boxes (at least 2 cells per axis).
@@ -510,7 +535,7 @@ HD long long cursor_row(const Boxes& B, const Cursor& u, const int lo[3], unsign
 // Starts the copy of row r into ring slot `slot` (this lane's entries; lane 0 also the right-hand
 // side and the norm), or zero-fills the slot for a missing row (r < 0); commits one group.
 template <typename T, int D>
-__device__ __forceinline__ void stage_row(const Args<T>& a, const LaneTab<D>& tab, const cx<T>* rhs, long long r,
+__device__ __forceinline__ void stage_row(const Args<T>& a, const LaneTabSm<D>& tab, const cx<T>* rhs, long long r,
                                           int c, int hl, cx<T>* slot) {
   constexpr int NE = Shape<D>::NE, SL = Shape<D>::SL;
   if (r >= 0) {
@@ -550,9 +575,10 @@ HD int region_code(const Boxes& B, int t) {
 // reg: the half-warp's region, followed by its ring of PD row slots; rtab: region_code of every
 // region entry (shared by the block).
 template <typename T, int D, int FIXB>
-__device__ void sweep_boxes(const Args<T>& a, const LaneTab<D>& tab, const cx<T>* rhs, const cx<T>* xin, cx<T>* reg,
+__device__ void sweep_boxes(const Args<T>& a, const LaneTabSm<D>& tab, const cx<T>* rhs, const cx<T>* xin, cx<T>* reg,
                             const int* rtab, int ghw, int nhw) {
   constexpr int NE = Shape<D>::NE, SL = Shape<D>::SL, SLOT = Ring<D>::SLOT;
+  constexpr int RB = D == 3 ? 4 : 8;  // region loads in flight per lane (fewer in 3D: registers)
   const int hl = threadIdx.x & (HW - 1);
   const Boxes& B = a.B;
   const unsigned N = (unsigned)a.N;
@@ -581,11 +607,11 @@ __device__ void sweep_boxes(const Args<T>& a, const LaneTab<D>& tab, const cx<T>
       stage_row<T, D>(a, tab, rhs, r, 0, hl, slot);
     };
     for (int q = 0; q < PD - 1; ++q) stage_next(ring + q * SLOT);
-    // the region from xin, 8 independent loads in flight per lane
-    for (int t0 = hl; t0 < B.RS; t0 += 8 * HW) {
-      cx<T> v[8];
+    // the region from xin, RB independent loads in flight per lane
+    for (int t0 = hl; t0 < B.RS; t0 += RB * HW) {
+      cx<T> v[RB];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < RB; ++u) {
         const int t = t0 + u * HW;
         v[u] = czero<T>();
         if (live && xin && t < B.RS) {
@@ -603,7 +629,7 @@ __device__ void sweep_boxes(const Args<T>& a, const LaneTab<D>& tab, const cx<T>
         }
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
+      for (int u = 0; u < RB; ++u)
         if (t0 + u * HW < B.RS) reg[t0 + u * HW] = v[u];
     }
     Cursor cu;
@@ -623,7 +649,9 @@ __device__ void sweep_boxes(const Args<T>& a, const LaneTab<D>& tab, const cx<T>
         co[t] = czero<T>();
         if (pk >= 0) {
           const int cc = pk_c2(pk);
-          idx[t] = pk_off(pk) + (cu.l[2] * B.ry[cc] + cu.l[1]) * B.rx[cc] + cu.l[0];
+          const int st2 = tab.strides(c, t);
+          idx[t] = pk_off(pk) + cu.l[2] * (st2 >> 16) + cu.l[1] * (st2 & 0xffff) + cu.l[0];
+          (void)cc;
           co[t] = sl[hl + HW * t];
           const cx<T> xv = reg[idx[t]];
           sr += co[t].re * xv.re - co[t].im * xv.im;
@@ -664,6 +692,7 @@ __device__ void sweep_boxes(const Args<T>& a, const LaneTab<D>& tab, const cx<T>
 template <typename T, int D, int FIXB>
 __device__ void average(const Args<T>& a, cx<T>* out, size_t tid, size_t nthr) {
   const Boxes& B = a.B;
+  const RegGeo rg(B);
   const unsigned N = (unsigned)a.N, n0 = (unsigned)B.n[0], n1 = (unsigned)B.n[1];
   const unsigned DN = (unsigned)D * N;
   for (unsigned q = (unsigned)tid; q < DN; q += (unsigned)nthr) {
@@ -671,7 +700,7 @@ __device__ void average(const Args<T>& a, cx<T>* out, size_t tid, size_t nthr) {
     const unsigned cell = q - (unsigned)c2 * N;
     const unsigned t = cell / n0;
     const int m[3] = {(int)(cell - t * n0), (int)(D == 3 ? t % n1 : t), D == 3 ? (int)(t / n1) : 0};
-    if (m[c2] < 1) {
+    if ((c2 == 0 ? m[0] : (c2 == 1 ? m[1] : m[2])) < 1) {  // (selects: no run-time-indexed array)
       out[q] = czero<T>();
       continue;
     }
@@ -688,29 +717,11 @@ __device__ void average(const Args<T>& a, cx<T>* out, size_t tid, size_t nthr) {
       blo[ax] = lo < 0 ? 0 : lo;
       bhi[ax] = hi > B.nb[ax] - 1 ? B.nb[ax] - 1 : hi;
     }
-    const int rx = B.rx[c2], ry = B.ry[c2];
-    // every candidate box's copy loaded before any is summed (independent loads), then summed
-    // in box order; CA candidates per axis (4 for boxes of one cell, else 3)
+    const int rx = rg.rx(c2), ry = rg.ry(c2), rb = rg.rbase(c2);
+    // the candidate boxes in box order, CA per axis (4 for boxes of one cell, else 3); the loop is
+    // unrolled, so the loads are independent and the compiler issues them ahead of the sums
     constexpr int CA = FIXB == 1 ? 4 : 3;
     constexpr int NZ = D == 3 ? CA : 1;
-    cx<T> v[NZ * CA * CA];
-#pragma unroll
-    for (int dz = 0; dz < NZ; ++dz)
-#pragma unroll
-      for (int dy = 0; dy < CA; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < CA; ++dx) {
-          const int bz = blo[2] + dz, by = blo[1] + dy, bxx = blo[0] + dx;
-          const int u = (dz * CA + dy) * CA + dx;
-          v[u] = czero<T>();
-          if (bz <= bhi[2] && by <= bhi[1] && bxx <= bhi[0]) {
-            const int box = (bz * B.nb[1] + by) * B.nb[0] + bxx;
-            const int lz = D == 3 ? m[2] - (bz * bsz<D, FIXB>(B, 2) - reach_lo(c2, 2)) : 0;
-            const int ly = m[1] - (by * bsz<D, FIXB>(B, 1) - reach_lo(c2, 1));
-            const int lx = m[0] - (bxx * bsz<D, FIXB>(B, 0) - reach_lo(c2, 0));
-            v[u] = ldcg(a.copies + (size_t)box * B.RS + B.rbase[c2] + (lz * ry + ly) * rx + lx);
-          }
-        }
     T sr = T(0), si = T(0);
     int cnt = 0;
 #pragma unroll
@@ -718,20 +729,26 @@ __device__ void average(const Args<T>& a, cx<T>* out, size_t tid, size_t nthr) {
 #pragma unroll
       for (int dy = 0; dy < CA; ++dy)
 #pragma unroll
-        for (int dx = 0; dx < CA; ++dx)
-          if (blo[2] + dz <= bhi[2] && blo[1] + dy <= bhi[1] && blo[0] + dx <= bhi[0]) {
-            const cx<T> w = v[(dz * CA + dy) * CA + dx];
+        for (int dx = 0; dx < CA; ++dx) {
+          const int bz = blo[2] + dz, by = blo[1] + dy, bxx = blo[0] + dx;
+          if (bz <= bhi[2] && by <= bhi[1] && bxx <= bhi[0]) {
+            const int box = (bz * B.nb[1] + by) * B.nb[0] + bxx;
+            const int lz = D == 3 ? m[2] - (bz * bsz<D, FIXB>(B, 2) - reach_lo(c2, 2)) : 0;
+            const int ly = m[1] - (by * bsz<D, FIXB>(B, 1) - reach_lo(c2, 1));
+            const int lx = m[0] - (bxx * bsz<D, FIXB>(B, 0) - reach_lo(c2, 0));
+            const cx<T> w = ldcg(a.copies + (size_t)box * B.RS + rb + (lz * ry + ly) * rx + lx);
             sr += w.re;
             si += w.im;
             ++cnt;
           }
+        }
     out[q] = mkc<T>(sr / T(cnt), si / T(cnt));
   }
 }
 
 // S z at row r (or 0 for r < 0) as this half-warp's lanes' shares summed over the half-warp.
 template <typename T, int D>
-__device__ __forceinline__ cx<T> row_dot(const Args<T>& a, const LaneTab<D>& tab, const cx<T>* z, long long r, int hl) {
+__device__ __forceinline__ cx<T> row_dot(const Args<T>& a, const LaneTabSm<D>& tab, const cx<T>* z, long long r, int hl) {
   constexpr int NE = Shape<D>::NE, SL = Shape<D>::SL;
   const Boxes& B = a.B;
   const size_t N = a.N;
@@ -740,7 +757,7 @@ __device__ __forceinline__ cx<T> row_dot(const Args<T>& a, const LaneTab<D>& tab
     const int c = (int)(r / N);
     const size_t cell = r % N;
     const int k[3] = {(int)(cell % B.n[0]), (int)((cell / B.n[0]) % B.n[1]), D == 3 ? (int)(cell / ((size_t)B.n[0] * B.n[1])) : 0};
-    if (k[c] >= 1) {
+    if ((c == 0 ? k[0] : (c == 1 ? k[1] : k[2])) >= 1) {
 #pragma unroll
       for (int t = 0; t < SL; ++t) {
         const int pk = tab.get(c, t);
@@ -768,7 +785,7 @@ __device__ __forceinline__ cx<T> row_dot(const Args<T>& a, const LaneTab<D>& tab
 // w = S z (or rhs - S z), one row per half-warp and two rows in flight; adds this thread's share
 // of sum conj(v) w (v given) or of |w|^2 (v == nullptr) to (dre, dim_).
 template <typename T, int D>
-__device__ void matvec(const Args<T>& a, const LaneTab<D>& tab, const cx<T>* z, const cx<T>* rhs, cx<T>* w,
+__device__ void matvec(const Args<T>& a, const LaneTabSm<D>& tab, const cx<T>* z, const cx<T>* rhs, cx<T>* w,
                        const cx<T>* v, double& dre, double& dim_, int ghw, int nhw) {
   const int hl = threadIdx.x & (HW - 1);
   const long long rows = (long long)D * a.N;
@@ -802,8 +819,10 @@ __device__ void matvec(const Args<T>& a, const LaneTab<D>& tab, const cx<T>* z, 
   }
 }
 
+// The parameter block is __grid_constant__: the kernels index its box geometry by components known
+// only at run time, which on an ordinary parameter makes the compiler copy it to local memory.
 template <typename T, int D, int FIXB>
-__global__ void __launch_bounds__(NT, 1) solve(Args<T> a) {
+__global__ void __launch_bounds__(NT, 1) solve(const __grid_constant__ Args<T> a) {
   extern __shared__ __align__(16) unsigned char kz_smem[];
   __shared__ Shared sh;
   const int hwb = threadIdx.x / HW;  // half-warp in the block
@@ -811,14 +830,28 @@ __global__ void __launch_bounds__(NT, 1) solve(Args<T> a) {
   cx<T>* reg = reinterpret_cast<cx<T>*>(kz_smem) + (size_t)(hwb < a.warps_a ? hwb : 0) * half_warp_smem(a.B, D);
   const size_t tid = (size_t)blockIdx.x * NT + threadIdx.x, nthr = (size_t)gridDim.x * NT;
   const int ghw_all = blockIdx.x * (NT / HW) + hwb, nhw_all = gridDim.x * (NT / HW);
-  const int ghw_a = blockIdx.x * a.warps_a + hwb, nhw_a = gridDim.x * a.warps_a;
+  // box-sweeping half-warps numbered block-fastest, so that a grid with few boxes still spreads
+  // them over every SM; the two halves of a warp stay consecutive (they run in lock-step)
+  const int ghw_a = ((hwb >> 1) * gridDim.x + blockIdx.x) * 2 + (hwb & 1), nhw_a = gridDim.x * a.warps_a;
   const size_t N = a.N, DN = (size_t)D * N;
   const Grid<T>& g = a.g;
-  LaneTab<D> tab;
-  tab.init(a.B, threadIdx.x & (HW - 1));
-  // the region layout, after the half-warps' regions and rings (read after the first barrier)
+  // the region layout and the lane tables, after the half-warps' regions and rings (read after
+  // the first barrier)
   int* rtab = reinterpret_cast<int*>(reinterpret_cast<cx<T>*>(kz_smem) + (size_t)a.warps_a * half_warp_smem(a.B, D));
   for (int t = threadIdx.x; t < a.B.RS; t += NT) rtab[t] = region_code(a.B, t);
+  int* ltab = rtab + a.B.RS;
+  if (threadIdx.x < HW) {
+    LaneTab<D> lt;
+    lt.init(a.B, threadIdx.x);
+    for (int c = 0; c < D; ++c)
+      for (int t = 0; t < Shape<D>::SL; ++t) {
+        const int pk = lt.pk[c][t];
+        ltab[(c * Shape<D>::SL + t) * HW + threadIdx.x] = pk;
+        const int cc = pk >= 0 ? pk_c2(pk) : 0;
+        ltab[(D * Shape<D>::SL + c * Shape<D>::SL + t) * HW + threadIdx.x] = a.B.rx[cc] | (a.B.rx[cc] * a.B.ry[cc]) << 16;
+      }
+  }
+  const LaneTabSm<D> tab{ltab};
   int parity = 0;
   cx<double> red;
 

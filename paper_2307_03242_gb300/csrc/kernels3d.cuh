@@ -139,6 +139,8 @@ __global__ void __launch_bounds__(BX * BY * BZ) prolong_add(const cx<T>* __restr
   // per-axis cell-type interpolation: two coarse indices with weights 3/4, 1/4
   int ci[3][2];
   T cw[3][2];
+  // every loop is unrolled, so that no array is indexed at run time (no local memory)
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int K0 = f[a] >> 1;
     ci[a][0] = K0;
@@ -152,6 +154,7 @@ __global__ void __launch_bounds__(BX * BY * BZ) prolong_add(const cx<T>* __restr
     if (comp < 3 && IC[comp] == 0) return czero<T>();
     return ec[((size_t)K * nyc + J) * nxc + I];
   };
+#pragma unroll
   for (int c = 0; c < 4; ++c) {
     const cx<T>* ec = e + c * Nc;
     if (c < 3 && f[c] == 0) {
@@ -162,6 +165,7 @@ __global__ void __launch_bounds__(BX * BY * BZ) prolong_add(const cx<T>* __restr
     int idx[3][2];
     T wgt[3][2];
     int cnt[3];
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
       if (a == c) {  // face axis: even -> coarse face f/2; odd -> mean of f/2 and f/2+1
         idx[a][0] = f[a] >> 1;
@@ -178,10 +182,14 @@ __global__ void __launch_bounds__(BX * BY * BZ) prolong_add(const cx<T>* __restr
       }
     }
     cx<T> acc = czero<T>();
-    for (int s2_ = 0; s2_ < cnt[2]; ++s2_)
-      for (int s1 = 0; s1 < cnt[1]; ++s1)
-        for (int s0 = 0; s0 < cnt[0]; ++s0)
-          acc = acc + (wgt[0][s0] * wgt[1][s1] * wgt[2][s2_]) * ev(ec, c, idx[0][s0], idx[1][s1], idx[2][s2_]);
+#pragma unroll
+    for (int s2_ = 0; s2_ < 2; ++s2_)
+#pragma unroll
+      for (int s1 = 0; s1 < 2; ++s1)
+#pragma unroll
+        for (int s0 = 0; s0 < 2; ++s0)
+          if (s2_ < cnt[2] && s1 < cnt[1] && s0 < cnt[0])
+            acc = acc + (wgt[0][s0] * wgt[1][s1] * wgt[2][s2_]) * ev(ec, c, idx[0][s0], idx[1][s1], idx[2][s2_]);
     x[c * N + q] = x[c * N + q] + acc;
   }
   (void)nc;

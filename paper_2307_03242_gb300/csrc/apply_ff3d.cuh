@@ -51,15 +51,11 @@ HD void cell_rows(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double
     return m;
   };
   cx<double> out[4];
-  // every loop below is unrolled, so that no array is indexed at run time (which would put it,
-  // and the descriptor's W, edge and m arrays, in local memory)
-#pragma unroll
   for (int c = 0; c < 3; ++c) {
     cacc r;
     if (q[c] >= 1) {
       // part_e for the three derivative axes
       f2 part[3][3];
-#pragma unroll
       for (int e = 0; e < 3; ++e) {
         f2 ma, mb;
         int s[3] = {0, 0, 0};
@@ -77,18 +73,14 @@ HD void cell_rows(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double
         part[e][2] = fneg(mb);
       }
       const cx<TI>* u = x + c * N;
-#pragma unroll
       for (int dk = -1; dk <= 1; ++dk)
-#pragma unroll
         for (int dj = -1; dj <= 1; ++dj)
-#pragma unroll
           for (int di = -1; di <= 1; ++di) {
             const int a = i + di, bb = j + dj, cc = k + dk;
             const int qa[3] = {a, bb, cc};
             if (!inside(a, bb, cc) || qa[c] < 1) continue;
             const int dl[3] = {di, dj, dk};
             f2 C = {0.f, 0.f};
-#pragma unroll
             for (int e = 0; e < 3; ++e) {
               const int t1 = (e + 1) % 3, t2 = (e + 2) % 3;
               C = add(C, mul(part[e][dl[e] + 1], g.W[dl[t1] + 1][dl[t2] + 1]));
@@ -117,13 +109,10 @@ HD void cell_rows(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double
   }
   {
     cacc r;
-#pragma unroll
     for (int c = 0; c < 3; ++c) {
       const int t1 = (c + 1) % 3, t2 = (c + 2) % 3;
       const cx<TI>* u = x + c * N;
-#pragma unroll
       for (int a = -1; a <= 1; ++a)
-#pragma unroll
         for (int bb = -1; bb <= 1; ++bb) {
           int o[3] = {0, 0, 0};
           o[t1] = a;
@@ -147,7 +136,6 @@ HD void cell_rows(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double
     r.rterm(g.cp[kq], ld(pc.re), ld(pc.im));
     out[3] = mkc<double>(r.re.to_double(), r.im.to_double());
   }
-#pragma unroll
   for (int c = 0; c < 4; ++c) {
     cx<double> v = out[c];
     if (b) v = (c < 3 && q[c] < 1) ? czero<double>() : bscale * b[c * N + kq] - v;

@@ -99,9 +99,10 @@ def hot_kernel_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_profile(key):
+def recorded_profile(key, n):
     """A per-launch figure (DRAM bytes, FP32 flops) from the committed ncu summary of the dominant
-    kernel, if its sources still hash to the value recorded there; else None."""
+    kernel, if it was captured on a finest grid of n cells and its sources still hash to the value
+    recorded there; else None (DRAM traffic does not scale with the grid once it fits in L2)."""
     try:
         vals = {}
         with open(os.path.join(ROOT, HOT_KERNEL_PROFILE)) as f:
@@ -111,13 +112,15 @@ def recorded_profile(key):
                     vals[k.strip()] = v.strip()
         if vals.get("source_hash") != hot_kernel_hash():
             return None
+        if tuple(int(v) for v in vals["grid"].split("x")) != tuple(n):
+            return None
         return float(vals[key])
     except Exception:
         return None
 
 
-def recorded_traffic():
-    return recorded_profile("dram_bytes_per_launch")
+def recorded_traffic(n):
+    return recorded_profile("dram_bytes_per_launch", n)
 
 
 # FP32 CUDA-core peak from the unit counts and the maximum clock: 152 SMs x 128 FP32 lanes x 2
@@ -424,10 +427,10 @@ def bench_single(args, w, steps, warmup, fp64_steps, cpu_baseline, e2e_steps=Non
                         "bound": "hbm", "achieved": achieved,
                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                         "frac": achieved / peak if achieved else None,
-                        "traffic": recorded_traffic() if tiled_finest(w, paths) else None,
+                        "traffic": recorded_traffic(w.n) if tiled_finest(w, paths) else None,
                         "launches": prof["launches"], "avg_launch_ms": prof["ms"] / max(prof["launches"], 1),
                         "bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
-                        "fp32": fp32_fraction(prof) if tiled_finest(w, paths) else None}),
+                        "fp32": fp32_fraction(prof, w.n) if tiled_finest(w, paths) else None}),
            "fine_level_ms_per_solve": dict({"smooth": prof["ms"] / steps},
                                            **{k: v["ms"] / steps for k, v in breakdown.items()}),
            "coarse_levels_ms_per_solve": coarse_ms,
@@ -736,10 +739,10 @@ def finest_sweep_kernel(w, paths):
             "bytes_basis": "76 B per cell per half-sweep"}
 
 
-def fp32_fraction(prof):
+def fp32_fraction(prof, n):
     """The dominant kernel's FP32 rate: its flops per launch (ncu FADD + FMUL + 2 FFMA thread
     instructions of one launch, from the committed summary) over the live mean launch time."""
-    flops = recorded_profile("fp32_flops_per_launch")
+    flops = recorded_profile("fp32_flops_per_launch", n)
     if not flops or prof["ms"] <= 0:
         return None
     tf = flops / (prof["ms"] / max(prof["launches"], 1) * 1e-3) / 1e12

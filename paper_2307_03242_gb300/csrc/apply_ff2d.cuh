@@ -195,17 +195,20 @@ HD void apply_cell(const FineFF& g, const cx<TI>* __restrict__ x, const cx<doubl
     rp.rterm(g.cp[k], ld(pc.re), ld(pc.im));
   }
   auto out = [&](const cacc& a) { return mkc<double>(a.re.to_double(), a.im.to_double()); };
-  cx<double> y1 = i >= 1 ? out(r1) : czero<double>();
-  cx<double> y2 = j >= 1 ? out(r2) : czero<double>();
-  cx<double> yp = out(rp);
   if (b) {
-    y1 = i >= 1 ? bscale * b[k] - y1 : czero<double>();
-    y2 = j >= 1 ? bscale * b[N + k] - y2 : czero<double>();
-    yp = bscale * b[2 * N + k] - yp;
+    // bscale * b - H x in float-float when bscale is a power of two in the float range
+    const float bs = df::pow2_float(bscale);
+    auto res = [&](const cacc& a, cx<double> bv) {
+      return mkc<double>(df::scaled_sub(bv.re, bs, bscale, a.re), df::scaled_sub(bv.im, bs, bscale, a.im));
+    };
+    out3[0] = i >= 1 ? res(r1, b[k]) : czero<double>();
+    out3[1] = j >= 1 ? res(r2, b[N + k]) : czero<double>();
+    out3[2] = res(rp, b[2 * N + k]);
+  } else {
+    out3[0] = i >= 1 ? out(r1) : czero<double>();
+    out3[1] = j >= 1 ? out(r2) : czero<double>();
+    out3[2] = out(rp);
   }
-  out3[0] = y1;
-  out3[1] = y2;
-  out3[2] = yp;
   (void)z;
 }
 

@@ -87,26 +87,60 @@ HD f2 split(double x) {
   return r;
 }
 
-// A float widened to a double by assembling its bits (no FP64 instruction); subnormal floats
-// take the plain conversion.
-HD double widen(float f) {
+// Leading-zero count of a nonzero 32-bit word.
+HD int clz32(unsigned v) {
+#ifdef __CUDA_ARCH__
+  return __clz((int)v);
+#else
+  return __builtin_clz(v);
+#endif
+}
+
+// Bits of a float widened to a double, assembled with integer operations only (no FP64
+// instruction, no conversion): normal floats move their exponent and mantissa, subnormal ones are
+// normalised with a leading-zero count, infinities and NaNs keep their class and payload.
+HD unsigned long long widen_bits(float f) {
   const unsigned u = fbits(f);
   const unsigned ex = (u >> 23) & 0xffu, m = u & 0x7fffffu;
   const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
-  if (ex == 0) return m == 0 ? bdouble(sgn) : (double)f;
+  if (ex == 0) {
+    if (m == 0) return sgn;
+    const int p = 31 - clz32(m);  // leading bit of the subnormal mantissa: the value is 1.f 2^(p-149)
+    return sgn | ((unsigned long long)(p + 874) << 52) | (((unsigned long long)m << (52 - p)) & 0xfffffffffffffull);
+  }
   const unsigned long long dex = ex == 255 ? 0x7ffull : (unsigned long long)(ex + 896);
-  return bdouble(sgn | (dex << 52) | ((unsigned long long)m << 29));
+  return sgn | (dex << 52) | ((unsigned long long)m << 29);
 }
-
-// hi + lo as a double: two assembled widenings and one FP64 addition (instead of two conversions
-// and an addition on the FP64 pipe).
-HD double join(float hi, float lo) { return widen(hi) + widen(lo); }
+HD double widen(float f) { return bdouble(widen_bits(f)); }
 
 // Knuth TwoSum: s + e == a + b exactly.
 HD void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   float bb = s - a;
   e = (a - (s - bb)) + (b - bb);
+}
+
+// hi + lo as a double with FP32 and integer operations only. The pair is first normalised with
+// TwoSum (exact: s + e = hi + lo, |e| <= ulp(s)/2). e is then added to the bits of s widened:
+// in units of the double ulp of s, 2^(E_s - 52), e is its 24-bit integer mantissa shifted by
+// E_e - E_s + 29 <= 5 (one more when s is a power of two and e has the opposite sign, whose sum
+// lies in the binade below, where the unit is half as large). Adding or subtracting that integer
+// to the bit pattern is exact for the bits that fit in 53; the bits of e below the double's
+// last place are truncated (an error below one ulp of the result).
+HD double join(float hi, float lo) {
+  float s, e;
+  two_sum(hi, lo, s, e);
+  const unsigned long long d = widen_bits(s);
+  const unsigned us = fbits(s), ue = fbits(e);
+  const int es = (int)((us >> 23) & 0xffu), ee = (int)((ue >> 23) & 0xffu);
+  const unsigned me = (ue & 0x7fffffu) | (ee != 0 ? 0x800000u : 0u);
+  if (es == 0 || es == 255 || me == 0) return bdouble(d);  // zero, subnormal (e is 0), non-finite
+  const bool opp = ((us ^ ue) >> 31) != 0;
+  int sh = (ee != 0 ? ee : 1) - es + 29;
+  if (opp && (us & 0x7fffffu) == 0) sh += 1;
+  const unsigned long long off =
+      sh >= 0 ? ((unsigned long long)me << sh) : (sh > -32 ? (unsigned long long)(me >> -sh) : 0ull);
+  return bdouble(opp ? d - off : d + off);
 }
 
 // Accumulator: hi + lo (lo unnormalised).
@@ -134,6 +168,13 @@ struct acc {
     hi = s;
     lo += t + a.lo;
   }
+  // += a (a float)
+  HD void add(float a) {
+    float s, t;
+    two_sum(hi, a, s, t);
+    hi = s;
+    lo += t;
+  }
   HD double to_double() const { return join(hi, lo); }
   HD f2 norm() const {
     f2 r;
@@ -141,5 +182,30 @@ struct acc {
     return r;
   }
 };
+
+
+// x as a float when it is a power of two inside the normal float range, else 0 (integer
+// operations on the bits of x).
+HD float pow2_float(double x) {
+  const unsigned long long b = dbits(x);
+  if (b & 0xfffffffffffffull) return 0.0f;
+  const int e = (int)((b >> 52) & 0x7ffu) - 1023;
+  if (e < -126 || e > 127) return 0.0f;
+  return bfloat((unsigned)(b >> 32 & 0x80000000u) | ((unsigned)(e + 127) << 23));
+}
+
+// bscale * b - r as a double. With bs = pow2_float(bscale) != 0 it is evaluated in float-float
+// (the scaling of the split b by a power of two is exact) and assembled without FP64
+// instructions; otherwise in FP64.
+HD double scaled_sub(double b, float bs, double bscale, const acc& r) {
+  if (bs == 0.0f) return bscale * b - r.to_double();
+  const f2 bb = split(b);
+  acc t;
+  t.hi = bb.hi * bs;
+  t.lo = bb.lo * bs;
+  const f2 rn = r.norm();
+  t.add({-rn.hi, -rn.lo});
+  return t.to_double();
+}
 
 }  // namespace df

@@ -78,6 +78,7 @@ inline FineFF3 make(const HostFF3& o, const f2* mu, const f2* cp, const f2* cons
   g.ih2 = to_f2(1.0 / (h * h));
   g.beta = to_f2(beta);
   g.sm = to_f2((1.0 - beta) / 6.0);
+  g.kap = to_f2((1.0 - beta) / 16.0);
   g.alpha = to_f2(alpha);
   for (int a = -1; a <= 1; ++a)
     for (int b = -1; b <= 1; ++b) {

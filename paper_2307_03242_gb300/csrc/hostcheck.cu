@@ -629,6 +629,12 @@ int emg_hc_split_join(const double* x, int n, float* hi, float* lo, double* join
   return 0;
 }
 
+// df::join on n arbitrary float pairs (the FP64 value of hi + lo).
+int emg_hc_join(const float* hi, const float* lo, int n, double* out) {
+  for (int k = 0; k < n; ++k) out[k] = df::join(hi[k], lo[k]);
+  return 0;
+}
+
 // x += P e, then `sweeps` one-pass tiled sweeps with the correction added by the first one's tile
 // loads (the fused post-smoothing of the cycle); e: complex128 coarse vector of 3 (nx/2)(ny/2).
 int emg_hc_prolong_sweep_tiled(const int* n, double h, double beta, double omega, double att, double abl_len,
@@ -695,6 +701,52 @@ int emg_hc_apply_ff3(const int* n, double h, double beta, double omega, double g
     for (int j = 0; j < n[1]; ++j)
       for (int i = 0; i < n[0]; ++i)
         ff3::cell_rows<double>(g, (const cx<double>*)x, nullptr, 0.0, (cx<double>*)y, i, j, k);
+  return 0;
+}
+
+// The outer solve's residual form y = bscale * b - H x in float-float arithmetic, 2D (d = 2, L
+// unused) or 3D (ff2::apply_cell / ff3::cell_rows), x FP64 (x32 = 0) or rounded to FP32 first
+// (x32 = 1); b == NULL gives y = H x.
+int emg_hc_residual_ff(int d, const int* n, double h, double beta, double omega, double gamma, double abl_len,
+                       double abl_gmax, const double* L, const double* lam, const double* mu, const double* rho,
+                       const double* x, const double* b, double bscale, double* y, int x32) {
+  const size_t N = (size_t)n[0] * n[1] * (d == 3 ? n[2] : 1), nv = (size_t)(d + 1) * N;
+  std::vector<cx<double>> xd(nv);
+  std::vector<cx<float>> xf(nv);
+  for (size_t k = 0; k < nv; ++k) {
+    xd[k] = mkc<double>(x[2 * k], x[2 * k + 1]);
+    xf[k] = mkc<float>((float)x[2 * k], (float)x[2 * k + 1]);
+  }
+  const cx<double>* bb = (const cx<double>*)b;
+  if (d == 2) {
+    ff2::HostFF2 o;
+    ff2::build_host(o, n[0], n[1], h, lam, mu, rho, omega, gamma, abl_len, abl_gmax, n[0] * h, n[1] * h);
+    const ff2::FineFF g = ff2::make(o.mu.data(), o.mun.data(), o.cp.data(), o.m1.data(), o.m2.data(), n[0], n[1], h,
+                                    beta, 0.0);
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) {
+        cx<double> out[3];
+        if (x32) ff2::apply_cell<float>(g, xf.data(), bb, bscale, i, j, out);
+        else ff2::apply_cell<double>(g, xd.data(), bb, bscale, i, j, out);
+        for (int c = 0; c < 3; ++c) {
+          const size_t q = c * N + (size_t)j * n[0] + i;
+          y[2 * q] = out[c].re;
+          y[2 * q + 1] = out[c].im;
+        }
+      }
+    return 0;
+  }
+  ff3::HostFF3 o;
+  ff3::build_host(o, n[0], n[1], n[2], h, lam, mu, rho, omega, gamma, abl_len, abl_gmax, L);
+  const df::f2* edge[3] = {o.edge[0].data(), o.edge[1].data(), o.edge[2].data()};
+  const ff2::c2* m[3] = {o.m[0].data(), o.m[1].data(), o.m[2].data()};
+  const ff3::FineFF3 g = ff3::make(o, o.mu.data(), o.cp.data(), edge, m, n[0], n[1], n[2], h, beta, 0.0);
+  for (int k = 0; k < n[2]; ++k)
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) {
+        if (x32) ff3::cell_rows<float>(g, xf.data(), bb, bscale, (cx<double>*)y, i, j, k);
+        else ff3::cell_rows<double>(g, xd.data(), bb, bscale, (cx<double>*)y, i, j, k);
+      }
   return 0;
 }
 

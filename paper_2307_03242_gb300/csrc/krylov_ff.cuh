@@ -1,6 +1,7 @@
 // FP64 Krylov vector kernels evaluated in double-FP32 arithmetic (dfloat.cuh): the vectors are
 // IEEE FP64 in memory, every product and sum is carried with ~48 significant bits on the FP32
-// pipe, and only per-thread partial sums and final stores touch the FP64 pipe.
+// pipe, and doubles are split and assembled with integer operations, so that no FP64
+// instruction runs per element (this part's FP64 pipe is ~57x slower than its FP32 pipe).
 #pragma once
 #include "dfloat.cuh"
 #include "vector_kernels.cuh"
@@ -13,6 +14,41 @@ constexpr int RT = kv::RT;
 // Elements per thread and loop iteration: their loads are issued together, so that enough bytes
 // are in flight per thread to cover the HBM latency (the vectors are 100s of MB).
 constexpr int UPD = 4;
+
+// Warp sum of float-float values by an XOR butterfly; TwoSum is exact and symmetric in its
+// operands, so every lane ends with the same sum.
+__device__ __forceinline__ f2 warp_sum_ff(f2 v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float h = __shfl_xor_sync(0xffffffffu, v.hi, off), l = __shfl_xor_sync(0xffffffffu, v.lo, off);
+    float s, t;
+    df::two_sum(v.hi, h, s, t);
+    t += v.lo + l;
+    df::two_sum(s, t, v.hi, v.lo);
+  }
+  return v;
+}
+
+// Block sums of every thread's accumulators, in float-float on the FP32 pipe; part[blk][r] is the
+// block's sum r as a double (assembled without FP64 instructions).
+template <int NR>
+__device__ __forceinline__ void block_reduce_store_ff(const df::acc (&a)[NR], double* part) {
+  __shared__ f2 sh[RT / 32][NR];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const f2 v = warp_sum_ff(a[r].norm());
+    if (lane == 0) sh[wid][r] = v;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const f2 v = warp_sum_ff(lane < RT / 32 ? sh[lane][r] : f2{0.f, 0.f});
+      if (lane == 0) part[(size_t)blockIdx.x * NR + r] = df::join(v.hi, v.lo);
+    }
+  }
+}
 
 // part[blk][2i], [2i+1] = Re, Im of sum conj(V_i) w (i < NV); part[blk][2NV] = sum |w|^2.
 template <int NV>
@@ -56,14 +92,14 @@ __global__ void __launch_bounds__(RT) mdot(const cx<double>* __restrict__ V, siz
       ann.fma_ff(wi, wi);
     }
   }
-  double acc[2 * NV + 1];
+  df::acc all[2 * NV + 1];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    acc[2 * v] = are[v].to_double();
-    acc[2 * v + 1] = aim[v].to_double();
+    all[2 * v] = are[v];
+    all[2 * v + 1] = aim[v];
   }
-  acc[2 * NV] = ann.to_double();
-  kv::block_reduce_store<2 * NV + 1>(acc, part);
+  all[2 * NV] = ann;
+  block_reduce_store_ff<2 * NV + 1>(all, part);
 }
 
 // Complex float-float coefficient.
@@ -124,8 +160,8 @@ __global__ void __launch_bounds__(RT) update_scale(cx<double>* __restrict__ w, c
       nn.fma_ff(fi, fi);
     }
   }
-  double acc[1] = {nn.to_double()};
-  kv::block_reduce_store<1>(acc, part);
+  const df::acc all[1] = {nn};
+  block_reduce_store_ff<1>(all, part);
 }
 
 // x += sum_i y_i Z_i with Z in FP32 (exact floats) or FP64.

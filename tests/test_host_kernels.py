@@ -304,6 +304,74 @@ def test_float_float_split_and_join_are_exact_to_46_bits(hc):
     assert hi[-10] == 0 and lo[-10] == 0
 
 
+@pytest.mark.parametrize("bscale", [None, 0.125, 0.3])
+@pytest.mark.parametrize("x32", [0, 1])
+@pytest.mark.parametrize("n", [(14, 11), (9, 8, 7), (6, 6, 6)])
+def test_host_float_float_residual_form_matches_the_oracle(hc, n, x32, bscale):
+    """The outer apply's residual form y = bscale b - H x (the true residual at every restart):
+    float-float throughout when bscale is a power of two (the split b is scaled exactly), FP64
+    otherwise; x in FP64 or FP32; 2D and 3D; against the oracle's operator to 1e-12."""
+    w = small_heterogeneous(n, seed=9, levels=2, abl_cells=2, sigma_cells=2.0)
+    pb = oracle_problem(w)
+    x = random_field(pb, 81).ravel()
+    if x32:
+        x = x.astype(np.complex64).astype(np.complex128)
+    H = oracle.assemble(pb, 0.0)
+    act = oracle.active_mask(pb)
+    b = random_field(pb, 82).ravel() * 50.0
+    ref = H @ x if bscale is None else (bscale * b - H @ x) * act
+    nn = np.array(n + (1,) * (3 - len(n)), dtype=np.int32)
+    L = np.array(tuple(pb.domain) + (1.0,) * (3 - len(n)), dtype=np.float64)
+    mats = [np.ascontiguousarray(a.ravel()) for a in (pb.lam, pb.mu, pb.rho)]
+    y = np.zeros_like(ref)
+    xx, bb = np.ascontiguousarray(x), np.ascontiguousarray(b)
+    assert hc.emg_hc_residual_ff(len(n), nn.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.c_double(pb.h),
+                                 ctypes.c_double(pb.beta), ctypes.c_double(pb.omega), ctypes.c_double(pb.gamma),
+                                 ctypes.c_double(pb.abl_length), ctypes.c_double(pb.abl_gamma_max), L.ctypes.data_as(DP),
+                                 *[m.ctypes.data_as(DP) for m in mats], _cvec(xx),
+                                 None if bscale is None else _cvec(bb), ctypes.c_double(bscale or 0.0), _cvec(y),
+                                 x32) == 0
+    scale = max(np.abs(H @ x).max(), np.abs(ref).max())
+    assert np.abs((y - ref) * act).max() <= 1e-12 * scale
+    assert np.all(y[~act.astype(bool)] == 0)
+
+
+def test_float_float_join_is_within_one_ulp_of_the_exact_sum(hc):
+    """df::join (TwoSum, then integer operations on the bits: no FP64 instruction) returns hi + lo
+    truncated to a double: within one ulp of the exact sum (computed with fractions), exact where
+    the sum fits in 53 bits. Pairs: normalised (|lo| <= ulp(hi)/2), opposite signs, powers of two
+    with a lo of the other sign (the sum falls into the binade below), unnormalised pairs (lo as
+    large as hi), subnormal parts, zeros and non-finite values."""
+    from fractions import Fraction
+    rng = np.random.default_rng(11)
+    m = 4000
+    hi = (rng.standard_normal(m) * 10.0 ** rng.uniform(-20, 20, m)).astype(np.float32)
+    ulp = np.spacing(np.abs(hi)).astype(np.float64)
+    lo = (rng.uniform(-0.5, 0.5, m) * ulp).astype(np.float32)
+    p2 = np.float32(2.0) ** rng.integers(-60, 60, 500).astype(np.float32)
+    p2lo = (-np.sign(p2) * rng.uniform(0, 0.25, 500) * np.spacing(p2).astype(np.float64)).astype(np.float32)
+    big = rng.standard_normal(500).astype(np.float32)
+    biglo = (rng.standard_normal(500) * 10.0 ** rng.uniform(-9, 0, 500)).astype(np.float32)
+    tiny = np.array([1e-45, -3e-42, 1.2e-38, 2.0 ** -126, 0.0, -0.0, 1.0, 1.0], np.float32)
+    tinylo = np.array([0.0, 1e-45, -1e-45, -1e-45, 0.0, 0.0, -2.0 ** -25, 2.0 ** -40], np.float32)
+    H = np.concatenate([hi, p2, -p2, big, tiny])
+    L = np.concatenate([lo, p2lo, -p2lo, biglo, tinylo])
+    out = np.zeros(H.size)
+    fp = ctypes.POINTER(ctypes.c_float)
+    assert hc.emg_hc_join(H.ctypes.data_as(fp), L.ctypes.data_as(fp), H.size, out.ctypes.data_as(DP)) == 0
+    for h, l, o in zip(H, L, out):
+        exact = Fraction(float(h)) + Fraction(float(l))
+        err = abs(Fraction(float(o)) - exact)
+        assert err < Fraction(np.spacing(abs(float(o)))) or err == 0, (h, l, o)
+        if float(np.float64(h) + np.float64(l)) == exact:  # the sum fits in a double: exact
+            assert float(o) == float(exact), (h, l, o)
+    special = np.array([np.inf, -np.inf, np.nan, 3e38], np.float32)
+    out4 = np.zeros(4)
+    zero = np.zeros(4, np.float32)
+    assert hc.emg_hc_join(special.ctypes.data_as(fp), zero.ctypes.data_as(fp), 4, out4.ctypes.data_as(DP)) == 0
+    assert out4[0] == np.inf and out4[1] == -np.inf and np.isnan(out4[2]) and out4[3] == np.float64(np.float32(3e38))
+
+
 @pytest.mark.parametrize("ty", [24, 8])
 @pytest.mark.parametrize("case", list(TILED))
 @pytest.mark.parametrize("level", [0, 1])

@@ -4,6 +4,7 @@
 // cycle into a preconditioner for H^H. One thread per cell, grid-stride; the per-cell arithmetic
 // is adjoint.cuh, which the tests also run in a host build against the FP64 oracle.
 #include "adjoint.cuh"
+#include "apply_ff2d.cuh"
 #include "launch.h"
 
 namespace adjk {
@@ -15,9 +16,9 @@ inline int blocks_for(size_t n) {
   return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
 }
 
-template <int D, typename TI>
+template <int D, typename TI, bool FFO>
 __global__ void __launch_bounds__(RT) apply(Grid<double> g, const cx<TI>* __restrict__ x, const cx<double>* b,
-                                           double bscale, cx<double>* __restrict__ y) {
+                                           double bscale, void* __restrict__ y) {
   const size_t N = (size_t)g.nx * g.ny * g.nz;
   const cx<TI>* xs[4];
   for (int c = 0; c <= D; ++c) xs[c] = x + (size_t)c * N;
@@ -25,10 +26,10 @@ __global__ void __launch_bounds__(RT) apply(Grid<double> g, const cx<TI>* __rest
     const int i = (int)(idx % g.nx), j = (int)((idx / g.nx) % g.ny), k = (int)(idx / ((size_t)g.nx * g.ny));
     for (int c = 0; c < D; ++c) {
       const cx<double> r = adj::row_u<D, double, TI>(c, xs, g, i, j, k);
-      y[(size_t)c * N + idx] = b ? bscale * b[(size_t)c * N + idx] - r : r;
+      ff2::store_val<FFO>(y, (size_t)c * N + idx, b ? bscale * b[(size_t)c * N + idx] - r : r);
     }
     const cx<double> r = adj::row_p<D, double, TI>(xs, g, i, j, k);
-    y[(size_t)D * N + idx] = b ? bscale * b[(size_t)D * N + idx] - r : r;
+    ff2::store_val<FFO>(y, (size_t)D * N + idx, b ? bscale * b[(size_t)D * N + idx] - r : r);
   }
 }
 
@@ -70,10 +71,11 @@ __global__ void __launch_bounds__(RT) sconj(cx<float>* z, size_t nu, size_t n) {
 }  // namespace adjk
 
 template <int D, typename TI>
-void launch_adjoint_apply(const Grid<double>& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y,
-                          cudaStream_t st) {
+void launch_adjoint_apply(const Grid<double>& g, const cx<TI>* x, const cx<double>* b, double bscale, void* y,
+                          bool ffo, cudaStream_t st) {
   const size_t N = (size_t)g.nx * g.ny * g.nz;
-  adjk::apply<D, TI><<<adjk::blocks_for(N), adjk::RT, 0, st>>>(g, x, b, bscale, y);
+  if (ffo) adjk::apply<D, TI, true><<<adjk::blocks_for(N), adjk::RT, 0, st>>>(g, x, b, bscale, y);
+  else adjk::apply<D, TI, false><<<adjk::blocks_for(N), adjk::RT, 0, st>>>(g, x, b, bscale, y);
 }
 
 template <int D>
@@ -87,14 +89,14 @@ void launch_sconj(cx<float>* z, size_t nu, size_t n, cudaStream_t st) {
   adjk::sconj<<<adjk::blocks_for(n), adjk::RT, 0, st>>>(z, nu, n);
 }
 
-template void launch_adjoint_apply<2, float>(const Grid<double>&, const cx<float>*, const cx<double>*, double,
-                                             cx<double>*, cudaStream_t);
-template void launch_adjoint_apply<2, double>(const Grid<double>&, const cx<double>*, const cx<double>*, double,
-                                              cx<double>*, cudaStream_t);
-template void launch_adjoint_apply<3, float>(const Grid<double>&, const cx<float>*, const cx<double>*, double,
-                                             cx<double>*, cudaStream_t);
-template void launch_adjoint_apply<3, double>(const Grid<double>&, const cx<double>*, const cx<double>*, double,
-                                              cx<double>*, cudaStream_t);
+template void launch_adjoint_apply<2, float>(const Grid<double>&, const cx<float>*, const cx<double>*, double, void*,
+                                              bool, cudaStream_t);
+template void launch_adjoint_apply<2, double>(const Grid<double>&, const cx<double>*, const cx<double>*, double, void*,
+                                              bool, cudaStream_t);
+template void launch_adjoint_apply<3, float>(const Grid<double>&, const cx<float>*, const cx<double>*, double, void*,
+                                              bool, cudaStream_t);
+template void launch_adjoint_apply<3, double>(const Grid<double>&, const cx<double>*, const cx<double>*, double, void*,
+                                              bool, cudaStream_t);
 template void launch_adjoint_gradient<2>(const Grid<double>&, const cx<double>*, const cx<double>*, double*, double*,
                                          double*, int, cudaStream_t);
 template void launch_adjoint_gradient<3>(const Grid<double>&, const cx<double>*, const cx<double>*, double*, double*,

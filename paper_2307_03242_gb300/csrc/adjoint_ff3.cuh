@@ -12,9 +12,9 @@
 
 namespace ff3 {
 
-template <typename TI>
-HD void cell_rows_adjoint(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y, int i,
-                          int j, int k) {
+template <typename TI, bool FFO = false>
+HD void cell_rows_adjoint(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, void* y, int i, int j,
+                          int k) {
   const int q[3] = {i, j, k};
   const size_t N = (size_t)g.nx * g.ny * g.nz, kq = lin(g, i, j, k);
   auto inside = [&](int a, int bb, int c) { return a >= 0 && a < g.nx && bb >= 0 && bb < g.ny && c >= 0 && c < g.nz; };
@@ -147,19 +147,19 @@ HD void cell_rows_adjoint(const FineFF3& g, const cx<TI>* x, const cx<double>* b
   for (int c = 0; c < 4; ++c) {
     cx<double> v = out[c];
     if (b) v = (c < 3 && q[c] < 1) ? czero<double>() : bscale * b[c * N + kq] - v;
-    y[c * N + kq] = v;
+    ff2::store_val<FFO>(y, c * N + kq, v);
   }
 }
 
-template <typename TI>
+template <typename TI, bool FFO>
 __global__ void __launch_bounds__(BX * BY * BZ) apply_adjoint(FineFF3 g, const cx<TI>* __restrict__ x,
                                                              const cx<double>* __restrict__ b, double bscale,
-                                                             cx<double>* __restrict__ y) {
+                                                             void* __restrict__ y) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z * BZ + threadIdx.z;
   if (i >= g.nx || j >= g.ny || k >= g.nz) return;
-  cell_rows_adjoint(g, x, b, bscale, y, i, j, k);
+  cell_rows_adjoint<TI, FFO>(g, x, b, bscale, y, i, j, k);
 }
 
 }  // namespace ff3

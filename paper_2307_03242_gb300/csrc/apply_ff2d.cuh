@@ -79,10 +79,11 @@ struct cacc {
 };
 
 // y at cell (i, j): the u1 row at face i, the u2 row at face j and the continuity row, each as
-// H x (b == nullptr) or bscale * b - H x; rows of faces that are not unknowns are 0.
+// H x (b == nullptr) or bscale * b - H x, as float-float accumulators; rows of faces that are not
+// unknowns are 0.
 template <typename TI>
-HD void apply_cell(const FineFF& g, const cx<TI>* __restrict__ x, const cx<double>* __restrict__ b, double bscale, int i,
-                   int j, cx<double> out3[3]) {
+HD void apply_cell_acc(const FineFF& g, const cx<TI>* __restrict__ x, const cx<double>* __restrict__ b, double bscale,
+                       int i, int j, cacc out3[3]) {
   const int nx = g.nx, ny = g.ny;
   const size_t N = (size_t)nx * ny, k = (size_t)j * nx + i;
   const cx<TI>* u1 = x;
@@ -194,37 +195,63 @@ HD void apply_cell(const FineFF& g, const cx<TI>* __restrict__ x, const cx<doubl
     const cx<TI> pc = p[k];
     rp.rterm(g.cp[k], ld(pc.re), ld(pc.im));
   }
-  auto out = [&](const cacc& a) { return mkc<double>(a.re.to_double(), a.im.to_double()); };
+  const cacc zero{};
   if (b) {
     // bscale * b - H x in float-float when bscale is a power of two in the float range
     const float bs = df::pow2_float(bscale);
     auto res = [&](const cacc& a, cx<double> bv) {
-      return mkc<double>(df::scaled_sub(bv.re, bs, bscale, a.re), df::scaled_sub(bv.im, bs, bscale, a.im));
+      cacc t;
+      t.re = df::scaled_sub_acc(bv.re, bs, bscale, a.re);
+      t.im = df::scaled_sub_acc(bv.im, bs, bscale, a.im);
+      return t;
     };
-    out3[0] = i >= 1 ? res(r1, b[k]) : czero<double>();
-    out3[1] = j >= 1 ? res(r2, b[N + k]) : czero<double>();
+    out3[0] = i >= 1 ? res(r1, b[k]) : zero;
+    out3[1] = j >= 1 ? res(r2, b[N + k]) : zero;
     out3[2] = res(rp, b[2 * N + k]);
   } else {
-    out3[0] = i >= 1 ? out(r1) : czero<double>();
-    out3[1] = j >= 1 ? out(r2) : czero<double>();
-    out3[2] = out(rp);
+    out3[0] = i >= 1 ? r1 : zero;
+    out3[1] = j >= 1 ? r2 : zero;
+    out3[2] = rp;
   }
   (void)z;
 }
 
+// The same rows as FP64 values.
 template <typename TI>
+HD void apply_cell(const FineFF& g, const cx<TI>* __restrict__ x, const cx<double>* __restrict__ b, double bscale, int i,
+                   int j, cx<double> out3[3]) {
+  cacc a[3];
+  apply_cell_acc<TI>(g, x, b, bscale, i, j, a);
+  for (int c = 0; c < 3; ++c) out3[c] = mkc<double>(a[c].re.to_double(), a[c].im.to_double());
+}
+
+// Stores a row: as a complex double, or (FFO) as a float-float pair (df::cff).
+template <bool FFO>
+HD void store_row(void* y, size_t at, const cacc& a) {
+  if constexpr (FFO) static_cast<df::cff*>(y)[at] = df::to_cff(a.re, a.im);
+  else static_cast<cx<double>*>(y)[at] = mkc<double>(a.re.to_double(), a.im.to_double());
+}
+// Stores an FP64 value: as it is, or (FFO) split into a float-float pair.
+template <bool FFO>
+HD void store_val(void* y, size_t at, cx<double> v) {
+  if constexpr (FFO) static_cast<df::cff*>(y)[at] = df::to_cff(v.re, v.im);
+  else static_cast<cx<double>*>(y)[at] = v;
+}
+
+// y (complex double, or with FFO float-float pairs) = H x or bscale * b - H x.
+template <typename TI, bool FFO>
 __global__ void __launch_bounds__(BX * BY) apply(FineFF g, const cx<TI>* __restrict__ x, const cx<double>* __restrict__ b,
-                                                double bscale, cx<double>* __restrict__ y) {
+                                                double bscale, void* __restrict__ y) {
   grid_dependency_wait();  // launched with programmatic stream serialisation
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
   const size_t N = (size_t)g.nx * g.ny, k = (size_t)j * g.nx + i;
-  cx<double> out[3];
-  apply_cell<TI>(g, x, b, bscale, i, j, out);
-  y[k] = out[0];
-  y[N + k] = out[1];
-  y[2 * N + k] = out[2];
+  cacc out[3];
+  apply_cell_acc<TI>(g, x, b, bscale, i, j, out);
+  store_row<FFO>(y, k, out[0]);
+  store_row<FFO>(y, N + k, out[1]);
+  store_row<FFO>(y, 2 * N + k, out[2]);
 }
 
 }  // namespace ff2

@@ -44,13 +44,22 @@ HD V sel3(int c, V a, V b, V d) {
   return c == 0 ? a : (c == 1 ? b : d);
 }
 
-// Loaded values as float-float: floats exactly, doubles split.
-HD f2 ldw(float v, float w) { return {v * w, 0.f}; }
-HD f2 ldw(double v, float w) {
-  const f2 r = df::split(v);
-  return {r.hi * w, r.lo * w};
-}
-// a * b for float-float a and a float or split double b (normalised).
+// A loaded complex value ready for float-float use: floats as they are, doubles split once.
+template <typename TI>
+struct Val;
+template <>
+struct Val<float> {
+  float re, im;
+};
+template <>
+struct Val<double> {
+  f2 re, im;
+};
+HD Val<float> val(cx<float> v) { return {v.re, v.im}; }
+HD Val<double> val(cx<double> v) { return {df::split(v.re), df::split(v.im)}; }
+HD f2 asf2(float v) { return {v, 0.f}; }
+HD f2 asf2(f2 v) { return v; }
+// a * b for float-float a and a float or float-float b (normalised).
 HD f2 mulv(f2 a, float b) {
   const float p = a.hi * b;
   float e = std::fma(a.hi, b, -p);
@@ -59,16 +68,15 @@ HD f2 mulv(f2 a, float b) {
   df::two_sum(p, e, r.hi, r.lo);
   return r;
 }
-HD f2 mulv(f2 a, double b) { return mul(a, df::split(b)); }
-template <typename TI>
-HD void wadd(df::acc& ar, df::acc& ai, cx<TI> v, float w) {
-  if constexpr (sizeof(TI) == 4) {
-    ar.add(v.re * w);  // w is 1, 2 or 4: the scaling is exact
-    ai.add(v.im * w);
-  } else {
-    ar.add(ldw(v.re, w));
-    ai.add(ldw(v.im, w));
-  }
+HD f2 mulv(f2 a, f2 b) { return mul(a, b); }
+// (ar, ai) += w v with w = 1, 2 or 4 (the scaling is exact)
+HD void wadd(df::acc& ar, df::acc& ai, Val<float> v, float w) {
+  ar.add(v.re * w);
+  ai.add(v.im * w);
+}
+HD void wadd(df::acc& ar, df::acc& ai, Val<double> v, float w) {
+  ar.add(f2{v.re.hi * w, v.re.lo * w});
+  ai.add(f2{v.im.hi * w, v.im.lo * w});
 }
 HD c2 csub(c2 a, c2 b) { return {add(a.re, fneg(b.re)), add(a.im, fneg(b.im))}; }
 
@@ -83,9 +91,8 @@ HD c2 csub(c2 a, c2 b) { return {add(a.re, fneg(b.re)), add(a.im, fneg(b.im))}; 
 // the same sum as sum_delta C(delta) u_c(q + delta) up to the order of the additions. Each of the
 // 27 values is loaded once and added into the three slab families it belongs to. The continuity
 // row's spread divergence of u_c is ih (S_c(+1) - S_c(0)) with the same slab sums.
-template <typename TI>
-HD void cell_rows(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y, int i, int j,
-                  int k) {
+template <typename TI, bool FFO = false>
+HD void cell_rows(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, void* y, int i, int j, int k) {
   const size_t N = (size_t)g.nx * g.ny * g.nz, kq = lin(g, i, j, k);
   const long long sy = g.nx, sz = (long long)g.nx * g.ny;
   const long long sl[3] = {1, sy, sz};
@@ -96,8 +103,14 @@ HD void cell_rows(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double
   };
   const float bs = b ? df::pow2_float(bscale) : 0.f;
   auto finish = [&](const cacc& r, size_t at) {
-    return b ? mkc<double>(df::scaled_sub(b[at].re, bs, bscale, r.re), df::scaled_sub(b[at].im, bs, bscale, r.im))
-             : mkc<double>(r.re.to_double(), r.im.to_double());
+    if (!b) {
+      ff2::store_row<FFO>(y, at, r);
+      return;
+    }
+    cacc t;
+    t.re = df::scaled_sub_acc(b[at].re, bs, bscale, r.re);
+    t.im = df::scaled_sub_acc(b[at].im, bs, bscale, r.im);
+    ff2::store_row<FFO>(y, at, t);
   };
   cacc dv;  // spread divergence sum_c (S_c(+1) - S_c(0)), without the 1/h
 #pragma unroll 1
@@ -106,7 +119,7 @@ HD void cell_rows(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double
     const cx<TI>* u = x + c * N + kq;
     // slab sums with integer weights: T[e][d+1]; the 7 values on the axes through q: v7
     df::acc tr[3][3], ti[3][3];
-    cx<TI> v7[7];  // centre, then -e0, +e0, -e1, +e1, -e2, +e2
+    Val<TI> v7[7];  // centre, then -e0, +e0, -e1, +e1, -e2, +e2
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
@@ -114,7 +127,7 @@ HD void cell_rows(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx) {
           const bool ok = inside(i + dx, j + dy, k + dz) && qc + sel3(c, dx, dy, dz) >= 1;
-          const cx<TI> v = ok ? u[dx + dy * sy + dz * sz] : czero<TI>();
+          const Val<TI> v = val(ok ? u[dx + dy * sy + dz * sz] : czero<TI>());
           const float wx = dx == 0 ? 2.f : 1.f, wy = dy == 0 ? 2.f : 1.f, wz = dz == 0 ? 2.f : 1.f;
           wadd(tr[0][dx + 1], ti[0][dx + 1], v, wy * wz);
           wadd(tr[1][dy + 1], ti[1][dy + 1], v, wx * wz);
@@ -129,7 +142,7 @@ HD void cell_rows(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double
     for (int e = 0; e < 3; ++e)
 #pragma unroll
       for (int d = -1; d <= 1; ++d) {
-        const cx<TI> va = d == 0 ? v7[0] : v7[1 + 2 * e + (d > 0)];
+        const Val<TI> va = d == 0 ? v7[0] : v7[1 + 2 * e + (d > 0)];
         S[e][d + 1] = {add(mulv(g.beta, va.re), mul(g.kap, tr[e][d + 1].norm())),
                        add(mulv(g.beta, va.im), mul(g.kap, ti[e][d + 1].norm()))};
       }
@@ -139,8 +152,9 @@ HD void cell_rows(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double
       dv.re.add(dd.re);
       dv.im.add(dd.im);
     }
-    cx<double> out = czero<double>();
-    if (qc >= 1) {
+    if (qc < 1) {
+      ff2::store_row<FFO>(y, c * N + kq, cacc{});
+    } else {
       // mu beside q along each derivative axis: cell centres for e = c, edge means otherwise
       df::acc lr, li;
 #pragma unroll
@@ -165,8 +179,10 @@ HD void cell_rows(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double
       cacc r;
       r.re.add(mul(g.ih2, lr.norm()));
       r.im.add(mul(g.ih2, li.norm()));
-      // mass: -(beta m u) at the face, -(sm m u) at its 6 neighbours (Eq. massHO3D)
+      // mass: -(beta m u) at the face, -(sm m u) at its 6 neighbours (Eq. massHO3D), summed as
+      // -beta A0 - sm A6 with A0 = m u at the face and A6 the sum over the neighbours
       const c2* mc = sel3(c, g.m[0], g.m[1], g.m[2]);
+      cacc a0, a6;
 #pragma unroll
       for (int t = 0; t < 7; ++t) {
         const int ax = (t - 1) / 2, sg = (t & 1) ? -1 : 1;
@@ -174,37 +190,39 @@ HD void cell_rows(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double
         const bool ok = inside(i + dx, j + dy, k + dz) && qc + sel3(c, dx, dy, dz) >= 1;
         if (!ok) continue;
         const c2 m = mshift(mc[(long long)kq + dx + dy * sy + dz * sz]);
-        const f2 f = t == 0 ? g.beta : g.sm;
-        r.cterm({fneg(mul(f, m.re)), fneg(mul(f, m.im))}, ldw(v7[t].re, 1.f), ldw(v7[t].im, 1.f));
+        (t == 0 ? a0 : a6).cterm(m, asf2(v7[t].re), asf2(v7[t].im));
       }
+      r.re.fms_ff(g.beta, a0.re.norm());
+      r.im.fms_ff(g.beta, a0.im.norm());
+      r.re.fms_ff(g.sm, a6.re.norm());
+      r.im.fms_ff(g.sm, a6.im.norm());
       // gradient: + (p(q) - p(q - e_c)) / h
       const cx<TI>* p = x + 3 * N + kq;
-      const cx<TI> pc = p[0], pm = p[-sel3(c, sl[0], sl[1], sl[2])];
-      r.rterm(g.ih, ldw(pc.re, 1.f), ldw(pc.im, 1.f));
-      r.rterm(fneg(g.ih), ldw(pm.re, 1.f), ldw(pm.im, 1.f));
-      out = finish(r, c * N + kq);
+      const Val<TI> pc = val(p[0]), pm = val(p[-sel3(c, sl[0], sl[1], sl[2])]);
+      r.rterm(g.ih, asf2(pc.re), asf2(pc.im));
+      r.rterm(fneg(g.ih), asf2(pm.re), asf2(pm.im));
+      finish(r, c * N + kq);
     }
-    y[c * N + kq] = out;
   }
   {
     cacc r;
     r.re.add(mul(g.ih, dv.re.norm()));
     r.im.add(mul(g.ih, dv.im.norm()));
-    const cx<TI> pc = x[3 * N + kq];
-    r.rterm(g.cp[kq], ldw(pc.re, 1.f), ldw(pc.im, 1.f));
-    y[3 * N + kq] = finish(r, 3 * N + kq);
+    const Val<TI> pc = val(x[3 * N + kq]);
+    r.rterm(g.cp[kq], asf2(pc.re), asf2(pc.im));
+    finish(r, 3 * N + kq);
   }
 }
 
-template <typename TI>
+template <typename TI, bool FFO>
 __global__ void __launch_bounds__(BX * BY * BZ) apply(FineFF3 g, const cx<TI>* __restrict__ x,
                                                      const cx<double>* __restrict__ b, double bscale,
-                                                     cx<double>* __restrict__ y) {
+                                                     void* __restrict__ y) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z * BZ + threadIdx.z;
   if (i >= g.nx || j >= g.ny || k >= g.nz) return;
-  cell_rows(g, x, b, bscale, y, i, j, k);
+  cell_rows<TI, FFO>(g, x, b, bscale, y, i, j, k);
 }
 
 }  // namespace ff3

@@ -194,18 +194,39 @@ HD float pow2_float(double x) {
   return bfloat((unsigned)(b >> 32 & 0x80000000u) | ((unsigned)(e + 127) << 23));
 }
 
-// bscale * b - r as a double. With bs = pow2_float(bscale) != 0 it is evaluated in float-float
-// (the scaling of the split b by a power of two is exact) and assembled without FP64
-// instructions; otherwise in FP64.
-HD double scaled_sub(double b, float bs, double bscale, const acc& r) {
-  if (bs == 0.0f) return bscale * b - r.to_double();
-  const f2 bb = split(b);
+// bscale * b - r. With bs = pow2_float(bscale) != 0 it is evaluated in float-float (the scaling
+// of the split b by a power of two is exact); otherwise in FP64.
+HD acc scaled_sub_acc(double b, float bs, double bscale, const acc& r) {
   acc t;
+  if (bs == 0.0f) {
+    t.add(split(bscale * b - r.to_double()));
+    return t;
+  }
+  const f2 bb = split(b);
   t.hi = bb.hi * bs;
   t.lo = bb.lo * bs;
   const f2 rn = r.norm();
   t.add({-rn.hi, -rn.lo});
-  return t.to_double();
+  return t;
+}
+HD double scaled_sub(double b, float bs, double bscale, const acc& r) {
+  return scaled_sub_acc(b, bs, bscale, r).to_double();
+}
+
+// A complex float-float value in memory: the normalised hi and lo floats of the real part, then
+// of the imaginary part (16 bytes, the size of a complex double). The outer solve keeps its
+// internal Krylov vectors in this form, so that its vector kernels neither split nor assemble
+// doubles; the caller's vectors (b, x, an applied y) stay IEEE FP64.
+struct __align__(16) cff {
+  float rh, rl, ih, il;
+};
+HD cff to_cff(const acc& re, const acc& im) {
+  const f2 a = re.norm(), b = im.norm();
+  return {a.hi, a.lo, b.hi, b.lo};
+}
+HD cff to_cff(double re, double im) {
+  const f2 a = split(re), b = split(im);
+  return {a.hi, a.lo, b.hi, b.lo};
 }
 
 }  // namespace df

@@ -1070,11 +1070,14 @@ void ensure_krylov(emg_ctx& c, int m) {
   if (!c.hred) CK(cudaMallocHost(&c.hred, 4096 * sizeof(double)));
 }
 
-// Launch one multi-dot pass over NV vectors; native FP64 (exact) or float-float (ff).
+// Launch one multi-dot pass over NV vectors: native FP64 (exact) on complex doubles, or float-float
+// (ff) on float-float pairs (df::cff, the Krylov basis and the applied vector).
 template <int NV>
 void launch_mdot(emg_ctx& c, bool ff, const cx<double>* V, size_t ldv, const cx<double>* w, size_t n, double* part,
                  int nblk) {
-  if (ff) launch_dep(kf::mdot<NV>, dim3(nblk), dim3(kv::RT), 0, c.st, V, ldv, w, n, part);
+  if (ff)
+    launch_dep(kf::mdot<NV>, dim3(nblk), dim3(kv::RT), 0, c.st, reinterpret_cast<const df::cff*>(V), ldv,
+               reinterpret_cast<const df::cff*>(w), n, part);
   else launch_dep(kv::mdot<NV>, dim3(nblk), dim3(kv::RT), 0, c.st, V, ldv, w, n, part);
   CKL();
   LAUNCHED(c);
@@ -1135,18 +1138,20 @@ void mdots(emg_ctx& c, bool ff, const cx<double>* V, size_t ldv, int cnt, const 
   if (!std::isfinite(wn2)) raise(EMG_ERR_NONFINITE, "non-finite Krylov norm");
 }
 
-// w <- s (w - sum_i h_i V_i), optionally also written in FP32 to out32. With want_norm, returns
+// w <- s (w - sum_i h_i V_i) on float-float vectors, optionally also written to outc (the next
+// cycle's right-hand side) in FP32 (outk 1) or FP64 (outk 2). With want_norm, returns
 // ||w_new||^2 (one reduction and a synchronisation); otherwise returns 0 and does not wait.
 double update_scale(emg_ctx& c, cx<double>* w, const cx<double>* V, size_t ldv,
-                    const std::vector<std::complex<double>>& h, double s, size_t n, cx<float>* out32,
+                    const std::vector<std::complex<double>>& h, double s, size_t n, void* outc, int outk,
                     bool want_norm = false) {
   const int nblk = vec_blocks(c, n);
   kf::Coefs co;
   const int cnt = (int)h.size();
   for (int i = 0; i < cnt; ++i) co.c[i] = {to_f2(h[i].real()), to_f2(h[i].imag())};
   {
-    ProfScope ps(c, EMG_K_KRYLOV, 0, (double)n * 16 * (cnt + 2) + (out32 ? n * 8.0 : 0.0));
-    launch_dep(kf::update_scale, dim3(nblk), dim3(kv::RT), 0, c.st, w, V, ldv, cnt, co, to_f2(s), n, out32, c.part.as<double>());
+    ProfScope ps(c, EMG_K_KRYLOV, 0, (double)n * 16 * (cnt + 2) + (double)n * 8.0 * outk);
+    launch_dep(kf::update_scale, dim3(nblk), dim3(kv::RT), 0, c.st, reinterpret_cast<df::cff*>(w),
+               reinterpret_cast<const df::cff*>(V), ldv, cnt, co, to_f2(s), n, outc, outk, c.part.as<double>());
     CKL();
     LAUNCHED(c);
   }
@@ -1161,7 +1166,9 @@ double update_scale(emg_ctx& c, cx<double>* w, const cx<double>* V, size_t ldv,
 }
 
 // y = H x (unshifted or shifted) or y = bscale*b - H x on the finest level in FP64; x in FP64 or FP32.
-void outer_apply(emg_ctx& c, const void* x, bool x32, const cx<double>* b, double bscale, cx<double>* y, bool shifted) {
+// ffo: y is one of the outer solve's float-float vectors (df::cff) instead of complex doubles.
+void outer_apply(emg_ctx& c, const void* x, bool x32, const cx<double>* b, double bscale, cx<double>* y, bool shifted,
+                 bool ffo = false) {
   const double cw = 16.0;
   if (c.dim == 2) {
     // float-float evaluation from precomputed FP64 coefficients (x, b, y + mu, node mu, cp, 2 masses)
@@ -1170,8 +1177,8 @@ void outer_apply(emg_ctx& c, const void* x, bool x32, const cx<double>* b, doubl
     const ff2::FineFF g = ff2::make(c.ff_mu.as<df::f2>(), c.ff_mun.as<df::f2>(), c.ff_cp.as<df::f2>(),
                                     c.ff_m1.as<ff2::c2>(), c.ff_m2.as<ff2::c2>(), F.n[0], F.n[1], F.h, c.prm.beta,
                                     shifted ? level_alpha(c.prm, 0) : 0.0);
-    if (x32) launch_apply_ff2<float>(g, (const cx<float>*)x, b, bscale, y, c.st);
-    else launch_apply_ff2<double>(g, (const cx<double>*)x, b, bscale, y, c.st);
+    if (x32) launch_apply_ff2<float>(g, (const cx<float>*)x, b, bscale, y, ffo, c.st);
+    else launch_apply_ff2<double>(g, (const cx<double>*)x, b, bscale, y, ffo, c.st);
     CKL();
     LAUNCHED(c);
     return;
@@ -1184,22 +1191,23 @@ void outer_apply(emg_ctx& c, const void* x, bool x32, const cx<double>* b, doubl
   ff3::HostFF3 none;
   ff3::FineFF3 g = ff3::make(none, c.ff_mu.as<df::f2>(), c.ff_cp.as<df::f2>(), ed, ms, F.n[0], F.n[1], F.n[2], F.h,
                              c.prm.beta, shifted ? level_alpha(c.prm, 0) : 0.0);
-  if (x32) launch_apply_ff3<float>(g, (const cx<float>*)x, b, bscale, y, c.st);
-  else launch_apply_ff3<double>(g, (const cx<double>*)x, b, bscale, y, c.st);
+  if (x32) launch_apply_ff3<float>(g, (const cx<float>*)x, b, bscale, y, ffo, c.st);
+  else launch_apply_ff3<double>(g, (const cx<double>*)x, b, bscale, y, ffo, c.st);
   CKL();
   LAUNCHED(c);
 }
 
 // y = H^H x (the unshifted finest operator, conjugate-transposed) or y = bscale*b - H^H x, FP64;
 // x in FP64 or FP32.
-void outer_apply_adjoint(emg_ctx& c, const void* x, bool x32, const cx<double>* b, double bscale, cx<double>* y) {
+void outer_apply_adjoint(emg_ctx& c, const void* x, bool x32, const cx<double>* b, double bscale, cx<double>* y,
+                         bool ffo = false) {
   const Level& F = c.lv[0];
   ProfScope ps(c, EMG_K_APPLY64, 0,
                (double)F.ncell * ((c.dim + 1) * ((x32 ? 8.0 : 16.0) + 16.0 + (b ? 16.0 : 0.0)) + 3 * 8.0));
   const Grid<double> g = make_grid<double>(c, 0, false, c.mu64.p, c.rho64.p, c.cp64.p);
   if (c.dim == 2) {
-    if (x32) launch_adjoint_apply<2, float>(g, (const cx<float>*)x, b, bscale, y, c.st);
-    else launch_adjoint_apply<2, double>(g, (const cx<double>*)x, b, bscale, y, c.st);
+    if (x32) launch_adjoint_apply<2, float>(g, (const cx<float>*)x, b, bscale, y, ffo, c.st);
+    else launch_adjoint_apply<2, double>(g, (const cx<double>*)x, b, bscale, y, ffo, c.st);
   } else {
     // float-float on the forward apply's coefficients (the FP64 pipe is ~57x slower)
     const df::f2* ed[3] = {c.ff3_edge[0].as<df::f2>(), c.ff3_edge[1].as<df::f2>(), c.ff3_edge[2].as<df::f2>()};
@@ -1207,8 +1215,8 @@ void outer_apply_adjoint(emg_ctx& c, const void* x, bool x32, const cx<double>* 
     ff3::HostFF3 none;
     const ff3::FineFF3 gf = ff3::make(none, c.ff_mu.as<df::f2>(), c.ff_cp.as<df::f2>(), ed, ms, F.n[0], F.n[1], F.n[2],
                                       F.h, c.prm.beta, 0.0);
-    if (x32) launch_apply_adjoint_ff3<float>(gf, (const cx<float>*)x, b, bscale, y, c.st);
-    else launch_apply_adjoint_ff3<double>(gf, (const cx<double>*)x, b, bscale, y, c.st);
+    if (x32) launch_apply_adjoint_ff3<float>(gf, (const cx<float>*)x, b, bscale, y, ffo, c.st);
+    else launch_apply_adjoint_ff3<double>(gf, (const cx<double>*)x, b, bscale, y, ffo, c.st);
   }
   CKL();
   LAUNCHED(c);
@@ -1260,8 +1268,9 @@ cudaGraphExec_t capture_cycle(emg_ctx& c, const cx<T>* b, cx<T>* z, int64_t& ker
 template <typename T>
 void precondition(emg_ctx& c, const cx<double>* v, cx<T>* z) {
   Level& F = c.lv[0];
-  // FP32 cycle: its right-hand side was written in FP32 to F.b by the update that produced v
-  const cx<T>* b = std::is_same<T, double>::value ? (const cx<T>*)v : F.b.as<cx<T>>();
+  // the cycle's right-hand side was written in its precision to F.b by the update that produced v
+  (void)v;
+  const cx<T>* b = F.b.as<cx<T>>();
   if (c.graphs_ok) {
     // with the instrumentation on, a graph that records its own event pairs (they are graph
     // nodes, so every replay times its kernels); otherwise one without
@@ -1327,7 +1336,10 @@ emg_status solve_impl(emg_ctx& c, const cx<double>* b, cx<double>* x, double tol
   cx<double>* V = c.V.as<cx<double>>();
   cx<T>* Z = c.Z.as<cx<T>>();
   cx<double>* r = c.wk64.as<cx<double>>();
-  cx<float>* b32 = f32 ? c.lv[0].b.as<cx<float>>() : nullptr;
+  // the Krylov vectors V (and r) are float-float pairs; each finished V_j is also written to the
+  // cycle's right-hand side in the cycle's precision
+  void* bcyc = c.lv[0].b.p;
+  const int bk = f32 ? 1 : 2;
   int hist = 0;
   auto push_hist = [&](double v) {
     if (st && st->history && hist < st->history_cap) st->history[hist] = v;
@@ -1349,8 +1361,8 @@ emg_status solve_impl(emg_ctx& c, const cx<double>* b, cx<double>* x, double tol
   CKL();
   LAUNCHED(c);
   auto true_residual = [&]() {
-    if (adj) outer_apply_adjoint(c, x, false, b, sc, r);  // r = sc*b - H^H (sc*x)
-    else outer_apply(c, x, false, b, sc, r, false);     // r = sc*b - H (sc*x)
+    if (adj) outer_apply_adjoint(c, x, false, b, sc, r, true);  // r = sc*b - H^H (sc*x)
+    else outer_apply(c, x, false, b, sc, r, false, true);     // r = sc*b - H (sc*x)
     double rn2 = 0;
     mdots(c, true, nullptr, 0, 0, r, n, h, rn2);
     return std::sqrt(rn2);
@@ -1362,7 +1374,7 @@ emg_status solve_impl(emg_ctx& c, const cx<double>* b, cx<double>* x, double tol
   while (beta / bhat > tol && its < max_iter) {
     // V_0 = r / beta (and its FP32 copy for the first cycle)
     CK(cudaMemcpyAsync(V, r, n * 16, cudaMemcpyDeviceToDevice, c.st));
-    update_scale(c, V, V, n, {}, 1.0 / beta, n, b32);
+    update_scale(c, V, V, n, {}, 1.0 / beta, n, bcyc, bk);
     std::fill(Hh.begin(), Hh.end(), 0.0);
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
@@ -1371,15 +1383,15 @@ emg_status solve_impl(emg_ctx& c, const cx<double>* b, cx<double>* x, double tol
     double pend_norm = 1.0;
     for (int j = 0; j < m; ++j) {
       cx<double>* vj = V + (size_t)j * n;
-      if (j > 0) update_scale(c, vj, V, n, pend, 1.0 / pend_norm, n, b32);  // finish V_j
+      if (j > 0) update_scale(c, vj, V, n, pend, 1.0 / pend_norm, n, bcyc, bk);  // finish V_j
       cx<double>* w = V + (size_t)(j + 1) * n;
       if (adj) sconj_cycle_vector<T>(c, c.lv[0].b.as<cx<T>>());  // the cycle solves with conj(S v_j)
       precondition<T>(c, vj, Z + (size_t)j * n);
       if (adj) {
         sconj_cycle_vector<T>(c, Z + (size_t)j * n);  // z_j = S conj(M conj(S v_j))
-        outer_apply_adjoint(c, Z + (size_t)j * n, f32, nullptr, 0.0, w);
+        outer_apply_adjoint(c, Z + (size_t)j * n, f32, nullptr, 0.0, w, true);
       } else {
-        outer_apply(c, Z + (size_t)j * n, f32, nullptr, 0.0, w, false);
+        outer_apply(c, Z + (size_t)j * n, f32, nullptr, 0.0, w, false, true);
       }
       double wn2 = 0;
       mdots(c, true, V, n, j + 1, w, n, h, wn2);
@@ -1388,14 +1400,14 @@ emg_status solve_impl(emg_ctx& c, const cx<double>* b, cx<double>* x, double tol
       double nn2 = wn2 - hh;
       pend = h;
       if (nn2 < kReorth * wn2) {  // cancellation: apply the projection now and orthogonalise again
-        update_scale(c, w, V, n, h, 1.0, n, nullptr);
+        update_scale(c, w, V, n, h, 1.0, n, nullptr, 0);
         double wn2b = 0;
         mdots(c, true, V, n, j + 1, w, n, h2, wn2b);
         double hh2 = 0;
         for (auto& z : h2) hh2 += std::norm(z);
         nn2 = wn2b - hh2;
         if (nn2 < kReorth * wn2b) {  // still cancelling: materialise and measure exactly
-          nn2 = update_scale(c, w, V, n, h2, 1.0, n, nullptr, true);
+          nn2 = update_scale(c, w, V, n, h2, 1.0, n, nullptr, 0, true);
           h2.assign(j + 1, 0.0);
         }
         for (int i = 0; i <= j; ++i) h[i] += h2[i];

@@ -1,13 +1,16 @@
-// FP64 Krylov vector kernels evaluated in double-FP32 arithmetic (dfloat.cuh): the vectors are
-// IEEE FP64 in memory, every product and sum is carried with ~48 significant bits on the FP32
-// pipe, and doubles are split and assembled with integer operations, so that no FP64
-// instruction runs per element (this part's FP64 pipe is ~57x slower than its FP32 pipe).
+// FP64 Krylov vector kernels evaluated in double-FP32 arithmetic (dfloat.cuh): every product and
+// sum is carried with ~48 significant bits on the FP32 pipe. The Krylov basis and the applied
+// vector w are stored as float-float pairs (df::cff, 16 bytes per complex value like a complex
+// double), so that these kernels neither split nor assemble doubles; the iterate x stays IEEE
+// FP64 and is split and assembled with integer operations. No FP64 instruction runs per element
+// (this part's FP64 pipe is ~57x slower than its FP32 pipe).
 #pragma once
 #include "dfloat.cuh"
 #include "vector_kernels.cuh"
 
 namespace kf {
 
+using df::cff;
 using df::f2;
 constexpr int RT = kv::RT;
 
@@ -52,15 +55,15 @@ __device__ __forceinline__ void block_reduce_store_ff(const df::acc (&a)[NR], do
 
 // part[blk][2i], [2i+1] = Re, Im of sum conj(V_i) w (i < NV); part[blk][2NV] = sum |w|^2.
 template <int NV>
-__global__ void __launch_bounds__(RT) mdot(const cx<double>* __restrict__ V, size_t ldv,
-                                           const cx<double>* __restrict__ w, size_t n, double* part) {
+__global__ void __launch_bounds__(RT) mdot(const cff* __restrict__ V, size_t ldv, const cff* __restrict__ w, size_t n,
+                                           double* part) {
   grid_dependency_wait();  // launched with programmatic stream serialisation
   constexpr int U = NV <= 2 ? 4 : (NV <= 6 ? 2 : 1);
   df::acc are[NV > 0 ? NV : 1], aim[NV > 0 ? NV : 1], ann;
   const size_t stride = (size_t)gridDim.x * RT;
-  const cx<double> z = czero<double>();
+  const cff z = {0.f, 0.f, 0.f, 0.f};
   for (size_t e0 = (size_t)blockIdx.x * RT + threadIdx.x; e0 < n; e0 += U * stride) {
-    cx<double> we[U], a[U][NV > 0 ? NV : 1];
+    cff we[U], a[U][NV > 0 ? NV : 1];
     // every load is issued before any arithmetic (indices clamped into the vector); elements
     // past the end are then replaced by zeros, which add nothing
 #pragma unroll
@@ -79,10 +82,10 @@ __global__ void __launch_bounds__(RT) mdot(const cx<double>* __restrict__ V, siz
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const f2 wr = df::split(we[u].re), wi = df::split(we[u].im);
+      const f2 wr = {we[u].rh, we[u].rl}, wi = {we[u].ih, we[u].il};
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const f2 ar = df::split(a[u][v].re), ai = df::split(a[u][v].im);
+        const f2 ar = {a[u][v].rh, a[u][v].rl}, ai = {a[u][v].ih, a[u][v].il};
         are[v].fma_ff(ar, wr);
         are[v].fma_ff(ai, wi);
         aim[v].fma_ff(ar, wi);
@@ -110,26 +113,27 @@ struct Coefs {
   c2 c[64];
 };
 
-// w <- s * (w - sum_i h_i V_i) (i < cnt), written back as FP64; optionally also written in FP32
-// to out32 (the next cycle's right-hand side); part[blk] = sum |w_new|^2.
-__global__ void __launch_bounds__(RT) update_scale(cx<double>* __restrict__ w, const cx<double>* __restrict__ V,
-                                                   size_t ldv, int cnt, Coefs h, f2 s, size_t n,
-                                                   cx<float>* __restrict__ out32, double* part) {
+// w <- s * (w - sum_i h_i V_i) (i < cnt), written back in place; optionally also written to
+// outc, the next cycle's right-hand side, in FP32 (outk = 1) or FP64 (outk = 2);
+// part[blk] = sum |w_new|^2.
+__global__ void __launch_bounds__(RT) update_scale(cff* __restrict__ w, const cff* __restrict__ V, size_t ldv, int cnt,
+                                                   Coefs h, f2 s, size_t n, void* __restrict__ outc, int outk,
+                                                   double* part) {
   grid_dependency_wait();  // launched with programmatic stream serialisation
   df::acc nn;
   const size_t stride = (size_t)gridDim.x * RT;
-  const cx<double> z = czero<double>();
+  const cff z = {0.f, 0.f, 0.f, 0.f};
   for (size_t e0 = (size_t)blockIdx.x * RT + threadIdx.x; e0 < n; e0 += UPD * stride) {
     df::acc re[UPD], im[UPD];
 #pragma unroll
     for (int u = 0; u < UPD; ++u) {
       const size_t e = e0 + u * stride;
-      const cx<double> we = e < n ? w[e] : z;
-      re[u].add(df::split(we.re));
-      im[u].add(df::split(we.im));
+      const cff we = e < n ? w[e] : z;
+      re[u].add(f2{we.rh, we.rl});
+      im[u].add(f2{we.ih, we.il});
     }
     for (int v = 0; v < cnt; ++v) {
-      cx<double> a[UPD];
+      cff a[UPD];
 #pragma unroll
       for (int u = 0; u < UPD; ++u) a[u] = V[v * ldv + (e0 + u * stride < n ? e0 + u * stride : n - 1)];
 #pragma unroll
@@ -138,7 +142,7 @@ __global__ void __launch_bounds__(RT) update_scale(cx<double>* __restrict__ w, c
       const c2 hv = h.c[v];
 #pragma unroll
       for (int u = 0; u < UPD; ++u) {
-        const f2 ar = df::split(a[u].re), ai = df::split(a[u].im);
+        const f2 ar = {a[u].rh, a[u].rl}, ai = {a[u].ih, a[u].il};
         // (hr + i hi)(ar + i ai) = (hr ar - hi ai) + i (hr ai + hi ar)
         re[u].fms_ff(hv.re, ar);
         re[u].fma_ff(hv.im, ai);
@@ -154,8 +158,9 @@ __global__ void __launch_bounds__(RT) update_scale(cx<double>* __restrict__ w, c
       ore.fma_ff(re[u].norm(), s);
       oim.fma_ff(im[u].norm(), s);
       const f2 fr = ore.norm(), fi = oim.norm();
-      w[e] = mkc<double>(df::join(fr.hi, fr.lo), df::join(fi.hi, fi.lo));
-      if (out32) out32[e] = mkc<float>(fr.hi, fi.hi);
+      w[e] = {fr.hi, fr.lo, fi.hi, fi.lo};
+      if (outk == 1) static_cast<cx<float>*>(outc)[e] = mkc<float>(fr.hi, fi.hi);
+      else if (outk == 2) static_cast<cx<double>*>(outc)[e] = mkc<double>(df::join(fr.hi, fr.lo), df::join(fi.hi, fi.lo));
       nn.fma_ff(fr, fr);
       nn.fma_ff(fi, fi);
     }

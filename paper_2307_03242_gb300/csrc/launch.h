@@ -37,8 +37,10 @@ void launch_restrict3(const Grid<T>& g, const cx<T>* b, const cx<T>* x, cx<T>* b
 template <typename T>
 void launch_prolong3(const cx<T>* e, cx<T>* x, const int n[3], const int nc[3], cudaStream_t st);
 
+// The FP64 outer applies write y as complex doubles, or with ffo as float-float pairs (df::cff,
+// the outer solve's internal Krylov vectors).
 template <typename TI>
-void launch_apply_ff2(const ff2::FineFF& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y,
+void launch_apply_ff2(const ff2::FineFF& g, const cx<TI>* x, const cx<double>* b, double bscale, void* y, bool ffo,
                       cudaStream_t st);
 
 // One full red-black sweep of a 2D FP32 level in one pass (k2t::sweep_tile): xin -> xout, which
@@ -63,19 +65,19 @@ cudaError_t launch_sweeps_coop2(const Grid<T>& g, const cx<T>* b, cx<T>* x, cx<T
                                 int zero_first, cudaStream_t st);
 
 template <typename TI>
-void launch_apply_ff3(const ff3::FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y,
+void launch_apply_ff3(const ff3::FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, void* y, bool ffo,
                       cudaStream_t st);
 
 template <typename TI>
-void launch_apply_adjoint_ff3(const ff3::FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale,
-                              cx<double>* y, cudaStream_t st);
+void launch_apply_adjoint_ff3(const ff3::FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, void* y,
+                              bool ffo, cudaStream_t st);
 
 // Adjoint-state gradient (adjoint.cu): y = H^H x or y = bscale b - H^H x on the finest level,
 // the per-cell material derivative, and z <- S conj(z) on an FP32 vector (nu displacement
 // entries, then the pressure).
 template <int D, typename TI>
-void launch_adjoint_apply(const Grid<double>& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y,
-                          cudaStream_t st);
+void launch_adjoint_apply(const Grid<double>& g, const cx<TI>* x, const cx<double>* b, double bscale, void* y,
+                          bool ffo, cudaStream_t st);
 template <int D>
 void launch_adjoint_gradient(const Grid<double>& g, const cx<double>* u, const cx<double>* a, double* glam,
                              double* gmu, double* grho, int accumulate, cudaStream_t st);

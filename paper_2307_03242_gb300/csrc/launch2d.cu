@@ -42,12 +42,15 @@ INST(float)
 INST(double)
 
 template <typename TI>
-void launch_apply_ff2(const ff2::FineFF& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y,
+void launch_apply_ff2(const ff2::FineFF& g, const cx<TI>* x, const cx<double>* b, double bscale, void* y, bool ffo,
                       cudaStream_t st) {
-  launch_dep(ff2::apply<TI>, dim3(g2(g.nx, g.ny)), dim3(ff2::BX, ff2::BY), 0, st, g, x, b, bscale, y);
+  if (ffo) launch_dep(ff2::apply<TI, true>, dim3(g2(g.nx, g.ny)), dim3(ff2::BX, ff2::BY), 0, st, g, x, b, bscale, y);
+  else launch_dep(ff2::apply<TI, false>, dim3(g2(g.nx, g.ny)), dim3(ff2::BX, ff2::BY), 0, st, g, x, b, bscale, y);
 }
-template void launch_apply_ff2<float>(const ff2::FineFF&, const cx<float>*, const cx<double>*, double, cx<double>*, cudaStream_t);
-template void launch_apply_ff2<double>(const ff2::FineFF&, const cx<double>*, const cx<double>*, double, cx<double>*, cudaStream_t);
+template void launch_apply_ff2<float>(const ff2::FineFF&, const cx<float>*, const cx<double>*, double, void*, bool,
+                                      cudaStream_t);
+template void launch_apply_ff2<double>(const ff2::FineFF&, const cx<double>*, const cx<double>*, double, void*, bool,
+                                       cudaStream_t);
 
 // All sweeps of one coarsest-level solve in one cooperative launch (x starts from zero).
 // Cooperative sweeps on a small level: 64-thread blocks spread the few cells over as many SMs as

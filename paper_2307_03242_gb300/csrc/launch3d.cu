@@ -58,23 +58,27 @@ INST(float)
 INST(double)
 
 template <typename TI>
-void launch_apply_ff3(const ff3::FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, cx<double>* y,
+void launch_apply_ff3(const ff3::FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, void* y, bool ffo,
                       cudaStream_t st) {
   dim3 grid((g.nx + ff3::BX - 1) / ff3::BX, (g.ny + ff3::BY - 1) / ff3::BY, (g.nz + ff3::BZ - 1) / ff3::BZ);
-  ff3::apply<TI><<<grid, dim3(ff3::BX, ff3::BY, ff3::BZ), 0, st>>>(g, x, b, bscale, y);
+  if (ffo) ff3::apply<TI, true><<<grid, dim3(ff3::BX, ff3::BY, ff3::BZ), 0, st>>>(g, x, b, bscale, y);
+  else ff3::apply<TI, false><<<grid, dim3(ff3::BX, ff3::BY, ff3::BZ), 0, st>>>(g, x, b, bscale, y);
 }
-template void launch_apply_ff3<float>(const ff3::FineFF3&, const cx<float>*, const cx<double>*, double, cx<double>*, cudaStream_t);
-template void launch_apply_ff3<double>(const ff3::FineFF3&, const cx<double>*, const cx<double>*, double, cx<double>*, cudaStream_t);
+template void launch_apply_ff3<float>(const ff3::FineFF3&, const cx<float>*, const cx<double>*, double, void*, bool,
+                                      cudaStream_t);
+template void launch_apply_ff3<double>(const ff3::FineFF3&, const cx<double>*, const cx<double>*, double, void*, bool,
+                                       cudaStream_t);
 
 // y = H^H x (or bscale b - H^H x) of the finest 3D operator in float-float arithmetic on the
 // forward apply's coefficient arrays (adjoint_ff3.cuh).
 template <typename TI>
-void launch_apply_adjoint_ff3(const ff3::FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale,
-                              cx<double>* y, cudaStream_t st) {
+void launch_apply_adjoint_ff3(const ff3::FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, void* y,
+                              bool ffo, cudaStream_t st) {
   dim3 grid((g.nx + ff3::BX - 1) / ff3::BX, (g.ny + ff3::BY - 1) / ff3::BY, (g.nz + ff3::BZ - 1) / ff3::BZ);
-  ff3::apply_adjoint<TI><<<grid, dim3(ff3::BX, ff3::BY, ff3::BZ), 0, st>>>(g, x, b, bscale, y);
+  if (ffo) ff3::apply_adjoint<TI, true><<<grid, dim3(ff3::BX, ff3::BY, ff3::BZ), 0, st>>>(g, x, b, bscale, y);
+  else ff3::apply_adjoint<TI, false><<<grid, dim3(ff3::BX, ff3::BY, ff3::BZ), 0, st>>>(g, x, b, bscale, y);
 }
-template void launch_apply_adjoint_ff3<float>(const ff3::FineFF3&, const cx<float>*, const cx<double>*, double,
-                                              cx<double>*, cudaStream_t);
+template void launch_apply_adjoint_ff3<float>(const ff3::FineFF3&, const cx<float>*, const cx<double>*, double, void*,
+                                              bool, cudaStream_t);
 template void launch_apply_adjoint_ff3<double>(const ff3::FineFF3&, const cx<double>*, const cx<double>*, double,
-                                               cx<double>*, cudaStream_t);
+                                               void*, bool, cudaStream_t);

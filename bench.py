@@ -722,7 +722,7 @@ def bench_gradient(args, steps, warmup):
 def tiled_finest(w, paths):
     """True when the finest level's sweeps run the one-pass tiled kernel (2D, FP32)."""
     from paper_2307_03242_gb300 import emg
-    return w.dim == 2 and paths and paths[0] in (emg.SWEEP_TILE24, emg.SWEEP_TILE8)
+    return w.dim == 2 and paths and paths[0] in (emg.SWEEP_TILE24, emg.SWEEP_TILE8, emg.SWEEP_TILE4)
 
 
 def finest_sweep_kernel(w, paths):

@@ -67,10 +67,18 @@ enum { EMG_VANKA_FULL = 0, EMG_VANKA_ECONOMIC = 1 };
  * size and sweep count for the life of the process). The others force one path on every 2D FP32
  * level that can take it (the others keep their automatic choice): EMG_SWEEP_HALF: one launch per
  * colour; EMG_SWEEP_COOP: all sweeps of a call in one cooperative launch; EMG_SWEEP_TILE24 /
- * EMG_SWEEP_TILE8: one launch per sweep, both colours in shared-memory tiles of 60 x 24 / 60 x 8
- * cells (n[0] of the level a multiple of 4). Every path computes the same sweeps (Sec. 3.2);
- * FP32 rounding differs. FP64 cycles and 3D levels ignore the field. */
-enum { EMG_SWEEP_AUTO = 0, EMG_SWEEP_HALF = 1, EMG_SWEEP_COOP = 2, EMG_SWEEP_TILE24 = 3, EMG_SWEEP_TILE8 = 4 };
+ * EMG_SWEEP_TILE8 / EMG_SWEEP_TILE4: one launch per sweep, both colours in shared-memory tiles of
+ * 60 x 24 / 60 x 8 / 60 x 4 cells (n[0] of the level a multiple of 4; the smaller tiles give
+ * small levels more blocks with shorter latency chains). Every path computes the same sweeps
+ * (Sec. 3.2); FP32 rounding differs. FP64 cycles and 3D levels ignore the field. */
+enum {
+  EMG_SWEEP_AUTO = 0,
+  EMG_SWEEP_HALF = 1,
+  EMG_SWEEP_COOP = 2,
+  EMG_SWEEP_TILE24 = 3,
+  EMG_SWEEP_TILE8 = 4,
+  EMG_SWEEP_TILE4 = 5
+};
 
 /* Solver description. All lengths in the same unit as h. */
 typedef struct {
@@ -264,7 +272,7 @@ emg_status emg_profile(emg_handle h, int enable);
 emg_status emg_profile_read(emg_handle h, int kernel_class, double* total_ms, int64_t* launches,
                             double* bytes);
 
-/* The sweep path level `level` took (EMG_SWEEP_HALF .. EMG_SWEEP_TILE8) and, when it was chosen
+/* The sweep path level `level` took (EMG_SWEEP_HALF .. EMG_SWEEP_TILE4) and, when it was chosen
  * by timing, the measured time of one smoothing call of the level in microseconds (else 0).
  * No counterpart in the paper: it reports the autotuner's choice. */
 emg_status emg_sweep_path(emg_handle h, int level, int32_t* path, double* us_per_call);

@@ -378,8 +378,11 @@ constexpr long long kCoopMaxColourCells = 1 << 17;
 // Whether level l's sweeps run as one-pass tiled sweeps (k2t::sweep_tile).
 bool tiled_level(const emg_ctx& c, int l) {
   const int p = c.lv[l].path;
-  return p == EMG_SWEEP_TILE24 || p == EMG_SWEEP_TILE8;
+  return p == EMG_SWEEP_TILE24 || p == EMG_SWEEP_TILE8 || p == EMG_SWEEP_TILE4;
 }
+
+// Tile height of a one-pass tiled path.
+int tile_height(int path) { return path == EMG_SWEEP_TILE24 ? 24 : (path == EMG_SWEEP_TILE8 ? 8 : 4); }
 
 // Whether a sweep path can run level l.
 bool path_ok(const emg_ctx& c, int l, int path) {
@@ -388,7 +391,8 @@ bool path_ok(const emg_ctx& c, int l, int path) {
     case EMG_SWEEP_HALF: return true;
     case EMG_SWEEP_COOP: return c.dim == 2;
     case EMG_SWEEP_TILE24:
-    case EMG_SWEEP_TILE8: return c.dim == 2 && c.prec == 32 && L.n[0] % 4 == 0 && L.n[0] >= 4;
+    case EMG_SWEEP_TILE8:
+    case EMG_SWEEP_TILE4: return c.dim == 2 && c.prec == 32 && L.n[0] % 4 == 0 && L.n[0] >= 4;
     default: return false;
   }
 }
@@ -433,7 +437,7 @@ cx<T>* smooth2(emg_ctx& c, int l, const cx<T>* b, cx<T>* cur, cx<T>* other, int 
   }
   if constexpr (std::is_same<T, float>::value) {
     if (tiled_level(c, l)) {
-      const int ty = L.path == EMG_SWEEP_TILE24 ? 24 : 8;
+      const int ty = tile_height(L.path);
       if (!sweep_tile_fits(g, b, cur, other)) raise(EMG_ERR_INVALID, "sweep buffers are not 16-byte aligned");
       for (int s = 0; s < sweeps; ++s) {
         const bool zin = zero_first && s == 0;
@@ -559,7 +563,7 @@ void choose_sweep_paths(emg_ctx& c) {
     // every process
     const long long colour_cells = (long long)((L.n[0] + 1) / 2) * L.n[1];
     std::vector<int> cand;
-    for (int p : {EMG_SWEEP_TILE24, EMG_SWEEP_TILE8})
+    for (int p : {EMG_SWEEP_TILE24, EMG_SWEEP_TILE8, EMG_SWEEP_TILE4})
       if (path_ok(c, l, p)) cand.push_back(p);
     if (colour_cells <= (1 << 19)) cand.push_back(EMG_SWEEP_COOP);
     cand.push_back(EMG_SWEEP_HALF);
@@ -596,11 +600,11 @@ void residual_restrict(emg_ctx& c, int l, const cx<T>* b, const cx<T>* x, cx<T>*
   ProfScope ps(c, EMG_K_RESTRICT, l, (double)L.ncell * (2 * (c.dim + 1) * cw + 3 * sizeof(T)) + C.ncell * (c.dim + 1) * cw);
   if constexpr (std::is_same<T, float>::value) {
     // 2D FP32 levels whose rows meet the tile kernel's alignment rule: one pass, no fine residual
-    // in memory; 60 x 24 tiles where they fill the GPU twice over, 60 x 8 tiles otherwise
+    // in memory; the tallest tiles (60 x 24, 60 x 8, 60 x 4) that still fill the GPU twice over
     if (c.dim == 2 && path_ok(c, l, EMG_SWEEP_TILE24) &&
         !(((uintptr_t)b | (uintptr_t)x | (uintptr_t)bc) % 16)) {
-      const long long tiles24 = (long long)((L.n[0] + 59) / 60) * ((L.n[1] + 23) / 24);
-      const int ty = tiles24 >= 2LL * c.sms ? 24 : 8;
+      const long long cols = (L.n[0] + 59) / 60;
+      const int ty = cols * ((L.n[1] + 23) / 24) >= 2LL * c.sms ? 24 : (cols * ((L.n[1] + 7) / 8) >= 2LL * c.sms ? 8 : 4);
       CK(launch_resid_restrict_tile(g, b, x, bc, C.n[0], C.n[1], ty, c.dev_err.as<int>(), c.st));
       LAUNCHED(c);
       return;
@@ -1485,7 +1489,7 @@ void check_level_params(const emg_params* p) {
   if (p->cycle_type != EMG_CYCLE_V && p->cycle_type != EMG_CYCLE_W && p->cycle_type != EMG_CYCLE_K)
     raise(EMG_ERR_INVALID, "unknown cycle_type");
   if (p->smoother != EMG_VANKA_FULL && p->smoother != EMG_VANKA_ECONOMIC) raise(EMG_ERR_INVALID, "unknown smoother");
-  if (p->sweep_path < EMG_SWEEP_AUTO || p->sweep_path > EMG_SWEEP_TILE8) raise(EMG_ERR_INVALID, "unknown sweep_path");
+  if (p->sweep_path < EMG_SWEEP_AUTO || p->sweep_path > EMG_SWEEP_TILE4) raise(EMG_ERR_INVALID, "unknown sweep_path");
 }
 
 // Every check of emg_create: one level's, then the hierarchy's.

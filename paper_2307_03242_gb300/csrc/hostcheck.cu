@@ -574,14 +574,15 @@ long emg_hc_kz_steps(int dim, const int* n, const int* box, const double* coef, 
 int emg_hc_resid_restrict_tiled(const int* n, double h, double beta, double omega, double att, double abl_len,
                                 double abl_gmax, double Lx, double Ly, const double* mu, const double* rho,
                                 const double* cp, const double* b64, const double* x64, double* bc64, int ty) {
-  if (n[0] % 4 || n[0] < 4 || n[1] < 2 || (ty != 24 && ty != 8)) return -1;
+  if (n[0] % 4 || n[0] < 4 || n[1] < 2 || (ty != 24 && ty != 8 && ty != 4)) return -1;
   Level2<float> L(n, h, beta, omega, att, abl_len, abl_gmax, Lx, Ly, mu, rho, cp);
   const size_t N = (size_t)n[0] * n[1];
   const int nxc = n[0] / 2, nyc = n[1] / 2;
   std::vector<cx<float>> b = to_cx<float>(b64, 3 * N), x = to_cx<float>(x64, 3 * N),
                          bc(3 * (size_t)nxc * nyc, mkc<float>(std::numeric_limits<float>::quiet_NaN(), 0.f));
   if (ty == 24) resid_restrict_tiled<24>(L.g, b.data(), x.data(), bc.data(), nxc, nyc);
-  else resid_restrict_tiled<8>(L.g, b.data(), x.data(), bc.data(), nxc, nyc);
+  else if (ty == 8) resid_restrict_tiled<8>(L.g, b.data(), x.data(), bc.data(), nxc, nyc);
+  else resid_restrict_tiled<4>(L.g, b.data(), x.data(), bc.data(), nxc, nyc);
   from_cx(bc, bc64);
   return 0;
 }
@@ -641,7 +642,7 @@ int emg_hc_prolong_sweep_tiled(const int* n, double h, double beta, double omega
                                double abl_gmax, double Lx, double Ly, const double* mu, const double* rho,
                                const double* cp, const double* b64, const double* e64, double* x64, double w,
                                int sweeps, int ty) {
-  if (ty != 24 && ty != 8) return -1;
+  if (ty != 24 && ty != 8 && ty != 4) return -1;
   if (n[0] % 4 || n[0] < 4 || n[1] < 2 || sweeps < 1) return -1;
   Level2<float> L(n, h, beta, omega, att, abl_len, abl_gmax, Lx, Ly, mu, rho, cp);
   const size_t N = (size_t)n[0] * n[1];
@@ -652,7 +653,8 @@ int emg_hc_prolong_sweep_tiled(const int* n, double h, double beta, double omega
   for (int s = 0; s < sweeps; ++s) {
     for (auto& v : y) v = mkc<float>(nan, nan);
     if (ty == 24) sweep_tiled<24>(L.g, b.data(), x.data(), y.data(), (float)w, 0, s == 0 ? e.data() : nullptr, nxc, nyc);
-    else sweep_tiled<8>(L.g, b.data(), x.data(), y.data(), (float)w, 0, s == 0 ? e.data() : nullptr, nxc, nyc);
+    else if (ty == 8) sweep_tiled<8>(L.g, b.data(), x.data(), y.data(), (float)w, 0, s == 0 ? e.data() : nullptr, nxc, nyc);
+    else sweep_tiled<4>(L.g, b.data(), x.data(), y.data(), (float)w, 0, s == 0 ? e.data() : nullptr, nxc, nyc);
     std::swap(x, y);
   }
   from_cx(x, x64);
@@ -666,7 +668,7 @@ int emg_hc_prolong_sweep_tiled(const int* n, double h, double beta, double omega
 int emg_hc_sweep_tiled(const int* n, double h, double beta, double omega, double att, double abl_len, double abl_gmax,
                        double Lx, double Ly, const double* mu, const double* rho, const double* cp, const double* b64,
                        double* x64, double w, int sweeps, int zero_first, int ty) {
-  if (n[0] % 4 || n[0] < 4 || n[1] < 2 || (ty != 24 && ty != 8)) return -1;
+  if (n[0] % 4 || n[0] < 4 || n[1] < 2 || (ty != 24 && ty != 8 && ty != 4)) return -1;
   Level2<float> L(n, h, beta, omega, att, abl_len, abl_gmax, Lx, Ly, mu, rho, cp);
   const size_t N = (size_t)n[0] * n[1];
   std::vector<cx<float>> b = to_cx<float>(b64, 3 * N), x = to_cx<float>(x64, 3 * N), y(3 * N);
@@ -674,14 +676,16 @@ int emg_hc_sweep_tiled(const int* n, double h, double beta, double omega, double
   for (int s = 0; s < sweeps; ++s) {
     for (auto& v : y) v = mkc<float>(nan, nan);  // every entry must be written
     if (ty == 24) sweep_tiled<24>(L.g, b.data(), x.data(), y.data(), (float)w, (zero_first && s == 0) ? 1 : 0);
-    else sweep_tiled<8>(L.g, b.data(), x.data(), y.data(), (float)w, (zero_first && s == 0) ? 1 : 0);
+    else if (ty == 8) sweep_tiled<8>(L.g, b.data(), x.data(), y.data(), (float)w, (zero_first && s == 0) ? 1 : 0);
+    else sweep_tiled<4>(L.g, b.data(), x.data(), y.data(), (float)w, (zero_first && s == 0) ? 1 : 0);
     std::swap(x, y);
   }
   from_cx(x, x64);
   int interior = 0;
   for (int by = 0; by < (n[1] + ty - 1) / ty; ++by)
     for (int bx = 0; bx < (n[0] + k2t::TX - 1) / k2t::TX; ++bx) {
-      const k2t::Tile t = ty == 24 ? k2t::tile_of<k2t::Geo<24>>(L.g, bx, by) : k2t::tile_of<k2t::Geo<8>>(L.g, bx, by);
+      const k2t::Tile t = ty == 24 ? k2t::tile_of<k2t::Geo<24>>(L.g, bx, by)
+                                   : (ty == 8 ? k2t::tile_of<k2t::Geo<8>>(L.g, bx, by) : k2t::tile_of<k2t::Geo<4>>(L.g, bx, by));
       interior += t.fast ? 1 : 0;
     }
   return interior;

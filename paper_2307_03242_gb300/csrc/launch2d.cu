@@ -185,6 +185,7 @@ cudaError_t launch_sweep_tile(const Grid<float>& g, const cx<float>* b, const cx
   if (e && (zero_in || nxc * 2 != g.nx || nyc * 2 != g.ny || ((uintptr_t)e % 16))) return cudaErrorInvalidValue;
   if (ty == 24) return launch_sweep_tile_ty<24>(g, b, xin, xout, w, zero_in, e, nxc, nyc, err, st);
   if (ty == 8) return launch_sweep_tile_ty<8>(g, b, xin, xout, w, zero_in, e, nxc, nyc, err, st);
+  if (ty == 4) return launch_sweep_tile_ty<4>(g, b, xin, xout, w, zero_in, e, nxc, nyc, err, st);
   return cudaErrorInvalidValue;
 }
 
@@ -230,5 +231,6 @@ cudaError_t launch_resid_restrict_tile(const Grid<float>& g, const cx<float>* b,
   if (nxc * 2 != g.nx || nyc * 2 != g.ny) return cudaErrorInvalidValue;
   if (ty == 24) return launch_resid_restrict_tile_ty<24>(g, b, x, bc, nxc, nyc, err, st);
   if (ty == 8) return launch_resid_restrict_tile_ty<8>(g, b, x, bc, nxc, nyc, err, st);
+  if (ty == 4) return launch_resid_restrict_tile_ty<4>(g, b, x, bc, nxc, nyc, err, st);
   return cudaErrorInvalidValue;
 }

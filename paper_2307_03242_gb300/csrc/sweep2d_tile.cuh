@@ -60,7 +60,7 @@ struct Geo {
   static constexpr int OFF_U = 0;
   static constexpr int OFF_V = OFF_U + 3 * PLANE * 8;
   static constexpr int OFF_MU = OFF_V + 2 * PLANE * 8;
-  static constexpr int OFF_RHO = OFF_MU + PLANE * 4;
+  static constexpr int OFF_RHO = (OFF_MU + PLANE * 4 + 127) / 128 * 128;  // 128-byte aligned for TMA
   static constexpr int OFF_BAR = OFF_RHO + PLANE * 4;
   static constexpr int SMEM_BYTES = OFF_BAR + 16 + 128;  // + slack for aligning the base
   static constexpr unsigned BYTES_X = 3u * PLANE * 8u, BYTES_MAT = 2u * PLANE * 4u;

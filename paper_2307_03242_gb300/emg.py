@@ -18,8 +18,9 @@ COARSE_DENSE, COARSE_SMOOTH, COARSE_KACZMARZ = 0, 1, 2
 CYCLE_V, CYCLE_W, CYCLE_K = 0, 1, 2
 K_SMOOTH, K_RESTRICT, K_PROLONG, K_APPLY64, K_KRYLOV, K_COARSE = range(6)
 VANKA_FULL, VANKA_ECONOMIC = 0, 1
-SWEEP_AUTO, SWEEP_HALF, SWEEP_COOP, SWEEP_TILE24, SWEEP_TILE8 = 0, 1, 2, 3, 4
-SWEEP_NAMES = {SWEEP_HALF: "half", SWEEP_COOP: "coop", SWEEP_TILE24: "tile24", SWEEP_TILE8: "tile8"}
+SWEEP_AUTO, SWEEP_HALF, SWEEP_COOP, SWEEP_TILE24, SWEEP_TILE8, SWEEP_TILE4 = 0, 1, 2, 3, 4, 5
+SWEEP_NAMES = {SWEEP_HALF: "half", SWEEP_COOP: "coop", SWEEP_TILE24: "tile24", SWEEP_TILE8: "tile8",
+               SWEEP_TILE4: "tile4"}
 K_ALL = 6
 
 STATUS = {0: "EMG_OK", 1: "EMG_ERR_INVALID", 2: "EMG_ERR_NOMEM", 3: "EMG_ERR_CUDA", 4: "EMG_ERR_NONFINITE",

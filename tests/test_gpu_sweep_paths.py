@@ -1,6 +1,7 @@
 """Every sweep path of 2D FP32 levels against the oracle: one launch per colour (half), all
 sweeps in one cooperative launch (coop), and the one-pass shared-memory tiled sweep with tiles of
-60 x 24 and 60 x 8 cells (tile24, tile8), forced on every level; and the autotuned choice.
+60 x 24, 60 x 8 and 60 x 4 cells (tile24, tile8, tile4), forced on every level; and the autotuned
+choice.
 
 The grids reach several tiles in each direction with a ragged last tile (200 x 72: four tile
 columns, the last 20 cells wide), tiles inside the absorbing layer, on the boundary and, for the
@@ -16,7 +17,7 @@ from _gpu_helpers import oracle_problem, oracle_hierarchy, gpu_solver, random_fi
 
 pytestmark = pytest.mark.gpu
 
-PATHS = {"half": 1, "coop": 2, "tile24": 3, "tile8": 4}
+PATHS = {"half": 1, "coop": 2, "tile24": 3, "tile8": 4, "tile4": 5}
 
 
 def _w(n=(200, 72), levels=3, abl=5):

@@ -220,7 +220,7 @@ def test_host_3d_float_float_adjoint_apply_matches_the_oracle(hc, n, abl):
 TILED = {"72x40": ((72, 40), 3, 5), "200x64": ((200, 64), 2, 5), "124x36_layer": ((124, 36), 2, 12)}
 
 
-@pytest.mark.parametrize("ty", [24, 8])
+@pytest.mark.parametrize("ty", [24, 8, 4])
 @pytest.mark.parametrize("case", list(TILED))
 @pytest.mark.parametrize("level", [0, 1])
 @pytest.mark.parametrize("sweeps,zero_first", [(1, 0), (2, 1)])
@@ -257,7 +257,7 @@ def test_host_tiled_sweep_matches_the_oracle(hc, case, level, sweeps, zero_first
     assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("ty", [24, 8])
+@pytest.mark.parametrize("ty", [24, 8, 4])
 @pytest.mark.parametrize("case", ["72x40", "200x64"])
 @pytest.mark.parametrize("sweeps", [1, 2])
 def test_host_tiled_sweep_with_prolongation_matches_the_oracle(hc, case, sweeps, ty):
@@ -372,7 +372,7 @@ def test_float_float_join_is_within_one_ulp_of_the_exact_sum(hc):
     assert out4[0] == np.inf and out4[1] == -np.inf and np.isnan(out4[2]) and out4[3] == np.float64(np.float32(3e38))
 
 
-@pytest.mark.parametrize("ty", [24, 8])
+@pytest.mark.parametrize("ty", [24, 8, 4])
 @pytest.mark.parametrize("case", list(TILED))
 @pytest.mark.parametrize("level", [0, 1])
 def test_host_tiled_residual_restriction_matches_the_oracle(hc, case, level, ty):

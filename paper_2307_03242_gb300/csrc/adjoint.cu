@@ -19,6 +19,7 @@ inline int blocks_for(size_t n) {
 template <int D, typename TI, bool FFO>
 __global__ void __launch_bounds__(RT) apply(Grid<double> g, const cx<TI>* __restrict__ x, const cx<double>* b,
                                            double bscale, void* __restrict__ y) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const size_t N = (size_t)g.nx * g.ny * g.nz;
   const cx<TI>* xs[4];
   for (int c = 0; c <= D; ++c) xs[c] = x + (size_t)c * N;
@@ -37,6 +38,7 @@ template <int D>
 __global__ void __launch_bounds__(RT) gradient(Grid<double> g, const cx<double>* __restrict__ u,
                                               const cx<double>* __restrict__ a, double* __restrict__ glam,
                                               double* __restrict__ gmu, double* __restrict__ grho, int accumulate) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const size_t N = (size_t)g.nx * g.ny * g.nz;
   const cx<double>* us[4];
   const cx<double>* as[4];
@@ -62,6 +64,7 @@ __global__ void __launch_bounds__(RT) gradient(Grid<double> g, const cx<double>*
 
 // z <- S conj(z): the first nu entries (displacements) conjugated, the rest (pressure) negated too
 __global__ void __launch_bounds__(RT) sconj(cx<float>* z, size_t nu, size_t n) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   for (size_t t = (size_t)blockIdx.x * RT + threadIdx.x; t < n; t += (size_t)gridDim.x * RT) {
     const cx<float> v = z[t];
     z[t] = t < nu ? mkc<float>(v.re, -v.im) : mkc<float>(-v.re, v.im);
@@ -74,19 +77,19 @@ template <int D, typename TI>
 void launch_adjoint_apply(const Grid<double>& g, const cx<TI>* x, const cx<double>* b, double bscale, void* y,
                           bool ffo, cudaStream_t st) {
   const size_t N = (size_t)g.nx * g.ny * g.nz;
-  if (ffo) adjk::apply<D, TI, true><<<adjk::blocks_for(N), adjk::RT, 0, st>>>(g, x, b, bscale, y);
-  else adjk::apply<D, TI, false><<<adjk::blocks_for(N), adjk::RT, 0, st>>>(g, x, b, bscale, y);
+  if (ffo) launch_dep(adjk::apply<D, TI, true>, dim3(adjk::blocks_for(N)), dim3(adjk::RT), 0, st, g, x, b, bscale, y);
+  else launch_dep(adjk::apply<D, TI, false>, dim3(adjk::blocks_for(N)), dim3(adjk::RT), 0, st, g, x, b, bscale, y);
 }
 
 template <int D>
 void launch_adjoint_gradient(const Grid<double>& g, const cx<double>* u, const cx<double>* a, double* glam,
                              double* gmu, double* grho, int accumulate, cudaStream_t st) {
   const size_t N = (size_t)g.nx * g.ny * g.nz;
-  adjk::gradient<D><<<adjk::blocks_for(N), adjk::RT, 0, st>>>(g, u, a, glam, gmu, grho, accumulate);
+  launch_dep(adjk::gradient<D>, dim3(adjk::blocks_for(N)), dim3(adjk::RT), 0, st, g, u, a, glam, gmu, grho, accumulate);
 }
 
 void launch_sconj(cx<float>* z, size_t nu, size_t n, cudaStream_t st) {
-  adjk::sconj<<<adjk::blocks_for(n), adjk::RT, 0, st>>>(z, nu, n);
+  launch_dep(adjk::sconj, dim3(adjk::blocks_for(n)), dim3(adjk::RT), 0, st, z, nu, n);
 }
 
 template void launch_adjoint_apply<2, float>(const Grid<double>&, const cx<float>*, const cx<double>*, double, void*,

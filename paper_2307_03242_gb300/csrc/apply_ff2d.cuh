@@ -30,6 +30,7 @@ struct FineFF {
   int nx, ny;
   f2 ih2, ih;        // 1/h^2, 1/h
   f2 t0, t1;         // (1+beta)/2, (1-beta)/4
+  f2 ht2[3], ht1[3]; // t / h^2 and t / h with t = (t1, t0, t1)
   f2 beta, sm;       // beta, (1-beta)/4
   f2 alpha;          // shift added to the attenuation (0 for H, alpha for H_s)
   const f2* mu;      // nx*ny cells
@@ -92,7 +93,6 @@ HD void apply_cell_acc(const FineFF& g, const cx<TI>* __restrict__ x, const cx<d
   const f2 z = {0.f, 0.f};
   auto clampc = [&](int ii, int jj) { return (size_t)iclamp(jj, 0, ny - 1) * nx + iclamp(ii, 0, nx - 1); };
   const f2 muC = g.mu[k];
-  const f2 t[3] = {g.t1, g.t0, g.t1};
   auto mshift = [&](c2 m) {  // m - i alpha Re(m)
     if (g.alpha.hi != 0.f) m.im = add(m.im, fneg(mul(g.alpha, m.re)));
     return m;
@@ -104,6 +104,7 @@ HD void apply_cell_acc(const FineFF& g, const cx<TI>* __restrict__ x, const cx<d
     const f2 nS = g.mun[(size_t)j * (nx + 1) + i], nN = g.mun[(size_t)(j + 1) * (nx + 1) + i];
     const f2 cell[3] = {fneg(muW), add(muW, muC), fneg(muC)};
     const f2 node[3] = {fneg(nS), add(nS, nN), fneg(nN)};
+    cacc a0, a4;
 #pragma unroll
     for (int dj = -1; dj <= 1; ++dj) {
       const int jj = j + dj;
@@ -112,19 +113,18 @@ HD void apply_cell_acc(const FineFF& g, const cx<TI>* __restrict__ x, const cx<d
         const int ii = i + di;
         if (ii < 1 || ii >= nx || jj < 0 || jj >= ny) continue;
         const cx<TI> u = u1[(size_t)jj * nx + ii];
-        const f2 C = mul(g.ih2, add(mul(cell[di + 1], t[dj + 1]), mul(node[dj + 1], t[di + 1])));
+        const f2 C = add(mul(cell[di + 1], g.ht2[dj + 1]), mul(node[dj + 1], g.ht2[di + 1]));
         const f2 ur = ld(u.re), ui = ld(u.im);
         r1.rterm(C, ur, ui);
-        // mass: -(beta m u) at the face, -(sm m u) at the 4 neighbours
-        if (di == 0 && dj == 0) {
-          const c2 m = mshift(g.m1[(size_t)jj * nx + ii]);
-          r1.cterm({fneg(mul(g.beta, m.re)), fneg(mul(g.beta, m.im))}, ur, ui);
-        } else if (di == 0 || dj == 0) {
-          const c2 m = mshift(g.m1[(size_t)jj * nx + ii]);
-          r1.cterm({fneg(mul(g.sm, m.re)), fneg(mul(g.sm, m.im))}, ur, ui);
-        }
+        // mass: m u at the face (a0) and at the 4 neighbours (a4)
+        if (di == 0 || dj == 0) (di == 0 && dj == 0 ? a0 : a4).cterm(mshift(g.m1[(size_t)jj * nx + ii]), ur, ui);
       }
     }
+    // - beta a0 - sm a4
+    r1.re.fms_ff(g.beta, a0.re.norm());
+    r1.im.fms_ff(g.beta, a0.im.norm());
+    r1.re.fms_ff(g.sm, a4.re.norm());
+    r1.im.fms_ff(g.sm, a4.im.norm());
     // + (p(i,j) - p(i-1,j)) / h
     const cx<TI> pc = p[k], pw = p[k - 1];
     r1.rterm(g.ih, ld(pc.re), ld(pc.im));
@@ -137,6 +137,7 @@ HD void apply_cell_acc(const FineFF& g, const cx<TI>* __restrict__ x, const cx<d
     const f2 nW = g.mun[(size_t)j * (nx + 1) + i], nE = g.mun[(size_t)j * (nx + 1) + i + 1];
     const f2 cell[3] = {fneg(muS), add(muS, muC), fneg(muC)};  // along x2 (dj)
     const f2 node[3] = {fneg(nW), add(nW, nE), fneg(nE)};      // along x1 (di)
+    cacc a0, a4;
 #pragma unroll
     for (int dj = -1; dj <= 1; ++dj) {
       const int jj = j + dj;
@@ -145,18 +146,16 @@ HD void apply_cell_acc(const FineFF& g, const cx<TI>* __restrict__ x, const cx<d
         const int ii = i + di;
         if (jj < 1 || jj >= ny || ii < 0 || ii >= nx) continue;
         const cx<TI> u = u2[(size_t)jj * nx + ii];
-        const f2 C = mul(g.ih2, add(mul(cell[dj + 1], t[di + 1]), mul(node[di + 1], t[dj + 1])));
+        const f2 C = add(mul(cell[dj + 1], g.ht2[di + 1]), mul(node[di + 1], g.ht2[dj + 1]));
         const f2 ur = ld(u.re), ui = ld(u.im);
         r2.rterm(C, ur, ui);
-        if (di == 0 && dj == 0) {
-          const c2 m = mshift(g.m2[(size_t)jj * nx + ii]);
-          r2.cterm({fneg(mul(g.beta, m.re)), fneg(mul(g.beta, m.im))}, ur, ui);
-        } else if (di == 0 || dj == 0) {
-          const c2 m = mshift(g.m2[(size_t)jj * nx + ii]);
-          r2.cterm({fneg(mul(g.sm, m.re)), fneg(mul(g.sm, m.im))}, ur, ui);
-        }
+        if (di == 0 || dj == 0) (di == 0 && dj == 0 ? a0 : a4).cterm(mshift(g.m2[(size_t)jj * nx + ii]), ur, ui);
       }
     }
+    r2.re.fms_ff(g.beta, a0.re.norm());
+    r2.im.fms_ff(g.beta, a0.im.norm());
+    r2.re.fms_ff(g.sm, a4.re.norm());
+    r2.im.fms_ff(g.sm, a4.im.norm());
     const cx<TI> pc = p[k], ps = p[k - nx];
     r2.rterm(g.ih, ld(pc.re), ld(pc.im));
     r2.rterm(fneg(g.ih), ld(ps.re), ld(ps.im));
@@ -168,7 +167,7 @@ HD void apply_cell_acc(const FineFF& g, const cx<TI>* __restrict__ x, const cx<d
     for (int dj = -1; dj <= 1; ++dj) {
       const int jj = j + dj;
       if (jj < 0 || jj >= ny) continue;
-      const f2 c = mul(g.ih, t[dj + 1]);
+      const f2 c = g.ht1[dj + 1];
       if (i + 1 < nx) {
         const cx<TI> a = u1[(size_t)jj * nx + i + 1];
         rp.rterm(c, ld(a.re), ld(a.im));
@@ -182,7 +181,7 @@ HD void apply_cell_acc(const FineFF& g, const cx<TI>* __restrict__ x, const cx<d
     for (int di = -1; di <= 1; ++di) {
       const int ii = i + di;
       if (ii < 0 || ii >= nx) continue;
-      const f2 c = mul(g.ih, t[di + 1]);
+      const f2 c = g.ht1[di + 1];
       if (j + 1 < ny) {
         const cx<TI> a = u2[(size_t)(j + 1) * nx + ii];
         rp.rterm(c, ld(a.re), ld(a.im));

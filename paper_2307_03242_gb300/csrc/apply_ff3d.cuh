@@ -218,6 +218,7 @@ template <typename TI, bool FFO>
 __global__ void __launch_bounds__(BX * BY * BZ) apply(FineFF3 g, const cx<TI>* __restrict__ x,
                                                      const cx<double>* __restrict__ b, double bscale,
                                                      void* __restrict__ y) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z * BZ + threadIdx.z;

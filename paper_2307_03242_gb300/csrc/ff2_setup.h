@@ -68,6 +68,10 @@ inline FineFF make(const f2* mu, const f2* mun, const f2* cp, const c2* m1, cons
   g.ih2 = to_f2(1.0 / (h * h));
   g.t0 = to_f2(0.5 * (1.0 + beta));
   g.t1 = to_f2(0.25 * (1.0 - beta));
+  g.ht2[0] = g.ht2[2] = to_f2(0.25 * (1.0 - beta) / (h * h));
+  g.ht2[1] = to_f2(0.5 * (1.0 + beta) / (h * h));
+  g.ht1[0] = g.ht1[2] = to_f2(0.25 * (1.0 - beta) / h);
+  g.ht1[1] = to_f2(0.5 * (1.0 + beta) / h);
   g.beta = to_f2(beta);
   g.sm = to_f2(0.25 * (1.0 - beta));
   g.alpha = to_f2(alpha);

@@ -46,6 +46,7 @@ HD void cell_solve(cx<T> a[3][4], const bool ex[6], T ih, T w00, T cp, cx<T> r[7
 template <typename T, typename TI>
 __global__ void __launch_bounds__(BX * BY * BZ) apply(Grid<T> g, const cx<TI>* __restrict__ x,
                                                      const cx<T>* __restrict__ b, T bscale, cx<T>* __restrict__ y) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z * BZ + threadIdx.z;
@@ -69,6 +70,7 @@ template <typename T>
 __global__ void __launch_bounds__(BX * BY * BZ) vanka(Grid<T> g, const cx<T>* __restrict__ b,
                                                      const cx<T>* __restrict__ uin, cx<T>* __restrict__ uout,
                                                      cx<T>* p, int colour, T w, int zero_in) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const int ip = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z * BZ + threadIdx.z;
@@ -128,6 +130,7 @@ __global__ void __launch_bounds__(BX * BY * BZ) vanka(Grid<T> g, const cx<T>* __
 template <typename T>
 __global__ void __launch_bounds__(BX * BY * BZ) prolong_add(const cx<T>* __restrict__ e, cx<T>* __restrict__ x,
                                                            int nx, int ny, int nz, int nxc, int nyc, int nzc) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z * BZ + threadIdx.z;

@@ -122,6 +122,7 @@ HD void residual_cell3(const Grid<T>& g, const cx<T>* __restrict__ b, const cx<T
 template <typename T>
 __global__ void __launch_bounds__(BX * BY * BZ, 2) residual(Grid<T> g, const cx<T>* __restrict__ b,
                                                         const cx<T>* __restrict__ x, cx<T>* __restrict__ r) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z * BZ + threadIdx.z;
@@ -147,6 +148,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, 2) residual(Grid<T> g, const cx<
 template <typename T>
 __global__ void __launch_bounds__(BX * BY * BZ) restrict_r(const cx<T>* __restrict__ r, cx<T>* __restrict__ bc,
                                                           int nx, int ny, int nz, int nxc, int nyc, int nzc) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   const int I = blockIdx.x * BX + threadIdx.x;
   const int J = blockIdx.y * BY + threadIdx.y;
   const int K = blockIdx.z * BZ + threadIdx.z;

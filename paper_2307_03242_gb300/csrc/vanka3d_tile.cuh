@@ -228,6 +228,7 @@ HD void tile_compute(const Tile<T>& s, const Grid<T>& g, cx<T>* uout, cx<T>* p, 
 template <typename T>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) vanka_tile(Grid<T> g, const cx<T>* __restrict__ b, const cx<T>* __restrict__ uin,
                                                    cx<T>* __restrict__ uout, cx<T>* p, int colour, T w, int zero_in) {
+  grid_dependency_wait();  // launched with programmatic stream serialisation
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Tile<T>& s = *reinterpret_cast<Tile<T>*>(smem_raw);
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;

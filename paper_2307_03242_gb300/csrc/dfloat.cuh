@@ -1,11 +1,12 @@
 // Double-FP32 ("float-float") arithmetic for the FP64 outer solve on a part whose FP64 pipe is
 // ~57x slower than its FP32 pipe. A value is hi + lo with two floats; products use Dekker's
-// error-free product via FMA (p = a*b, e = fma(a, b, -p)), sums use Knuth's TwoSum. Vectors stay
-// IEEE FP64 in memory: a double is split EXACTLY into hi + lo with integer operations only
-// (hi = the double truncated to 24 significant bits, lo = the remaining mantissa bits, rounded to
-// 24 bits), so the representation error is below 2^-47 relative. Values whose magnitude lies
-// outside the normal float range (about 1e-38 .. 3e38) lose the lo part or overflow; the outer
-// solve keeps its vectors near unit norm, far inside that range.
+// error-free product via FMA (p = a*b, e = fma(a, b, -p)), sums use Knuth's TwoSum. IEEE doubles
+// (the caller's vectors) are split into hi + lo with integer and FP32 operations only (hi = the
+// double truncated to 24 significant bits, lo = the next 23 mantissa bits), so the representation
+// error is below 2^-46 relative, and assembled back the same way (join); the outer solve's
+// internal vectors are stored as float-float pairs (cff). Values whose magnitude lies outside the
+// normal float range (about 1e-38 .. 3e38) lose the lo part or overflow; the outer solve keeps
+// its vectors near unit norm, far inside that range.
 #pragma once
 #include <cmath>
 #include <cstring>

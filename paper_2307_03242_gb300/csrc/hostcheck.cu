@@ -16,6 +16,7 @@
 #include "ff3_setup.h"
 #include "residual2d_fast.cuh"
 #include "residual3d.cuh"
+#include "vanka3d_tile.cuh"
 #include "sweep2d_tile.cuh"
 #include "residual2d_tile.cuh"
 #include "vanka2d_fast.cuh"
@@ -232,6 +233,34 @@ void residual3(const Level2<T, 3>& L, const double* b64, const double* x64, doub
         r[3 * N + q] = b[3 * N + q] - s3::row_p(u, p, g, i, j, k);
       }
   from_cx(r, r64);
+}
+
+// 3D red-black Vanka sweeps with the shared-memory tile kernel (k3t::vanka_tile) on the host:
+// per half-sweep every block's tile_load over its NT lanes, then its tile_compute over them, with
+// the library's ping-pong of the displacements (colour 0 reads x and writes alt, colour 1 reads
+// alt and writes x; p in place). Blocks run one after another, which gives the kernel's result
+// because a half-sweep reads no value that another block writes in it. Needs n >= (16, 8, 4), the
+// kernel's own condition; returns -1 otherwise.
+template <typename T>
+void sweeps3_tile(const Level2<T, 3>& L, const double* b64, double* x64, double w, int sweeps, int zero_first) {
+  const Grid<T>& g = L.g;
+  const size_t N = (size_t)g.nx * g.ny * g.nz;
+  std::vector<cx<T>> b = to_cx<T>(b64, 4 * N), x = to_cx<T>(x64, 4 * N), alt(4 * N, czero<T>());
+  std::vector<k3t::Tile<T>> tile(1);
+  cx<T>* p = x.data() + 3 * N;
+  for (int s = 0; s < sweeps; ++s)
+    for (int colour = 0; colour < 2; ++colour) {
+      const cx<T>* uin = colour == 0 ? x.data() : alt.data();
+      cx<T>* uout = colour == 0 ? alt.data() : x.data();
+      const int zin = (zero_first && s == 0 && colour == 0) ? 1 : 0;
+      for (int z0 = 0; z0 < g.nz; z0 += k3t::TZ)
+        for (int y0 = 0; y0 < g.ny; y0 += k3t::TY)
+          for (int x0 = 0; x0 < g.nx; x0 += k3t::TX) {
+            for (int t = 0; t < k3t::NT; ++t) k3t::tile_load(tile[0], g, b.data(), uin, p, zin, x0, y0, z0, t);
+            for (int t = 0; t < k3t::NT; ++t) k3t::tile_compute(tile[0], g, uout, p, colour, (T)w, zin, x0, y0, z0, t);
+          }
+    }
+  from_cx(x, x64);
 }
 
 // One full sweep of the one-pass tiled kernel (k2t::sweep_tile) on the host: the same tiles, the
@@ -778,6 +807,21 @@ int emg_hc_residual3(int prec, const int* n, double h, double beta, double omega
                                     b, x, r);
   else if (prec == 32) residual3<float>(Level2<float, 3>(n, h, beta, omega, att, abl_len, abl_gmax, Lx, Ly, mu, rho, cp, Lz),
                                         b, x, r);
+  else return 1;
+  return 0;
+}
+
+// 3D tile half-sweeps (sweeps3_tile); -1 for a grid below one tile.
+int emg_hc_vanka3_tile_sweeps(int prec, const int* n, double h, double beta, double omega, double att, double abl_len,
+                              double abl_gmax, double Lx, double Ly, double Lz, const double* mu, const double* rho,
+                              const double* cp, const double* b, double* x, double w, int sweeps, int zero_first) {
+  if (n[0] < k3t::TX || n[1] < k3t::TY || n[2] < k3t::TZ) return -1;
+  if (prec == 64)
+    sweeps3_tile<double>(Level2<double, 3>(n, h, beta, omega, att, abl_len, abl_gmax, Lx, Ly, mu, rho, cp, Lz), b, x, w,
+                         sweeps, zero_first);
+  else if (prec == 32)
+    sweeps3_tile<float>(Level2<float, 3>(n, h, beta, omega, att, abl_len, abl_gmax, Lx, Ly, mu, rho, cp, Lz), b, x, w,
+                        sweeps, zero_first);
   else return 1;
   return 0;
 }

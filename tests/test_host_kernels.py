@@ -146,6 +146,44 @@ def test_host_residual_restriction_matches_the_oracle(hc, case, prec, level):
 
 
 @pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("n,abl", [((20, 10, 6), 2), ((16, 8, 4), 0), ((18, 9, 7), 3)])
+@pytest.mark.parametrize("sweeps,zero_first", [(1, 0), (2, 1)])
+def test_host_3d_tile_sweep_matches_the_oracle(hc, prec, n, abl, sweeps, zero_first):
+    """The 3D shared-memory tile half-sweep (csrc/vanka3d_tile.cuh: 16 x 8 x 4 cells per block,
+    halo box, parity de-interleaved columns), its blocks run one after another with the library's
+    ping-pong of the displacements, against the oracle's red-black sweep. The grids give ragged
+    last tiles in every direction (20 x 10 x 6, 18 x 9 x 7) and a single tile (16 x 8 x 4)."""
+    from oracle.smoother import cell_dofs, cell_blocks, cell_colour
+    w = small_heterogeneous(n, seed=12, levels=1, abl_cells=abl, sigma_cells=2.0)
+    pb = oracle_problem(w)
+    alpha, wd = 0.4, 0.3
+    H = oracle.assemble(pb, alpha)
+    idx = cell_dofs(pb)
+    V = cell_blocks(H, idx)
+    b, x = random_field(pb, 91), random_field(pb, 92)
+    if zero_first:
+        x = np.zeros_like(x)
+    ref = x.ravel()
+    for _ in range(sweeps):
+        ref = red_black_sweep(H, V, idx, cell_colour(pb), b.ravel(), ref, wd)
+    got = np.ascontiguousarray(x.ravel()).copy()
+    if zero_first:
+        got[:] = np.nan  # a zero initial guess must not be read
+    nn = np.array(n, dtype=np.int32)
+    mats = [np.ascontiguousarray(pb.mu.ravel()), np.ascontiguousarray(pb.rho.ravel()),
+            np.ascontiguousarray((1.0 / (pb.lam + pb.mu)).ravel())]
+    bb = np.ascontiguousarray(b.ravel())
+    assert hc.emg_hc_vanka3_tile_sweeps(prec, nn.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.c_double(pb.h),
+                                        ctypes.c_double(pb.beta), ctypes.c_double(pb.omega),
+                                        ctypes.c_double(pb.gamma + alpha), ctypes.c_double(pb.abl_length),
+                                        ctypes.c_double(pb.abl_gamma_max), *[ctypes.c_double(v) for v in pb.domain],
+                                        *[m.ctypes.data_as(DP) for m in mats], _cvec(bb), _cvec(got),
+                                        ctypes.c_double(wd), sweeps, zero_first) == 0
+    tol = 1e-12 if prec == 64 else 2e-5
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("n,abl", [((12, 10, 9), 2), ((16, 8, 8), 3)])
 def test_host_3d_residual_matches_the_oracle(hc, prec, n, abl):
     """The 3D residual kernel's interior variants (the register cube with and without the

@@ -92,7 +92,8 @@ HD c2 csub(c2 a, c2 b) { return {add(a.re, fneg(b.re)), add(a.im, fneg(b.im))}; 
 // 27 values is loaded once and added into the three slab families it belongs to. The continuity
 // row's spread divergence of u_c is ih (S_c(+1) - S_c(0)) with the same slab sums.
 template <typename TI, bool FFO = false>
-HD void cell_rows(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, void* y, int i, int j, int k) {
+HD void cell_rows_factored(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, void* y, int i, int j,
+                           int k) {
   const size_t N = (size_t)g.nx * g.ny * g.nz, kq = lin(g, i, j, k);
   const long long sy = g.nx, sz = (long long)g.nx * g.ny;
   const long long sl[3] = {1, sy, sz};
@@ -212,6 +213,129 @@ HD void cell_rows(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double
     r.rterm(g.cp[kq], asf2(pc.re), asf2(pc.im));
     finish(r, 3 * N + kq);
   }
+}
+
+// The same rows in their direct 27-point form: the coefficient C(delta) of every point formed in
+// float-float from part_e and W, then the products. About twice the instructions of the factored
+// form, but 63 registers: for FP64 input, whose split values double the factored form's live
+// registers (150, one block per SM), it is the faster form (10.7 against ~19 ms per 256^3 launch).
+template <typename TI, bool FFO = false>
+HD void cell_rows_direct(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, void* y, int i, int j,
+                         int k) {
+  const int q[3] = {i, j, k};
+  const size_t N = (size_t)g.nx * g.ny * g.nz, kq = lin(g, i, j, k);
+  auto inside = [&](int a, int bb, int c) { return a >= 0 && a < g.nx && bb >= 0 && bb < g.ny && c >= 0 && c < g.nz; };
+  auto mclamp = [&](int a, int bb, int c) {
+    return g.mu[lin(g, iclamp(a, 0, g.nx - 1), iclamp(bb, 0, g.ny - 1), iclamp(c, 0, g.nz - 1))];
+  };
+  auto mshift = [&](c2 m) {
+    if (g.alpha.hi != 0.f) m.im = add(m.im, fneg(mul(g.alpha, m.re)));
+    return m;
+  };
+  const float bs = b ? df::pow2_float(bscale) : 0.f;
+  auto finish = [&](const cacc& r, size_t at) {
+    if (!b) {
+      ff2::store_row<FFO>(y, at, r);
+      return;
+    }
+    cacc t;
+    t.re = df::scaled_sub_acc(b[at].re, bs, bscale, r.re);
+    t.im = df::scaled_sub_acc(b[at].im, bs, bscale, r.im);
+    ff2::store_row<FFO>(y, at, t);
+  };
+  for (int c = 0; c < 3; ++c) {
+    if (q[c] < 1) {
+      ff2::store_row<FFO>(y, c * N + kq, cacc{});
+      continue;
+    }
+    cacc r;
+    // part_e for the three derivative axes
+    f2 part[3][3];
+    for (int e = 0; e < 3; ++e) {
+      f2 ma, mb;
+      int s[3] = {0, 0, 0};
+      s[e] = 1;
+      if (e == c) {
+        ma = mclamp(i - s[0], j - s[1], k - s[2]);
+        mb = mclamp(i, j, k);
+      } else {
+        const int rr = 3 - c - e;
+        ma = g.edge[rr][lat(g, i, j, k)];
+        mb = g.edge[rr][lat(g, i + s[0], j + s[1], k + s[2])];
+      }
+      part[e][0] = fneg(ma);
+      part[e][1] = add(ma, mb);
+      part[e][2] = fneg(mb);
+    }
+    const cx<TI>* u = x + c * N;
+    for (int dk = -1; dk <= 1; ++dk)
+      for (int dj = -1; dj <= 1; ++dj)
+        for (int di = -1; di <= 1; ++di) {
+          const int a = i + di, bb = j + dj, cc = k + dk;
+          const int qa[3] = {a, bb, cc};
+          if (!inside(a, bb, cc) || qa[c] < 1) continue;
+          const int dl[3] = {di, dj, dk};
+          f2 C = {0.f, 0.f};
+          for (int e = 0; e < 3; ++e) {
+            const int t1 = (e + 1) % 3, t2 = (e + 2) % 3;
+            C = add(C, mul(part[e][dl[e] + 1], g.W[dl[t1] + 1][dl[t2] + 1]));
+          }
+          C = mul(g.ih2, C);
+          const cx<TI> uv = u[lin(g, a, bb, cc)];
+          const f2 ur = ld(uv.re), ui = ld(uv.im);
+          r.rterm(C, ur, ui);
+          const int nz0 = (di != 0) + (dj != 0) + (dk != 0);
+          if (nz0 <= 1) {
+            const c2 m = mshift(g.m[c][lin(g, a, bb, cc)]);
+            const f2 f = nz0 == 0 ? g.beta : g.sm;
+            r.cterm({fneg(mul(f, m.re)), fneg(mul(f, m.im))}, ur, ui);
+          }
+        }
+    int s[3] = {0, 0, 0};
+    s[c] = 1;
+    const cx<TI>* p = x + 3 * N;
+    const cx<TI> pc = p[kq], pm = p[lin(g, i - s[0], j - s[1], k - s[2])];
+    r.rterm(g.ih, ld(pc.re), ld(pc.im));
+    r.rterm(fneg(g.ih), ld(pm.re), ld(pm.im));
+    finish(r, c * N + kq);
+  }
+  {
+    cacc r;
+    for (int c = 0; c < 3; ++c) {
+      const int t1 = (c + 1) % 3, t2 = (c + 2) % 3;
+      const cx<TI>* u = x + c * N;
+      for (int a = -1; a <= 1; ++a)
+        for (int bb = -1; bb <= 1; ++bb) {
+          int o[3] = {0, 0, 0};
+          o[t1] = a;
+          o[t2] = bb;
+          const f2 wgt = mul(g.ih, g.W[a + 1][bb + 1]);
+          // + u_c(q + s_c + o), - u_c(q + o)
+          int hi[3] = {i + o[0], j + o[1], k + o[2]};
+          int lo[3] = {hi[0], hi[1], hi[2]};
+          hi[c] += 1;
+          if (inside(hi[0], hi[1], hi[2]) && hi[c] >= 1) {
+            const cx<TI> uv = u[lin(g, hi[0], hi[1], hi[2])];
+            r.rterm(wgt, ld(uv.re), ld(uv.im));
+          }
+          if (inside(lo[0], lo[1], lo[2]) && lo[c] >= 1) {
+            const cx<TI> uv = u[lin(g, lo[0], lo[1], lo[2])];
+            r.rterm(fneg(wgt), ld(uv.re), ld(uv.im));
+          }
+        }
+    }
+    const cx<TI> pc = x[3 * N + kq];
+    r.rterm(g.cp[kq], ld(pc.re), ld(pc.im));
+    finish(r, 3 * N + kq);
+  }
+}
+
+// The rows as the kernel evaluates them: the factored form for FP32 input (the cycle's output,
+// every iteration), the direct form for FP64 input (the iterate, at restarts).
+template <typename TI, bool FFO = false>
+HD void cell_rows(const FineFF3& g, const cx<TI>* x, const cx<double>* b, double bscale, void* y, int i, int j, int k) {
+  if constexpr (sizeof(TI) == 8) cell_rows_direct<TI, FFO>(g, x, b, bscale, y, i, j, k);
+  else cell_rows_factored<TI, FFO>(g, x, b, bscale, y, i, j, k);
 }
 
 template <typename TI, bool FFO>

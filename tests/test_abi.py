@@ -82,3 +82,21 @@ def test_invalid_material_is_rejected_before_any_device_work():
     st = emg.LIB.emg_create(ctypes.byref(c), good.ctypes.data, good.ctypes.data, good.ctypes.data, 0, None,
                             ctypes.byref(h))
     assert st == 1 and b"smoother" in emg.LIB.emg_last_error()
+
+
+def test_sweep_path_range_is_checked_before_any_device_work():
+    """EMG_SWEEP_TILE4 (5) is the last sweep path; 6 and -1 are rejected with a message, before the
+    library touches a device."""
+    import ctypes
+    import numpy as np
+    from paper_2307_03242_gb300 import emg
+    assert (emg.SWEEP_AUTO, emg.SWEEP_HALF, emg.SWEEP_COOP, emg.SWEEP_TILE24, emg.SWEEP_TILE8, emg.SWEEP_TILE4) == \
+        (0, 1, 2, 3, 4, 5)
+    good = np.ones(64)
+    h = ctypes.c_void_p()
+    for bad in (6, -1):
+        c = emg.Params(n=(8, 8), levels=2).to_c()
+        c.sweep_path = bad
+        st = emg.LIB.emg_create(ctypes.byref(c), good.ctypes.data, good.ctypes.data, good.ctypes.data, 0, None,
+                                ctypes.byref(h))
+        assert st == 1 and b"sweep_path" in emg.LIB.emg_last_error()

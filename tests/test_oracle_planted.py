@@ -268,3 +268,22 @@ def test_planted_schur_sign_breaks_the_direct_solve_pin(monkeypatch):
 def test_planted_narrow_reach_breaks_the_footprint_pin(monkeypatch):
     monkeypatch.setattr(kz, "reach_offsets", lambda d, c: ((1,) * d, (1,) * d))
     _fails(tk.test_reach_is_the_schur_stencil_footprint, (10, 8))
+
+
+def test_planted_unorthogonalised_second_gcr_direction_breaks_the_least_squares_pin(monkeypatch):
+    """K-cycle with the second search direction not orthogonalised against the first."""
+    import oracle.multigrid as mg
+
+    def kcycle_no_orth(hier, r, level):
+        A = hier.H[level]
+        z1 = mg.vcycle(hier, r, None, level)
+        q1 = A @ z1
+        a1 = np.vdot(q1, r) / np.vdot(q1, q1).real
+        r2 = r - a1 * q1
+        z2 = mg.vcycle(hier, r2, None, level)
+        q2 = A @ z2
+        a2 = np.vdot(q2, r2) / np.vdot(q2, q2).real
+        return a1 * z1 + a2 * z2
+
+    monkeypatch.setattr(mg, "kcycle_correction", kcycle_no_orth)
+    _fails(tsol.test_kcycle_correction_is_the_least_squares_combination_of_its_two_cycles)

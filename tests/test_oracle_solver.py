@@ -222,6 +222,28 @@ def test_kcycle_gcr_steps_minimise_the_coarse_residual_and_converge():
     assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
 
 
+def test_kcycle_correction_is_the_least_squares_combination_of_its_two_cycles():
+    """K-cycle (Sec. 2.2): with z1 = B r and z2 = B r2 (r2 the residual after the first step), the
+    two GCR steps return the combination e = c1 z1 + c2 z2 that minimises ||r - A e||; computed
+    here by a least-squares solve (numpy lstsq) on [A z1, A z2], not by the GCR recurrences."""
+    import oracle.multigrid as mg
+    w = small_heterogeneous((32, 32), levels=4, abl_cells=3)
+    pb = _problem(w)
+    hier = oracle.Hierarchy(pb, 4, 0.5, 0.3, coarse="smooth", coarse_sweeps=8, coarse_damping=0.8, cycle="K")
+    rng = np.random.default_rng(9)
+    act = oracle.active_mask(hier.pbs[1])
+    r = (rng.standard_normal(act.size) + 1j * rng.standard_normal(act.size)) * act
+    A = hier.H[1]
+    e = mg.kcycle_correction(hier, r, 1)
+    z1 = oracle.vcycle(hier, r, None, 1)
+    c1 = np.linalg.lstsq((A @ z1)[:, None], r, rcond=None)[0][0]  # the first step: min over span{z1}
+    z2 = oracle.vcycle(hier, r - c1 * (A @ z1), None, 1)
+    Z = np.stack([z1, z2], axis=1)
+    c = np.linalg.lstsq(A @ Z, r, rcond=None)[0]
+    e_ls = Z @ c
+    assert np.linalg.norm(e - e_ls) <= 1e-10 * np.linalg.norm(e_ls)
+
+
 @pytest.mark.parametrize("n", [(8, 6), (4, 4, 4)])
 def test_economic_vanka_keeps_the_pressure_coupling_and_solves_the_pressure_row(n):
     """Economic Vanka (Section 2.3): the displacement part of the cell block becomes its diagonal,
